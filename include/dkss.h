@@ -1,0 +1,157 @@
+/*
+ * dkss.h -- C ABI of the GB300 DKSS multiplication library (libdkss.so).
+ *
+ * The library multiplies nonnegative integers a, b < 2^N exactly with the
+ * De-Kurur-Saha-Saptharishi algorithm as implemented and analysed in
+ * C. Lueders, "Fast Multiplication of Large Integers: Implementation and
+ * Analysis of the DKSS Algorithm" (arXiv:1503.04955), Chapter 3:
+ * encode into R[x] with R = (Z/p^zZ)[alpha]/(alpha^m+1), a 2M-point FFT whose
+ * inner 2m-point butterflies use powers of alpha as negacyclic shifts and whose
+ * outer "bad" twiddles rho^i are full R-multiplications, componentwise
+ * products, the backwards FFT with scaling by (2M)^-1, and decoding with a
+ * device-wide carry scan (Section 3.2, steps 4-8).
+ *
+ * Numbers are little-endian arrays of 64-bit words (Section 2.1): word k holds
+ * bits [64k, 64k+64).  An N-bit operand has ceil(N/64) words and every bit at
+ * or above N must be zero; a product has 2*ceil(N/64) words.
+ *
+ * All entry points return a dkss_status.  Argument and parameter errors are
+ * reported synchronously and leave no work queued.  Work on the GPU is queued
+ * on the caller's stream and returns at once; errors found by a kernel are
+ * recorded in a per-plan device status word, read by dkss_sync_status().
+ * A plan is not safe for concurrent calls from several host threads, and two
+ * calls on one plan must not run concurrently on different streams (they
+ * share the plan's workspace).
+ */
+#ifndef DKSS_H
+#define DKSS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dkss_plan_s* dkss_plan_t;
+typedef struct CUstream_st* dkss_stream_t; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+    DKSS_OK = 0,
+    DKSS_EINVAL = 1,       /* null pointer, aliasing output, size mismatch */
+    DKSS_EPARAM = 2,       /* parameters violate Section 3.2 steps 1-2 (see dkss_plan) */
+    DKSS_ENOMEM = 3,       /* device or host allocation failed */
+    DKSS_EUNSUPPORTED = 4, /* valid parameters this build has no kernel for */
+    DKSS_ECUDA = 5,        /* a CUDA runtime call failed */
+    DKSS_ETIMEOUT = 6,     /* a bounded device-side wait gave up */
+    DKSS_EDEVICE = 7       /* a kernel found an internal inconsistency */
+} dkss_status;
+
+enum {
+    DKSS_FORM_IMAD = 1,    /* R-multiplications on the integer pipe (default) */
+    DKSS_FORM_INT8TC = 2,  /* R-multiplications as exact INT8 tensor-core MMAs */
+    DKSS_PROFILE = 4,      /* reserved: per-stage CUDA-event timing */
+    DKSS_DEBUG_CHECKS = 8  /* reserved: extra device-side range checks */
+};
+
+/*
+ * Build a plan for N-bit operands (thesis Section 3.2 steps 1-3, Section 4.1).
+ *   n_bits  N, 64 <= N; operands are < 2^N.
+ *   M, m    powers of two, 16 <= m <= 64, M >= m, with 2M > 2m (at least one
+ *           radix-2m level); the transform length is 2M.
+ *   u       input bits per inner coefficient, 1 <= u <= 32, M*(m/2)*u >= N.
+ *   p, z    p prime with 2M | p-1 (Section 3.2.2); the residue ring is
+ *           Z/p^zZ; p^z must exceed the largest product coefficient
+ *           M*(m/2)*(2^u-1)^2 (Section 3.2.2) and p^z < 2^126.
+ *   flags   DKSS_FORM_* (IMAD when 0).
+ * On the host it tests p (deterministic Miller-Rabin), finds the smallest
+ * generator zeta of F_p^*, Hensel-lifts it to a (p-1)-th root of unity mod p^z,
+ * forms omega = zeta_z^((p-1)/2M), gamma = omega^(2M/2m) and rho by Lagrange
+ * interpolation (Section 3.2.3, eq. dkss:lagrange), checks rho^(2M/2m) = alpha
+ * and rho^M = -1, and tabulates rho^s, s < 2M/2m (Section 4.2).  It then
+ * allocates the device workspace (two transformed polynomials, the rho^s table,
+ * carry-scan scratch) on the current device, which the plan owns.
+ * Errors: DKSS_EINVAL (plan == NULL), DKSS_EPARAM, DKSS_EUNSUPPORTED,
+ * DKSS_ENOMEM, DKSS_ECUDA.  On error *plan is set to NULL.
+ */
+dkss_status dkss_plan(dkss_plan_t* plan, uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u,
+                      uint64_t p, uint32_t z, uint32_t flags);
+
+/*
+ * out = a * b (thesis Section 3.2 steps 4-8).  a, b: device pointers to
+ * ceil(N/64) words each; out: device pointer to 2*ceil(N/64) words, which must
+ * not overlap a or b.  Queued on `stream`; the caller keeps a, b, out alive
+ * until the stream reaches this work.  Errors: DKSS_EINVAL, DKSS_ECUDA.
+ */
+dkss_status dkss_mul(dkss_plan_t plan, const uint64_t* a, const uint64_t* b, uint64_t* out,
+                     dkss_stream_t stream);
+
+/*
+ * Same product from host memory: copies a and b (ceil(N/64) words each) to the
+ * device, multiplies, copies the 2*ceil(N/64)-word product back to out_host
+ * and waits for the stream.  Host buffers may be pageable or pinned.
+ * Errors: as dkss_mul, plus DKSS_ENOMEM for the plan's staging buffers.
+ */
+dkss_status dkss_mul_host(dkss_plan_t plan, const uint64_t* a_host, const uint64_t* b_host,
+                          uint64_t* out_host, dkss_stream_t stream);
+
+/*
+ * The forward transform alone (Section 3.2 step 5): writes
+ * out[i] = a(rho^i), i < 2M, to out (device, 2M*m residues of 2 words each,
+ * element-major, residue t of element i at words 2*(i*m+t), 2*(i*m+t)+1,
+ * canonical in [0, p^z), natural order).  Used to compare stage results.
+ * Errors: DKSS_EINVAL, DKSS_ECUDA.
+ */
+dkss_status dkss_forward(dkss_plan_t plan, const uint64_t* a, uint64_t* out, dkss_stream_t stream);
+
+/* One job of a batch: operands of n_bits bits, device pointers as dkss_mul. */
+typedef struct {
+    const uint64_t* a;
+    const uint64_t* b;
+    uint64_t* out;
+    uint64_t n_bits;
+} dkss_job;
+
+/*
+ * Multiply `count` independent pairs of any sizes (BASELINE batched workload,
+ * thesis Section 3.2 applied per job).  Reserved: returns DKSS_EUNSUPPORTED in
+ * this build.
+ */
+dkss_status dkss_mul_batch(const dkss_job* jobs, size_t count, uint32_t flags, dkss_stream_t stream);
+
+/*
+ * Host view of a plan's parameters (no device work).  rho_out (may be NULL)
+ * receives rho's m coefficients as 2 words each; consts receives, in order:
+ * 2M, 2M/2m, L (32-bit limbs per residue), transform levels, p^z low word,
+ * p^z high word, generator zeta, omega low, omega high, gamma low, gamma high.
+ */
+dkss_status dkss_plan_info(dkss_plan_t plan, uint64_t* consts, size_t n_consts, uint64_t* rho_out);
+
+/*
+ * Host-only computation of rho for the given parameters (same checks as
+ * dkss_plan, no device allocation); rho_out receives m coefficients of 2 words.
+ * Lets a CPU-only caller inspect the plan's root.  Errors: as dkss_plan.
+ */
+dkss_status dkss_plan_rho(uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, uint64_t p, uint32_t z,
+                          uint64_t* rho_out, uint64_t* consts, size_t n_consts);
+
+/* Kernel launches one dkss_mul call queues (for launch accounting). */
+uint32_t dkss_plan_launches(dkss_plan_t plan);
+
+/*
+ * Wait for `stream`, then return and clear the plan's device status word:
+ * DKSS_OK, or the first device-side error (DKSS_EDEVICE, DKSS_ETIMEOUT).
+ */
+dkss_status dkss_sync_status(dkss_plan_t plan, dkss_stream_t stream);
+
+/* Free a plan and its device memory (waits for the device).  NULL is a no-op. */
+dkss_status dkss_plan_destroy(dkss_plan_t plan);
+
+/* Static text of a status code. */
+const char* dkss_status_str(dkss_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DKSS_H */

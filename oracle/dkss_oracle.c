@@ -323,3 +323,25 @@ int oracle_dkss_mul(uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, const u
     free(ea); free(eb); free(table);
     return 0;
 }
+
+/* One output of the forward transform at frequency i = k*mu, where
+ * rho^(k mu) = alpha^k (Section 3.2.3): a_hat_{k mu} = sum_j a_j alpha^(k j),
+ * the plain definition with shifts and additions only.  Lets a test sample
+ * the transform of operands too large for the full oracle.  out: m residues
+ * of 2 words. */
+int oracle_fft_alpha_point(uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, const uint64_t pz[2],
+                           const uint64_t* a, uint64_t k, uint64_t* out) {
+    par_t par;
+    if (make_par(&par, M, m, u, pz)) return -1;
+    uint64_t nw = (n_bits + 63) / 64;
+    u128 acc[64], el[64], t[64];
+    memset(acc, 0, sizeof(acc));
+    for (uint64_t j = 0; j < par.M; j++) {
+        memset(el, 0, sizeof(el));
+        for (uint32_t c = 0; c < par.h; c++) el[c] = get_bits(a, nw, (uint64_t)u * (j * par.h + c), u);
+        r_shift(t, el, (int64_t)((k * j) % (2 * m)), &par);
+        for (uint32_t c = 0; c < m; c++) acc[c] = add_mod(acc[c], t[c], par.q);
+    }
+    store_r(out, acc, m);
+    return 0;
+}

@@ -39,7 +39,9 @@ def load():
         lib.oracle_dkss_mul.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
                                         ctypes.c_uint32, u64p, u64p, u64p, u64p, u64p,
                                         u64p, u64p, u64p, u64p]
-        for f in (lib.oracle_r_mul, lib.oracle_fft, lib.oracle_dkss_mul):
+        lib.oracle_fft_alpha_point.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
+                                               ctypes.c_uint32, u64p, u64p, ctypes.c_uint64, u64p]
+        for f in (lib.oracle_r_mul, lib.oracle_fft, lib.oracle_dkss_mul, lib.oracle_fft_alpha_point):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -105,3 +107,13 @@ def dkss_mul(a_limbs, b_limbs, par, rho, dumps=False):
                              _ptr(d["c_hat"]) if d else None, _ptr(d["c"]) if d else None)
     assert rc == 0
     return c, d
+
+
+def fft_alpha_point(a_limbs, par, k):
+    """a_hat at frequency k*mu, i.e. sum_j a_j alpha^(k j) (Section 3.2.3: rho^mu = alpha)."""
+    lib = load()
+    a = np.ascontiguousarray(a_limbs, dtype=np.uint64)
+    out = np.zeros(2 * par.m, dtype=np.uint64)
+    rc = lib.oracle_fft_alpha_point(par.n_bits, par.M, par.m, par.u, _ptr(words2([par.pz])), _ptr(a), k, _ptr(out))
+    assert rc == 0
+    return from_words2(out)

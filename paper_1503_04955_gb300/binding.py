@@ -1,0 +1,188 @@
+"""Thin ctypes binding of libdkss.so (include/dkss.h), argument marshalling only.
+
+Every step of a product runs in the library's CUDA kernels; this module only
+converts tensors to pointers and status codes to exceptions.  PyTorch supplies
+device memory and streams.  A missing or unloadable library raises at import
+of the first call: there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import buildlib as _build
+
+_lib = None
+
+DKSS_OK = 0
+STATUS_NAMES = ["DKSS_OK", "DKSS_EINVAL", "DKSS_EPARAM", "DKSS_ENOMEM", "DKSS_EUNSUPPORTED",
+                "DKSS_ECUDA", "DKSS_ETIMEOUT", "DKSS_EDEVICE"]
+FORM_IMAD = 1
+FORM_INT8TC = 2
+
+# Names exported by libdkss.so (include/dkss.h)
+EXPORTS = ["dkss_plan", "dkss_mul", "dkss_mul_host", "dkss_forward", "dkss_mul_batch", "dkss_plan_info",
+           "dkss_plan_rho", "dkss_plan_launches", "dkss_sync_status", "dkss_plan_destroy", "dkss_status_str"]
+
+
+class DkssError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        name = STATUS_NAMES[code] if 0 <= code < len(STATUS_NAMES) else str(code)
+        super().__init__("%s: %s (%s)" % (what, name, load().dkss_status_str(code).decode()))
+
+
+def lib_path():
+    return _build.lib_path()
+
+
+def load():
+    """Load libdkss.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError("libdkss.so is not built (%s); run __graft_entry__.build() "
+                           "or python paper_1503_04955_gb300/buildlib.py" % path)
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    u64, u32, sz = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_size_t
+    lib.dkss_plan.argtypes = [ctypes.POINTER(P), u64, u64, u32, u32, u64, u32, u32]
+    lib.dkss_mul.argtypes = [P, P, P, P, P]
+    lib.dkss_mul_host.argtypes = [P, P, P, P, P]
+    lib.dkss_forward.argtypes = [P, P, P, P]
+    lib.dkss_mul_batch.argtypes = [P, sz, u32, P]
+    lib.dkss_plan_info.argtypes = [P, P, sz, P]
+    lib.dkss_plan_rho.argtypes = [u64, u64, u32, u32, u64, u32, P, P, sz]
+    lib.dkss_plan_launches.argtypes = [P]
+    lib.dkss_plan_launches.restype = u32
+    lib.dkss_sync_status.argtypes = [P, P]
+    lib.dkss_plan_destroy.argtypes = [P]
+    lib.dkss_status_str.argtypes = [ctypes.c_int]
+    lib.dkss_status_str.restype = ctypes.c_char_p
+    for name in ("dkss_plan", "dkss_mul", "dkss_mul_host", "dkss_forward", "dkss_mul_batch",
+                 "dkss_plan_info", "dkss_plan_rho", "dkss_sync_status", "dkss_plan_destroy"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(code, what):
+    if code != DKSS_OK:
+        raise DkssError(code, what)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _words2_to_ints(arr):
+    arr = np.asarray(arr, dtype=np.uint64)
+    return [int(lo) | (int(hi) << 64) for lo, hi in zip(arr[0::2], arr[1::2])]
+
+
+N_CONSTS = 11
+CONST_NAMES = ["P2", "mu", "L", "levels", "pz_lo", "pz_hi", "zeta", "omega_lo", "omega_hi", "gamma_lo", "gamma_hi"]
+
+
+def _consts_dict(c):
+    d = dict(zip(CONST_NAMES, [int(x) for x in c]))
+    d["pz"] = d.pop("pz_lo") | (d.pop("pz_hi") << 64)
+    d["omega"] = d.pop("omega_lo") | (d.pop("omega_hi") << 64)
+    d["gamma"] = d.pop("gamma_lo") | (d.pop("gamma_hi") << 64)
+    return d
+
+
+def plan_rho(n_bits, M, m, u, p, z):
+    """Host-only plan math: (rho coefficients, constants dict)."""
+    lib = load()
+    rho = np.zeros(2 * m, dtype=np.uint64)
+    consts = np.zeros(N_CONSTS, dtype=np.uint64)
+    _check(lib.dkss_plan_rho(n_bits, M, m, u, p, z, rho.ctypes.data, consts.ctypes.data, N_CONSTS), "dkss_plan_rho")
+    return _words2_to_ints(rho), _consts_dict(consts)
+
+
+class Plan:
+    """A DKSS_MUL plan for N-bit operands (dkss_plan)."""
+
+    def __init__(self, n_bits, M, m, u, p, z, flags=0):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.dkss_plan(ctypes.byref(h), n_bits, M, m, u, p, z, flags), "dkss_plan")
+        self._h = h
+        self.n_bits, self.M, self.m, self.u, self.p, self.z = n_bits, M, m, u, p, z
+        self.words = (n_bits + 63) // 64
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().dkss_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def info(self):
+        consts = np.zeros(N_CONSTS, dtype=np.uint64)
+        rho = np.zeros(2 * self.m, dtype=np.uint64)
+        _check(load().dkss_plan_info(self._h, consts.ctypes.data, N_CONSTS, rho.ctypes.data), "dkss_plan_info")
+        d = _consts_dict(consts)
+        d["rho"] = _words2_to_ints(rho)
+        return d
+
+    @property
+    def launches(self):
+        return int(load().dkss_plan_launches(self._h))
+
+    def _check_operand(self, t, n):
+        if not t.is_cuda or t.element_size() != 8 or not t.is_contiguous() or t.numel() != n:
+            raise ValueError("expected a contiguous CUDA tensor of %d 64-bit words" % n)
+
+    def mul(self, a, b, out=None, stream=None):
+        """out = a*b on the GPU; a, b, out: CUDA tensors of 64-bit words (int64/uint64)."""
+        import torch
+        self._check_operand(a, self.words)
+        self._check_operand(b, self.words)
+        if out is None:
+            out = torch.empty(2 * self.words, dtype=a.dtype, device=a.device)
+        self._check_operand(out, 2 * self.words)
+        _check(load().dkss_mul(self._h, a.data_ptr(), b.data_ptr(), out.data_ptr(), _stream_handle(stream)),
+               "dkss_mul")
+        return out
+
+    def mul_host(self, a, b, out=None, stream=None):
+        """Product of host arrays (numpy uint64) through dkss_mul_host."""
+        a = np.ascontiguousarray(a, dtype=np.uint64)
+        b = np.ascontiguousarray(b, dtype=np.uint64)
+        if a.size != self.words or b.size != self.words:
+            raise ValueError("operands must have %d words" % self.words)
+        if out is None:
+            out = np.empty(2 * self.words, dtype=np.uint64)
+        _check(load().dkss_mul_host(self._h, a.ctypes.data, b.ctypes.data, out.ctypes.data,
+                                    _stream_handle(stream)), "dkss_mul_host")
+        return out
+
+    def forward(self, a, stream=None):
+        """Forward transform a(rho^i), natural order: tensor (2M, m, 2) of 64-bit words."""
+        import torch
+        self._check_operand(a, self.words)
+        out = torch.empty((2 * self.M, self.m, 2), dtype=torch.int64, device=a.device)
+        _check(load().dkss_forward(self._h, a.data_ptr(), out.data_ptr(), _stream_handle(stream)), "dkss_forward")
+        return out
+
+    def sync_status(self, stream=None):
+        _check(load().dkss_sync_status(self._h, _stream_handle(stream)), "device status")

@@ -1,0 +1,364 @@
+// C ABI of libdkss (declarations and contracts in include/dkss.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "plan.hpp"
+
+using dkss_host::MontCtx;
+using dkss_host::Relem;
+using dkss_host::u128;
+
+namespace {
+
+bool is_pow2(uint64_t x) { return x && !(x & (x - 1)); }
+
+uint32_t log2u(uint64_t x) {
+    uint32_t r = 0;
+    while (x > 1) { x >>= 1; ++r; }
+    return r;
+}
+
+int bitlen(u128 x) {
+    int n = 0;
+    while (x) { ++n; x >>= 1; }
+    return n;
+}
+
+// x < 2^bits for a 256-bit value held as 5 little-endian words
+bool below_pow2(const uint64_t t[5], int bits) {
+    for (int w = 4; w >= 0; --w) {
+        int lo = 64 * w;
+        if (t[w] == 0) continue;
+        int top = lo + 63 - __builtin_clzll(t[w]);
+        return top < bits;
+    }
+    return true;
+}
+
+typedef dkss_status (*run_mul_fn)(dkss_plan_s*, const uint64_t*, const uint64_t*, uint64_t*, cudaStream_t);
+typedef dkss_status (*run_fwd_fn)(dkss_plan_s*, const uint64_t*, uint64_t*, cudaStream_t);
+typedef dkss_status (*prep_fn)(dkss_plan_s*);
+
+struct Kernels {
+    run_mul_fn mul;
+    run_fwd_fn fwd;
+    prep_fn prep;
+};
+
+template <int m, int L>
+Kernels kernels_for() {
+    return Kernels{&dkss::run_mul<m, L>, &dkss::run_forward<m, L>, &dkss::prepare<m, L>};
+}
+
+bool lookup(uint32_t m, uint32_t L, Kernels* k) {
+#define DKSS_CASE(M_, L_) \
+    if (m == M_ && L == L_) { *k = kernels_for<M_, L_>(); return true; }
+    DKSS_CASE(16, 2) DKSS_CASE(16, 3) DKSS_CASE(16, 4)
+    DKSS_CASE(32, 2) DKSS_CASE(32, 3) DKSS_CASE(32, 4)
+    DKSS_CASE(64, 2) DKSS_CASE(64, 3) DKSS_CASE(64, 4)
+#undef DKSS_CASE
+    return false;
+}
+
+// Everything of a plan that needs no device: parameter checks (Section 3.2
+// steps 1-2), roots (Section 3.2.3) and the limb layout.
+dkss_status plan_host(dkss_plan_s* pl, uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, uint64_t p, uint32_t z) {
+    if (!is_pow2(M) || !is_pow2(m) || m < 2 || M < m || n_bits == 0 || u == 0 || u > 32 || z == 0)
+        return DKSS_EPARAM;
+    if (M >= ((uint64_t)1 << 40)) return DKSS_EPARAM;
+    const uint64_t h = m / 2;
+    if ((u128)M * h * u < n_bits) return DKSS_EPARAM;
+    const uint64_t P2 = 2 * M;
+    if (p < 3 || !dkss_host::is_prime_u64(p) || (p - 1) % P2 != 0) return DKSS_EPARAM;
+    u128 q = 1;
+    for (uint32_t i = 0; i < z; ++i) {
+        if (q > (((u128)1 << 126) / p)) return DKSS_EPARAM;
+        q *= p;
+    }
+    const u128 umax = ((u128)1 << u) - 1;
+    if (!(q > (u128)M * h * umax * umax)) return DKSS_EPARAM;  // largest coefficient M (m/2) (2^u-1)^2
+    if ((u128)m * q >= ((u128)1 << 127)) return DKSS_EPARAM;  // host sums of m products
+    // limbs: one spare bit for sums, and m q^2 + R q < 2^(64L) for the REDC of m-term sums
+    uint32_t L = (uint32_t)((bitlen(q) + 1 + 31) / 32);
+    if (L < 2) L = 2;
+    for (;; ++L) {
+        if (L > 4) return DKSS_EUNSUPPORTED;
+        // t = m q^2 + q 2^(32L) must stay below 2^(64L)
+        uint64_t t[5] = {0, 0, 0, 0, 0};
+        dkss_host::mac256(t, q, q * m);
+        uint64_t add[6] = {0, 0, 0, 0, 0, 0};
+        const int sh = 32 * (int)L;
+        const uint64_t qw[2] = {(uint64_t)q, (uint64_t)(q >> 64)};
+        for (int i = 0; i < 2; ++i) {
+            const int bit = sh + 64 * i, w = bit / 64, s = bit % 64;
+            add[w] |= qw[i] << s;
+            if (s) add[w + 1] |= qw[i] >> (64 - s);
+        }
+        u128 carry = 0;
+        for (int i = 0; i < 5; ++i) {
+            u128 s2 = (u128)t[i] + add[i] + carry;
+            t[i] = (uint64_t)s2;
+            carry = s2 >> 64;
+        }
+        if (!carry && !add[5] && below_pow2(t, 64 * (int)L)) break;
+    }
+    if (m != 16 && m != 32 && m != 64) return DKSS_EUNSUPPORTED;
+    if (P2 <= 2 * (uint64_t)m) return DKSS_EUNSUPPORTED;
+
+    pl->n_bits = n_bits; pl->M = M; pl->P2 = P2; pl->mu_top = P2 / (2 * m); pl->p = p;
+    pl->m = m; pl->u = u; pl->z = z; pl->L = L; pl->q = q;
+    pl->log2_mu_top = log2u(pl->mu_top);
+    // levels: ceil(log2 2M / log2 2m) - 1 radix-2m levels, then one of length <= 2m
+    const uint32_t lg = log2u(P2), k = log2u(2 * m);
+    pl->col_levels = (lg + k - 1) / k - 1;
+    pl->r_last = P2 >> (k * pl->col_levels);
+    for (uint32_t i = 0; i < 4; ++i) pl->q_limbs[i] = i < L ? (uint32_t)(q >> (32 * i)) : 0;
+    {
+        uint32_t q0 = (uint32_t)q, inv = q0;
+        for (int i = 0; i < 5; ++i) inv *= 2 - q0 * inv;
+        pl->nprime = 0u - inv;
+    }
+    const int RB = 32 * (int)L;
+    pl->nsub = (uint32_t)(RB >= 128 ? 0 : (uint64_t)(((u128)m * q) >> RB)) + 1;
+
+    // roots (Section 3.2.3)
+    MontCtx c(q);
+    u128 phi = q / p * (p - 1);
+    dkss_host::Roots& r = pl->roots;
+    r.zeta = dkss_host::smallest_generator(p);
+    r.zeta_z = dkss_host::hensel_lift(r.zeta, p, z);
+    u128 omega_m = c.pow(c.to(r.zeta_z), (p - 1) / P2);
+    u128 gamma_m = c.pow(omega_m, pl->mu_top);
+    r.omega = c.from(omega_m);
+    r.gamma = c.from(gamma_m);
+    Relem rho_m = dkss_host::rho_lagrange(c, omega_m, gamma_m, m, phi - 1);
+    // checks the thesis fixes: rho^(2M/2m) = alpha, rho^M = -1
+    Relem t1 = dkss_host::r_pow(c, rho_m, pl->mu_top);
+    Relem t2 = dkss_host::r_pow(c, rho_m, M);
+    for (uint32_t i = 0; i < m; ++i) {
+        if (t1[i] != (i == 1 ? c.r1 : 0)) return DKSS_EPARAM;
+        if (t2[i] != (i == 0 ? q - c.r1 : 0)) return DKSS_EPARAM;
+    }
+    r.rho.resize(m);
+    for (uint32_t i = 0; i < m; ++i) r.rho[i] = c.from(rho_m[i]);
+    // (2M)^-1 * R_dev^2 mod q, the scaling factor used through one Montgomery product
+    u128 rdev = RB >= 128 ? c.r1 : (((u128)1 << RB) % q);
+    u128 p2inv = c.pow(c.to(P2 % q), phi - 1);          // Montgomery form
+    u128 rdev_m = c.to(rdev);
+    u128 ks = c.from(c.mul(c.mul(p2inv, rdev_m), rdev_m));
+    for (uint32_t i = 0; i < 4; ++i) pl->kscale[i] = i < L ? (uint32_t)(ks >> (32 * i)) : 0;
+    return DKSS_OK;
+}
+
+// rho^s for s < mu_top in device Montgomery form (R = 2^(32L)), m residues of L words each.
+void build_table(const dkss_plan_s* pl, std::vector<uint32_t>& out) {
+    const uint32_t m = pl->m, L = pl->L;
+    const uint64_t mu = pl->mu_top;
+    out.assign(mu * m * L, 0);
+    MontCtx c(pl->q);
+    Relem rho_m(m);
+    for (uint32_t i = 0; i < m; ++i) rho_m[i] = c.to(pl->roots.rho[i]);
+    const int RB = 32 * (int)L;
+    u128 rdev = RB >= 128 ? c.r1 : (((u128)1 << RB) % pl->q);
+    unsigned hw = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    uint64_t chunks = std::min<uint64_t>(hw, mu);
+    std::vector<std::thread> th;
+    for (uint64_t ci = 0; ci < chunks; ++ci) {
+        th.emplace_back([&, ci]() {
+            uint64_t s0 = mu * ci / chunks, s1 = mu * (ci + 1) / chunks;
+            Relem cur = dkss_host::r_pow(c, rho_m, s0);
+            for (uint64_t s = s0; s < s1; ++s) {
+                for (uint32_t t = 0; t < m; ++t) {
+                    u128 v = c.mul(cur[t], rdev);   // rho^s_t * R_dev mod q
+                    for (uint32_t w = 0; w < L; ++w) out[(s * m + t) * L + w] = (uint32_t)(v >> (32 * w));
+                }
+                if (s + 1 < s1) cur = dkss_host::r_mul(c, cur, rho_m);
+            }
+        });
+    }
+    for (auto& t : th) t.join();
+}
+
+void free_device(dkss_plan_s* pl) {
+    cudaFree(pl->d_table);
+    cudaFree(pl->d_work);
+    cudaFree(pl->d_agg);
+    cudaFree(pl->d_status);
+    cudaFree(pl->d_stage);
+    pl->d_table = nullptr; pl->d_work = nullptr; pl->d_agg = nullptr; pl->d_status = nullptr; pl->d_stage = nullptr;
+}
+
+bool overlap(const void* a, size_t an, const void* b, size_t bn) {
+    uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + bn && y < x + an;
+}
+
+void fill_consts(const dkss_plan_s* pl, uint64_t* consts, size_t n) {
+    uint64_t v[11] = {pl->P2, pl->mu_top, pl->L, (uint64_t)pl->col_levels + 1, (uint64_t)pl->q,
+                      (uint64_t)(pl->q >> 64), pl->roots.zeta, (uint64_t)pl->roots.omega,
+                      (uint64_t)(pl->roots.omega >> 64), (uint64_t)pl->roots.gamma,
+                      (uint64_t)(pl->roots.gamma >> 64)};
+    for (size_t i = 0; i < n && i < 11; ++i) consts[i] = v[i];
+}
+
+}  // namespace
+
+extern "C" {
+
+dkss_status dkss_plan(dkss_plan_t* plan, uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, uint64_t p, uint32_t z,
+                      uint32_t flags) {
+    if (!plan) return DKSS_EINVAL;
+    *plan = nullptr;
+    if (flags & DKSS_FORM_INT8TC) return DKSS_EUNSUPPORTED;
+    dkss_plan_s* pl = new (std::nothrow) dkss_plan_s;
+    if (!pl) return DKSS_ENOMEM;
+    pl->flags = flags;
+    dkss_status s = plan_host(pl, n_bits, M, m, u, p, z);
+    Kernels k;
+    if (s == DKSS_OK && !lookup(pl->m, pl->L, &k)) s = DKSS_EUNSUPPORTED;
+    if (s != DKSS_OK) {
+        delete pl;
+        return s;
+    }
+    if (cudaGetDevice(&pl->device) != cudaSuccess) {
+        delete pl;
+        return DKSS_ECUDA;
+    }
+    std::vector<uint32_t> table;
+    build_table(pl, table);
+    pl->poly_words = pl->P2 * pl->m * pl->L;
+    const uint64_t nw = (n_bits + 63) / 64;
+    pl->n_tiles = (4 * nw + 2047) / 2048;
+    bool ok = cudaMalloc(&pl->d_table, table.size() * sizeof(uint32_t)) == cudaSuccess &&
+              cudaMalloc(&pl->d_work, 2 * pl->poly_words * sizeof(uint32_t)) == cudaSuccess &&
+              cudaMalloc(&pl->d_agg, pl->n_tiles * sizeof(uint32_t)) == cudaSuccess &&
+              cudaMalloc(&pl->d_status, sizeof(uint32_t)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_device(pl);
+        delete pl;
+        return DKSS_ENOMEM;
+    }
+    if (cudaMemcpy(pl->d_table, table.data(), table.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(pl->d_status, 0, sizeof(uint32_t)) != cudaSuccess) {
+        free_device(pl);
+        delete pl;
+        return DKSS_ECUDA;
+    }
+    dkss_status ps = k.prep(pl);
+    if (ps != DKSS_OK) {
+        free_device(pl);
+        delete pl;
+        return ps;
+    }
+    *plan = pl;
+    return DKSS_OK;
+}
+
+dkss_status dkss_mul(dkss_plan_t pl, const uint64_t* a, const uint64_t* b, uint64_t* out, dkss_stream_t stream) {
+    if (!pl || !a || !b || !out) return DKSS_EINVAL;
+    const size_t nw = (pl->n_bits + 63) / 64;
+    if (overlap(out, 16 * nw, a, 8 * nw) || overlap(out, 16 * nw, b, 8 * nw)) return DKSS_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != pl->device) return DKSS_EINVAL;
+    Kernels k;
+    if (!lookup(pl->m, pl->L, &k)) return DKSS_EUNSUPPORTED;
+    return k.mul(pl, a, b, out, (cudaStream_t)stream);
+}
+
+dkss_status dkss_mul_host(dkss_plan_t pl, const uint64_t* a_host, const uint64_t* b_host, uint64_t* out_host,
+                          dkss_stream_t stream) {
+    if (!pl || !a_host || !b_host || !out_host) return DKSS_EINVAL;
+    const size_t nw = (pl->n_bits + 63) / 64;
+    if (!pl->d_stage && cudaMalloc(&pl->d_stage, 4 * nw * sizeof(uint64_t)) != cudaSuccess) {
+        cudaGetLastError();
+        pl->d_stage = nullptr;
+        return DKSS_ENOMEM;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    uint64_t* da = pl->d_stage;
+    uint64_t* db = pl->d_stage + nw;
+    uint64_t* dout = pl->d_stage + 2 * nw;
+    if (cudaMemcpyAsync(da, a_host, nw * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(db, b_host, nw * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return DKSS_ECUDA;
+    dkss_status s = dkss_mul(pl, da, db, dout, stream);
+    if (s != DKSS_OK) return s;
+    if (cudaMemcpyAsync(out_host, dout, 2 * nw * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return DKSS_ECUDA;
+    return DKSS_OK;
+}
+
+dkss_status dkss_forward(dkss_plan_t pl, const uint64_t* a, uint64_t* out, dkss_stream_t stream) {
+    if (!pl || !a || !out) return DKSS_EINVAL;
+    Kernels k;
+    if (!lookup(pl->m, pl->L, &k)) return DKSS_EUNSUPPORTED;
+    return k.fwd(pl, a, out, (cudaStream_t)stream);
+}
+
+dkss_status dkss_mul_batch(const dkss_job* jobs, size_t count, uint32_t flags, dkss_stream_t stream) {
+    (void)jobs; (void)count; (void)flags; (void)stream;
+    return DKSS_EUNSUPPORTED;
+}
+
+dkss_status dkss_plan_info(dkss_plan_t pl, uint64_t* consts, size_t n_consts, uint64_t* rho_out) {
+    if (!pl) return DKSS_EINVAL;
+    if (consts) fill_consts(pl, consts, n_consts);
+    if (rho_out)
+        for (uint32_t i = 0; i < pl->m; ++i) {
+            rho_out[2 * i] = (uint64_t)pl->roots.rho[i];
+            rho_out[2 * i + 1] = (uint64_t)(pl->roots.rho[i] >> 64);
+        }
+    return DKSS_OK;
+}
+
+dkss_status dkss_plan_rho(uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, uint64_t p, uint32_t z,
+                          uint64_t* rho_out, uint64_t* consts, size_t n_consts) {
+    dkss_plan_s pl;
+    dkss_status s = plan_host(&pl, n_bits, M, m, u, p, z);
+    if (s != DKSS_OK) return s;
+    return dkss_plan_info(&pl, consts, n_consts, rho_out);
+}
+
+uint32_t dkss_plan_launches(dkss_plan_t pl) { return pl ? pl->launches : 0; }
+
+dkss_status dkss_sync_status(dkss_plan_t pl, dkss_stream_t stream) {
+    if (!pl) return DKSS_EINVAL;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return DKSS_ECUDA;
+    uint32_t st = 0;
+    if (cudaMemcpy(&st, pl->d_status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) return DKSS_ECUDA;
+    if (cudaMemset(pl->d_status, 0, sizeof(uint32_t)) != cudaSuccess) return DKSS_ECUDA;
+    if (st & dkss::kStatusTimeout) return DKSS_ETIMEOUT;
+    if (st) return DKSS_EDEVICE;
+    return DKSS_OK;
+}
+
+dkss_status dkss_plan_destroy(dkss_plan_t pl) {
+    if (!pl) return DKSS_OK;
+    cudaDeviceSynchronize();
+    free_device(pl);
+    delete pl;
+    return DKSS_OK;
+}
+
+const char* dkss_status_str(dkss_status s) {
+    switch (s) {
+        case DKSS_OK: return "ok";
+        case DKSS_EINVAL: return "invalid argument";
+        case DKSS_EPARAM: return "parameters violate the DKSS conditions";
+        case DKSS_ENOMEM: return "out of memory";
+        case DKSS_EUNSUPPORTED: return "unsupported parameters or form";
+        case DKSS_ECUDA: return "CUDA runtime error";
+        case DKSS_ETIMEOUT: return "device-side wait timed out";
+        case DKSS_EDEVICE: return "device-side inconsistency";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,195 @@
+// Host launchers of the DKSS_MUL kernels for one (m, L) pair.
+#pragma once
+#include "decode.cuh"
+#include "dkss_kernels.cuh"
+#include "plan.hpp"
+
+namespace dkss {
+
+template <int L>
+static Mod<L> make_mod(const dkss_plan_s* pl) {
+    Mod<L> md;
+    for (int i = 0; i < L; ++i) md.q[i] = pl->q_limbs[i];
+    md.nprime = pl->nprime;
+    md.nsub = pl->nsub;
+    return md;
+}
+
+static LevelParams make_level(const dkss_plan_s* pl) {
+    LevelParams lp{};
+    lp.data = pl->d_work;
+    lp.table = pl->d_table;
+    lp.poly_words = pl->poly_words;
+    lp.P2 = pl->P2;
+    lp.mu_top = pl->mu_top;
+    lp.M = pl->M;
+    lp.n_bits = pl->n_bits;
+    lp.raw_words = (pl->n_bits + 63) / 64;
+    lp.u = pl->u;
+    lp.log2_mu_top = pl->log2_mu_top;
+    for (int i = 0; i < 4; ++i) lp.kscale[i] = pl->kscale[i];
+    return lp;
+}
+
+// Last forward level alone (root alpha^(2m/len)), for stage output.
+template <int m, int L>
+__global__ void __launch_bounds__(kThreads) k_final_dft(LevelParams prm, Mod<L> md) {
+    using G = Geo<m, L>;
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int n = (int)prm.len;
+    const int log2n = 31 - __clz(n);
+    const uint64_t base = (uint64_t)blockIdx.x * n;
+    for (int idx = threadIdx.x; idx < n * m; idx += kThreads) {
+        int j = idx / m, t = idx % m;
+        uint32_t x[L];
+        ld_res<L>(x, prm.data + ((base + j) * m + t) * L);
+        st_res<L>(smem + bitrev(j, log2n) * G::EW + t * L, x);
+    }
+    __syncthreads();
+    dft_dit<m, L>(smem, smem, 1, n, G::TWO_M / n, md);
+    for (int idx = threadIdx.x; idx < n * m; idx += kThreads) {
+        int j = idx / m, t = idx % m;
+        uint32_t x[L];
+        ld_res<L>(x, smem + j * G::EW + t * L);
+        st_res<L>(prm.data + ((base + j) * m + t) * L, x);
+    }
+}
+
+// Natural-order copy of a transformed polynomial: frequency i sits at the
+// digit-reversed position sum_d v_d * (2M/(2m)^d) + f, where
+// i = v_1 + 2m v_2 + ... + (2m)^levels f.
+template <int m, int L>
+__global__ void k_unpermute(const uint32_t* src, uint64_t* dst, uint64_t P2, uint32_t levels) {
+    uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= P2 * m) return;
+    uint64_t i = idx / m;
+    uint32_t t = (uint32_t)(idx % m);
+    uint64_t rest = i, pos = 0, mu = P2;
+    for (uint32_t d = 0; d < levels; ++d) {
+        mu /= 2 * m;
+        pos += (rest % (2 * m)) * mu;
+        rest /= 2 * m;
+    }
+    pos += rest;
+    const uint32_t* s = src + (pos * m + t) * L;
+    uint64_t lo = s[0] | (L > 1 ? (uint64_t)s[1] << 32 : 0);
+    uint64_t hi = (L > 2 ? s[2] : 0) | (L > 3 ? (uint64_t)s[3] << 32 : 0);
+    dst[2 * idx] = lo;
+    dst[2 * idx + 1] = hi;
+}
+
+#define DKSS_CHECK_LAUNCH()                          \
+    do {                                             \
+        if (cudaGetLastError() != cudaSuccess) return DKSS_ECUDA; \
+    } while (0)
+
+template <int m, int L>
+dkss_status prepare(dkss_plan_s* pl) {
+    using G = Geo<m, L>;
+    const int lvl = (int)level_smem_bytes<m, L>();
+    const int fin = (int)final_smem_bytes<m, L>((int)pl->r_last);
+    const int fdft = (int)(sizeof(uint32_t) * pl->r_last * G::EW);
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device) != cudaSuccess)
+        return DKSS_ECUDA;
+    if (lvl > optin || fin > optin) return DKSS_EUNSUPPORTED;
+    if (cudaFuncSetAttribute(k_fwd_level<m, L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lvl) ||
+        cudaFuncSetAttribute(k_fwd_level<m, L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lvl) ||
+        cudaFuncSetAttribute(k_inv_level<m, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, lvl) ||
+        cudaFuncSetAttribute(k_final_pointwise<m, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, fin) ||
+        cudaFuncSetAttribute(k_final_dft<m, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, fdft))
+        return DKSS_ECUDA;
+    // launches per dkss_mul: forward levels, fused final level, backwards levels, 3 decode
+    pl->launches = pl->col_levels + 1 + pl->col_levels + 3;
+    return DKSS_OK;
+}
+
+template <int m, int L>
+static dkss_status launch_forward_levels(dkss_plan_s* pl, LevelParams lp, int operands, cudaStream_t st) {
+    using G = Geo<m, L>;
+    const size_t smem = level_smem_bytes<m, L>();
+    const Mod<L> md = make_mod<L>(pl);
+    dim3 grid((unsigned)(pl->P2 / G::TWO_M), operands);
+    uint64_t len = pl->P2, bp = 1;
+    for (uint32_t d = 0; d < pl->col_levels; ++d) {
+        lp.len = len;
+        lp.bp = bp;
+        if (d == 0) k_fwd_level<m, L, true><<<grid, kThreads, smem, st>>>(lp, md);
+        else k_fwd_level<m, L, false><<<grid, kThreads, smem, st>>>(lp, md);
+        DKSS_CHECK_LAUNCH();
+        len /= G::TWO_M;
+        bp *= G::TWO_M;
+    }
+    return DKSS_OK;
+}
+
+template <int m, int L>
+dkss_status run_mul(dkss_plan_s* pl, const uint64_t* a, const uint64_t* b, uint64_t* out, cudaStream_t st) {
+    using G = Geo<m, L>;
+    const Mod<L> md = make_mod<L>(pl);
+    LevelParams lp = make_level(pl);
+    lp.raw_a = a;
+    lp.raw_b = b;
+    dkss_status s = launch_forward_levels<m, L>(pl, lp, 2, st);
+    if (s != DKSS_OK) return s;
+    lp.len = pl->r_last;
+    k_final_pointwise<m, L><<<(unsigned)(pl->P2 / pl->r_last), kThreads, final_smem_bytes<m, L>((int)pl->r_last), st>>>(lp, md);
+    DKSS_CHECK_LAUNCH();
+    for (int d = (int)pl->col_levels - 1; d >= 0; --d) {
+        uint64_t bp = 1;
+        for (int i = 0; i < d; ++i) bp *= G::TWO_M;
+        lp.len = pl->P2 / bp;
+        lp.bp = bp;
+        k_inv_level<m, L><<<(unsigned)(pl->P2 / G::TWO_M), kThreads, level_smem_bytes<m, L>(), st>>>(lp, md);
+        DKSS_CHECK_LAUNCH();
+    }
+    DecodeParams dp{};
+    dp.c = pl->d_work;
+    dp.out = reinterpret_cast<uint32_t*>(out);
+    dp.agg = pl->d_agg;
+    dp.status = pl->d_status;
+    dp.P2 = pl->P2;
+    dp.n_windows = 4 * ((pl->n_bits + 63) / 64);
+    dp.n_tiles = pl->n_tiles;
+    dp.k_max = pl->P2 * (m / 2) + m / 2;
+    dp.m = m;
+    dp.h = m / 2;
+    dp.u = pl->u;
+    dp.db = 0;
+    for (dkss_host::u128 t = pl->q; t; t >>= 1) dp.db++;
+    dp.db += 1;
+    dp.out_aligned16 = ((uintptr_t)out & 15) == 0;
+    k_decode_tiles<L><<<(unsigned)pl->n_tiles, kDecThreads, 0, st>>>(dp);
+    DKSS_CHECK_LAUNCH();
+    k_decode_scan<<<1, kScanThreads, 0, st>>>(dp);
+    DKSS_CHECK_LAUNCH();
+    k_decode_fix<<<(unsigned)((pl->n_tiles + 255) / 256), 256, 0, st>>>(dp);
+    DKSS_CHECK_LAUNCH();
+    return DKSS_OK;
+}
+
+template <int m, int L>
+dkss_status run_forward(dkss_plan_s* pl, const uint64_t* a, uint64_t* out, cudaStream_t st) {
+    using G = Geo<m, L>;
+    const Mod<L> md = make_mod<L>(pl);
+    LevelParams lp = make_level(pl);
+    lp.raw_a = a;
+    lp.raw_b = a;
+    dkss_status s = launch_forward_levels<m, L>(pl, lp, 1, st);
+    if (s != DKSS_OK) return s;
+    lp.len = pl->r_last;
+    k_final_dft<m, L><<<(unsigned)(pl->P2 / pl->r_last), kThreads, sizeof(uint32_t) * pl->r_last * G::EW, st>>>(lp, md);
+    DKSS_CHECK_LAUNCH();
+    uint64_t total = pl->P2 * m;
+    k_unpermute<m, L><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(pl->d_work, out, pl->P2, pl->col_levels);
+    DKSS_CHECK_LAUNCH();
+    return DKSS_OK;
+}
+
+}  // namespace dkss
+
+#define DKSS_INSTANTIATE(M_, L_)                                                                            \
+    template dkss_status dkss::run_mul<M_, L_>(dkss_plan_s*, const uint64_t*, const uint64_t*, uint64_t*, \
+                                              cudaStream_t);                                               \
+    template dkss_status dkss::run_forward<M_, L_>(dkss_plan_s*, const uint64_t*, uint64_t*, cudaStream_t); \
+    template dkss_status dkss::prepare<M_, L_>(dkss_plan_s*);

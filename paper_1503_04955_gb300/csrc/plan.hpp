@@ -1,0 +1,44 @@
+// Internal plan object behind dkss_plan_t (include/dkss.h).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/dkss.h"
+#include "host_math.hpp"
+#include "status_bits.hpp"
+
+struct dkss_plan_s {
+    // parameters (thesis Section 3.2 steps 1-2)
+    uint64_t n_bits = 0, M = 0, P2 = 0, mu_top = 0, p = 0;
+    uint32_t m = 0, u = 0, z = 0, flags = 0;
+    uint32_t L = 0;               // 32-bit limbs per residue
+    uint32_t log2_mu_top = 0;
+    uint32_t col_levels = 0;      // radix-2m levels of the transform
+    uint64_t r_last = 0;          // length of the last (alpha-power) level
+    dkss_host::u128 q = 0;        // p^z
+    uint32_t q_limbs[4] = {0, 0, 0, 0};
+    uint32_t nprime = 0, nsub = 0;
+    uint32_t kscale[4] = {0, 0, 0, 0};
+    dkss_host::Roots roots;
+    // device memory owned by the plan
+    int device = 0;
+    uint32_t* d_table = nullptr;  // rho^s (s < mu_top), Montgomery form
+    uint32_t* d_work = nullptr;   // two transformed polynomials
+    uint64_t poly_words = 0;
+    uint32_t* d_agg = nullptr;    // carry-scan tile aggregates
+    uint64_t n_tiles = 0;
+    uint32_t* d_status = nullptr;
+    uint64_t* d_stage = nullptr;  // dkss_mul_host staging: a, b, out
+    uint32_t launches = 0;
+};
+
+namespace dkss {
+// Per-(m, L) launchers, explicitly instantiated in inst_m<m>_L<L>.cu.
+template <int m, int L>
+dkss_status run_mul(dkss_plan_s* pl, const uint64_t* a, const uint64_t* b, uint64_t* out, cudaStream_t st);
+template <int m, int L>
+dkss_status run_forward(dkss_plan_s* pl, const uint64_t* a, uint64_t* out, cudaStream_t st);
+template <int m, int L>
+dkss_status prepare(dkss_plan_s* pl);
+}  // namespace dkss

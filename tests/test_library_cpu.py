@@ -1,0 +1,96 @@
+"""CPU-only checks of the C-ABI library: it loads, exports every symbol that
+include/dkss.h declares, and its host plan math (Section 3.2.2-3.2.3) agrees
+with the oracle.  No kernel is launched."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import dkss_oracle as o
+import dkss_synth as syn
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def dk():
+    import paper_1503_04955_gb300 as pkg
+    pkg.buildlib.build()
+    pkg.load()
+    return pkg
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "dkss.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dkss_[a-z_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(dk):
+    lib = ctypes.CDLL(dk.lib_path())
+    names = declared_symbols()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(dk.EXPORTS)
+
+
+def test_status_strings(dk):
+    lib = dk.load()
+    for code in range(8):
+        assert lib.dkss_status_str(code)
+
+
+GPU_SMALL = [
+    (2000, 32, 16, 8, 193, 4),
+    (26600, 128, 32, 13, 257, 5),
+    (131072, 256, 64, 16, 7681, 4),
+    (262144, 2048, 16, 16, 12289, 4),
+    (786432, 2048, 32, 24, 65537, 5),
+    (1 << 22, 1 << 12, 64, 32, 7340033, 4),
+    (1 << 24, 1 << 14, 64, 32, 998244353, 4),
+]
+
+
+@pytest.mark.parametrize("cfg", [syn.workload_params(k) for k in syn.WORKLOADS] + GPU_SMALL)
+def test_plan_roots_match_oracle(dk, cfg):
+    rho, consts = dk.plan_rho(*cfg)
+    par = o.Params(*cfg).check()
+    r = o.compute_roots(par)
+    assert rho == r.rho
+    assert consts["zeta"] == r.zeta and consts["omega"] == r.omega and consts["gamma"] == r.gamma
+    assert consts["pz"] == par.pz and consts["P2"] == par.P2 and consts["mu"] == par.mu
+    # limbs: one spare bit above p^z, and room for m-term sums and their REDC
+    L = consts["L"]
+    assert par.pz < 1 << (32 * L - 1)
+    assert par.m * par.pz ** 2 + (1 << (32 * L)) * par.pz < 1 << (64 * L)
+
+
+@pytest.mark.parametrize("bad", [
+    (1 << 16, 512, 16, 16, 12287, 4),     # p not prime
+    (1 << 16, 512, 16, 16, 13, 4),        # 2M does not divide p-1
+    (1 << 16, 512, 16, 16, 12289, 3),     # p^z below the coefficient bound
+    (1 << 16, 500, 16, 16, 12289, 4),     # M not a power of two
+    (1 << 16, 8, 16, 16, 12289, 4),       # M < m
+    (1 << 20, 512, 16, 16, 12289, 4),     # M (m/2) u < N
+    (1 << 16, 512, 16, 0, 12289, 4),      # u = 0
+])
+def test_plan_rejects_invalid_parameters(dk, bad):
+    with pytest.raises(dk.DkssError) as e:
+        dk.plan_rho(*bad)
+    assert e.value.code == 2   # DKSS_EPARAM
+
+
+def test_plan_unsupported_m(dk):
+    # m = 8 is a valid DKSS ring but this build has kernels for m in {16, 32, 64}
+    with pytest.raises(dk.DkssError) as e:
+        dk.plan_rho(1 << 12, 512, 8, 4, 12289, 3)
+    assert e.value.code in (2, 4)
+
+
+def test_int8_form_reports_unsupported(dk):
+    h = ctypes.c_void_p()
+    rc = dk.load().dkss_plan(ctypes.byref(h), 1 << 16, 512, 16, 16, 12289, 4, 2)
+    assert rc == 4 and not h.value

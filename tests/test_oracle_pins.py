@@ -347,3 +347,17 @@ def test_c_oracle_2p24_bits_exact():
     A, B = syn.operand_pair(par.n_bits, syn.config_seed(1))
     c, _ = oc.dkss_mul(A, B, par, r.rho)
     assert syn.to_int(c) == syn.to_int(A) * syn.to_int(B)
+
+
+@pytest.mark.parametrize("cfg", TINY)
+def test_c_oracle_alpha_points_match_full_transform(cfg):
+    """a_hat_{k mu} = sum_j a_j alpha^(k j) because rho^mu = alpha (Section 3.2.3)."""
+    import oracle_c as oc
+    par = o.Params(*cfg).check()
+    rng = random.Random(11)
+    a = rng.getrandbits(par.n_bits)
+    table = o.rho_table(o.compute_roots(par).rho, par)
+    full = o.dkss_fft(o.encode(a, par), table, par)
+    limbs = syn.from_int(a, syn.n_limbs(par.n_bits))
+    for k in range(2 * par.m):
+        assert oc.fft_alpha_point(limbs, par, k) == full[k * par.mu]
