@@ -1,0 +1,348 @@
+#!/usr/bin/env python3
+"""Throughput of the DKSS_MUL hot path on GB300; prints one JSON line.
+
+A step is one full product c = a*b of the 2^24-bit workload (M = 2^15,
+m = 32, u = 32, p = 65537, z = 6): encode, forward transforms of both
+operands, componentwise products, backwards transform, decode and carry scan,
+all in libdkss's CUDA kernels.  Operands are seeded uniform random integers.
+
+value      operand Gbit/s = 2N bits per product / device time per product
+           (CUDA events on the launching stream; L2 flushed between steps
+           by writing a 256 MiB buffer outside the timed events).
+e2e        the same metric through dkss_mul_host (pinned host buffers,
+           host->device copies of a and b and device->host copy of c inside
+           the timed region).
+roofline   the kernel group with the most device time, timed live with the
+           library's per-stage CUDA events over the timed steps.
+cpu_baseline  the CPU oracle (oracle/dkss_oracle.c, single thread) on one full
+           product of the same workload.
+
+--impl reference times that oracle alone on the host cores, same metric.
+With torchrun (N > 1) every rank multiplies its own pair on its own GPU
+(independent replicas; the product itself is not sharded).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+for _p in (ROOT, os.path.join(ROOT, "oracle")):
+    if _p not in sys.path:
+        sys.path.insert(0, _p)
+
+import numpy as np  # noqa: E402
+
+import dkss_synth as syn  # noqa: E402
+
+METRIC = "DKSS_MUL operand Gbit/s and batched products/s on 1 GB300, bit-exact; TC vs IMAD"
+WORKLOAD = "dkss_2p24b"
+L2_FLUSH_BYTES = 256 << 20
+SM_COUNT_GB300 = 152
+IMAD_PER_SM_PER_CLK = 64          # 32-bit integer multiply-add lanes per SM per clock
+SM_MAX_MHZ = 2070.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(syn.WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=30)
+    return ap.parse_args()
+
+
+def workload_config(name):
+    w = syn.WORKLOADS[name]
+    return {"workload": name, "n_bits": w["n_bits"], "M": w["M"], "m": w["m"], "u": w["u"], "p": w["p"],
+            "z": w["z"], "products_per_step": 1}
+
+
+def dist_info():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------- clocks ----
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(prefix="dkss_clocks_", suffix=".csv")
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------ algorithmic counts ----
+
+def rmul_imads(m, L):
+    """32-bit multiply-adds of one R-multiplication, the negacyclic convolution
+    (thesis eq. ncycconv) with one Montgomery reduction per output: m^2 L^2
+    limb products (lo and hi halves) plus m reductions of L(L+1) products."""
+    return 2 * m * m * L * L + m * (2 * L * L + L)
+
+
+def stage_work(info, m):
+    """Per kernel group: (algorithmic 32-bit multiply-adds per step, launches
+    per step).  Twiddles rho^0 = 1 are not work; every other twiddle and every
+    componentwise product is one R-multiplication; the scaling by (2M)^-1 is one
+    Montgomery product per coefficient."""
+    P2, L, col_levels = info["P2"], info["L"], info["levels"] - 1
+    nontrivial = []
+    length = P2
+    for _ in range(col_levels):
+        mu_d = length // (2 * m)
+        nontrivial.append((P2 // length) * (mu_d - 1) * (2 * m - 1))
+        length //= 2 * m
+    r = rmul_imads(m, L)
+    scale = 4 * L * L + 2 * L
+    return {
+        "fwd_first_level": (2 * nontrivial[0] * r, 1),
+        "fwd_level": (2 * sum(nontrivial[1:]) * r, col_levels - 1),
+        "final_pointwise": (P2 * r + P2 * m * scale, 1),
+        "inv_level": (sum(nontrivial) * r, col_levels),
+    }
+
+
+# ----------------------------------------------------------------- ours ----
+
+def check_product(got, A, B):
+    if int(got[0]) != (int(A[0]) * int(B[0])) % (1 << 64):
+        return False
+    ga, ia, ib = syn.to_int(got), syn.to_int(A), syn.to_int(B)
+    for q in ((1 << 61) - 1, (1 << 89) - 1, (1 << 107) - 1):   # Mersenne primes
+        if ga % q != ia * ib % q:
+            return False
+    return True
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1503_04955_gb300 as dk
+    from paper_1503_04955_gb300 import binding
+
+    world, rank, local = dist_info()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg = syn.workload_params(args.workload)
+    n_bits = cfg[0]
+    A, B = syn.operand_pair(n_bits, syn.config_seed(syn.WORKLOADS[args.workload]["index"]), product=rank)
+    plan = dk.Plan(*cfg, flags=binding.FORM_PROFILE)
+    info = plan.info()
+    a = torch.from_numpy(A.view(np.int64)).to(dev)
+    b = torch.from_numpy(B.view(np.int64)).to(dev)
+    out = torch.empty(2 * A.size, dtype=torch.int64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(max(3, args.warmup)):
+        plan.mul(a, b, out)
+    torch.cuda.synchronize(dev)
+    plan.profile_read()
+    plan.sync_status()
+
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local if world > 1 else 0]
+    sampler = ClockSampler(gpu_index) if rank == 0 else None
+    events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    wall0 = time.perf_counter()
+    for e0, e1 in events:
+        flush.fill_(1)                       # evict L2 (untimed: outside the events)
+        e0.record(stream)
+        plan.mul(a, b, out)
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop() if sampler else None
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in events]
+    prof = plan.profile_read()
+    plan.sync_status()
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    bits_per_step = 2 * n_bits * world
+    value = bits_per_step / (ms_per_step * 1e-3) / 1e9
+    ok = check_product(out.cpu().numpy().view(np.uint64), A, B)
+
+    # end to end through dkss_mul_host from pinned host memory
+    a_h = torch.from_numpy(A.view(np.int64)).pin_memory()
+    b_h = torch.from_numpy(B.view(np.int64)).pin_memory()
+    c_h = torch.empty(2 * A.size, dtype=torch.int64).pin_memory()
+    an, bn, cn = (x.numpy().view(np.uint64) for x in (a_h, b_h, c_h))
+    plan.mul_host(an, bn, cn)
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        plan.mul_host(an, bn, cn)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    ok = ok and check_product(cn, A, B)
+    e2e_value = bits_per_step / e2e_s / 1e9
+
+    # roofline of the kernel group with the most device time
+    work = stage_work(info, cfg[2])
+    dom = max((k for k in prof if k in work), key=lambda k: prof[k][0])
+    dom_ms, dom_n = prof[dom]
+    ops_per_step, launches_per_step = work[dom]
+    ops_per_launch = ops_per_step / max(1, launches_per_step)
+    avg_launch_ms = dom_ms / max(1, dom_n)
+    achieved = ops_per_launch / (avg_launch_ms * 1e-3) / 1e12
+    peak = SM_COUNT_GB300 * IMAD_PER_SM_PER_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 3),
+                "unit": "TIMAD/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "avg_launch_ms": round(avg_launch_ms, 4), "ops_per_launch": int(ops_per_launch),
+                "stage_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items()},
+                "peak_basis": "152 SMs x 64 IMAD/clk x 2070 MHz (recipe unit counts and max clock)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.workload, A, B)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 4), "unit": "Gbit/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(ms_per_step, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic: SplitMix64 uniform operands in [0, 2^N)",
+            "config": dict(workload_config(args.workload), form="imad",
+                           l2="flushed between steps (256 MiB write outside the timed events)",
+                           parallelism="replicas" if world > 1 else "single GPU"),
+            "products_per_s": round(world / (ms_per_step * 1e-3), 3),
+            "bit_exact": bool(ok),
+            "gpu_launches": plan.launches * args.steps,
+            "e2e": {"value": round(e2e_value, 4), "unit": "Gbit/s", "h2d_bytes_per_step": 2 * A.nbytes,
+                    "d2h_bytes_per_step": 4 * A.nbytes},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "wall_s": round(wall, 3),
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------- reference ----
+
+def oracle_product_seconds(name, A, B):
+    import dkss_oracle
+    import oracle_c
+    cfg = syn.workload_params(name)
+    par = dkss_oracle.Params(*cfg).check()
+    rho = dkss_oracle.compute_roots(par).rho
+    oracle_c.load()
+    t0 = time.perf_counter()
+    c, _ = oracle_c.dkss_mul(A, B, par, rho)
+    dt = time.perf_counter() - t0
+    return dt, c
+
+
+def cpu_baseline(name, A, B):
+    dt, c = oracle_product_seconds(name, A, B)
+    ok = syn.to_int(c[:4]) == (syn.to_int(A[:2]) * syn.to_int(B[:2])) % (1 << 256)
+    n_bits = syn.WORKLOADS[name]["n_bits"]
+    return {"value": round(2 * n_bits / dt / 1e9, 6), "unit": "Gbit/s", "cores": 1, "kind": "oracle",
+            "sample": "one full %s product (C oracle, single thread, %.2f s)" % (name, dt),
+            "low_words_ok": bool(ok)}
+
+
+def run_reference(args):
+    world, rank, _ = dist_info()
+    if rank != 0:
+        return
+    name = args.workload
+    n_bits = syn.WORKLOADS[name]["n_bits"]
+    A, B = syn.operand_pair(n_bits, syn.config_seed(syn.WORKLOADS[name]["index"]))
+    small = syn.workload_params("dkss_65536b")
+    Aw, Bw = syn.operand_pair(small[0], 7)
+    for _ in range(max(3, args.warmup)):      # warm-up on the small workload (bounded)
+        oracle_product_seconds("dkss_65536b", Aw, Bw)
+    budget_s = 150.0
+    times = []
+    while len(times) < args.steps:
+        dt, _ = oracle_product_seconds(name, A, B)
+        times.append(dt)
+        if sum(times) + dt > budget_s:
+            break
+    mean = sum(times) / len(times)
+    value = 2 * n_bits / mean / 1e9
+    sample = "%d full %s product(s) by the C oracle, single thread (of %d steps requested; capped at %.0f s)" % (
+        len(times), name, args.steps, budget_s)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "Gbit/s", "n_gpus": world,
+        "steps": len(times), "warmup": max(3, args.warmup), "ms_per_step": round(mean * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u128",
+        "data": "synthetic: SplitMix64 uniform operands in [0, 2^N)",
+        "config": dict(workload_config(name), form="cpu oracle"),
+        "cpu_baseline": {"value": round(value, 6), "unit": "Gbit/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 6), "unit": "Gbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

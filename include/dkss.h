@@ -50,7 +50,7 @@ typedef enum {
 enum {
     DKSS_FORM_IMAD = 1,    /* R-multiplications on the integer pipe (default) */
     DKSS_FORM_INT8TC = 2,  /* R-multiplications as exact INT8 tensor-core MMAs */
-    DKSS_PROFILE = 4,      /* reserved: per-stage CUDA-event timing */
+    DKSS_PROFILE = 4,      /* per-stage CUDA-event timing, read with dkss_profile_read */
     DKSS_DEBUG_CHECKS = 8  /* reserved: extra device-side range checks */
 };
 
@@ -113,9 +113,9 @@ typedef struct {
 } dkss_job;
 
 /*
- * Multiply `count` independent pairs of any sizes (BASELINE batched workload,
- * thesis Section 3.2 applied per job).  Reserved: returns DKSS_EUNSUPPORTED in
- * this build.
+ * Multiply `count` independent pairs of any sizes in one call (thesis
+ * Section 3.2 applied per job).  Reserved: returns DKSS_EUNSUPPORTED in this
+ * build.
  */
 dkss_status dkss_mul_batch(const dkss_job* jobs, size_t count, uint32_t flags, dkss_stream_t stream);
 
@@ -134,6 +134,18 @@ dkss_status dkss_plan_info(dkss_plan_t plan, uint64_t* consts, size_t n_consts, 
  */
 dkss_status dkss_plan_rho(uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, uint64_t p, uint32_t z,
                           uint64_t* rho_out, uint64_t* consts, size_t n_consts);
+
+/*
+ * Per-stage device times of the plan's calls since the last read (needs
+ * DKSS_PROFILE at dkss_plan; CUDA events recorded on the caller's stream around
+ * each kernel group).  Waits for those events.  Index k of ms (milliseconds
+ * summed) and counts (groups timed): 0 first forward level (with encoding),
+ * 1 later forward levels, 2 last forward level + componentwise products +
+ * first backwards level, 3 backwards levels, 4 decoding and carry scan.
+ * Either array may be NULL; n is their length (at most 8 used).  Resets the
+ * sums.  Errors: DKSS_EINVAL, DKSS_ECUDA.
+ */
+dkss_status dkss_profile_read(dkss_plan_t plan, double* ms, uint64_t* counts, size_t n);
 
 /* Kernel launches one dkss_mul call queues (for launch accounting). */
 uint32_t dkss_plan_launches(dkss_plan_t plan);

@@ -22,7 +22,10 @@ FORM_INT8TC = 2
 
 # Names exported by libdkss.so (include/dkss.h)
 EXPORTS = ["dkss_plan", "dkss_mul", "dkss_mul_host", "dkss_forward", "dkss_mul_batch", "dkss_plan_info",
-           "dkss_plan_rho", "dkss_plan_launches", "dkss_sync_status", "dkss_plan_destroy", "dkss_status_str"]
+           "dkss_plan_rho", "dkss_profile_read", "dkss_plan_launches", "dkss_sync_status", "dkss_plan_destroy",
+           "dkss_status_str"]
+FORM_PROFILE = 4
+PROFILE_KINDS = ["fwd_first_level", "fwd_level", "final_pointwise", "inv_level", "decode"]
 
 
 class DkssError(RuntimeError):
@@ -55,6 +58,7 @@ def load():
     lib.dkss_mul_batch.argtypes = [P, sz, u32, P]
     lib.dkss_plan_info.argtypes = [P, P, sz, P]
     lib.dkss_plan_rho.argtypes = [u64, u64, u32, u32, u64, u32, P, P, sz]
+    lib.dkss_profile_read.argtypes = [P, P, P, sz]
     lib.dkss_plan_launches.argtypes = [P]
     lib.dkss_plan_launches.restype = u32
     lib.dkss_sync_status.argtypes = [P, P]
@@ -62,7 +66,7 @@ def load():
     lib.dkss_status_str.argtypes = [ctypes.c_int]
     lib.dkss_status_str.restype = ctypes.c_char_p
     for name in ("dkss_plan", "dkss_mul", "dkss_mul_host", "dkss_forward", "dkss_mul_batch",
-                 "dkss_plan_info", "dkss_plan_rho", "dkss_sync_status", "dkss_plan_destroy"):
+                 "dkss_plan_info", "dkss_plan_rho", "dkss_profile_read", "dkss_sync_status", "dkss_plan_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -183,6 +187,13 @@ class Plan:
         out = torch.empty((2 * self.M, self.m, 2), dtype=torch.int64, device=a.device)
         _check(load().dkss_forward(self._h, a.data_ptr(), out.data_ptr(), _stream_handle(stream)), "dkss_forward")
         return out
+
+    def profile_read(self):
+        """{kind: (total ms, groups timed)} since the last read (plan built with FORM_PROFILE)."""
+        ms = np.zeros(8, dtype=np.float64)
+        cnt = np.zeros(8, dtype=np.uint64)
+        _check(load().dkss_profile_read(self._h, ms.ctypes.data, cnt.ctypes.data, 8), "dkss_profile_read")
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(PROFILE_KINDS)}
 
     def sync_status(self, stream=None):
         _check(load().dkss_sync_status(self._h, _stream_handle(stream)), "device status")

@@ -339,9 +339,34 @@ dkss_status dkss_sync_status(dkss_plan_t pl, dkss_stream_t stream) {
     return DKSS_OK;
 }
 
+dkss_status dkss_profile_read(dkss_plan_t pl, double* ms, uint64_t* counts, size_t n) {
+    if (!pl) return DKSS_EINVAL;
+    dkss_status status = DKSS_OK;
+    for (auto& r : pl->prof) {
+        float t = 0.f;
+        if (cudaEventSynchronize(r.stop) != cudaSuccess || cudaEventElapsedTime(&t, r.start, r.stop) != cudaSuccess)
+            status = DKSS_ECUDA;
+        if (r.kind >= 0 && r.kind < 8) {
+            pl->prof_ms[r.kind] += t;
+            pl->prof_count[r.kind] += 1;
+        }
+        cudaEventDestroy(r.start);
+        cudaEventDestroy(r.stop);
+    }
+    pl->prof.clear();
+    for (size_t i = 0; i < n && i < 8; ++i) {
+        if (ms) ms[i] = pl->prof_ms[i];
+        if (counts) counts[i] = pl->prof_count[i];
+        pl->prof_ms[i] = 0;
+        pl->prof_count[i] = 0;
+    }
+    return status;
+}
+
 dkss_status dkss_plan_destroy(dkss_plan_t pl) {
     if (!pl) return DKSS_OK;
     cudaDeviceSynchronize();
+    dkss_profile_read(pl, nullptr, nullptr, 0);
     free_device(pl);
     delete pl;
     return DKSS_OK;

@@ -114,6 +114,7 @@ static dkss_status launch_forward_levels(dkss_plan_s* pl, LevelParams lp, int op
     for (uint32_t d = 0; d < pl->col_levels; ++d) {
         lp.len = len;
         lp.bp = bp;
+        ProfScope ps(pl, st, d == 0 ? kProfFwdFirst : kProfFwdLevel);
         if (d == 0) k_fwd_level<m, L, true><<<grid, kThreads, smem, st>>>(lp, md);
         else k_fwd_level<m, L, false><<<grid, kThreads, smem, st>>>(lp, md);
         DKSS_CHECK_LAUNCH();
@@ -133,9 +134,13 @@ dkss_status run_mul(dkss_plan_s* pl, const uint64_t* a, const uint64_t* b, uint6
     dkss_status s = launch_forward_levels<m, L>(pl, lp, 2, st);
     if (s != DKSS_OK) return s;
     lp.len = pl->r_last;
+    {
+    ProfScope ps(pl, st, kProfFinal);
     k_final_pointwise<m, L><<<(unsigned)(pl->P2 / pl->r_last), kThreads, final_smem_bytes<m, L>((int)pl->r_last), st>>>(lp, md);
     DKSS_CHECK_LAUNCH();
+    }
     for (int d = (int)pl->col_levels - 1; d >= 0; --d) {
+        ProfScope ps(pl, st, kProfInvLevel);
         uint64_t bp = 1;
         for (int i = 0; i < d; ++i) bp *= G::TWO_M;
         lp.len = pl->P2 / bp;
@@ -159,6 +164,7 @@ dkss_status run_mul(dkss_plan_s* pl, const uint64_t* a, const uint64_t* b, uint6
     for (dkss_host::u128 t = pl->q; t; t >>= 1) dp.db++;
     dp.db += 1;
     dp.out_aligned16 = ((uintptr_t)out & 15) == 0;
+    ProfScope ps(pl, st, kProfDecode);
     k_decode_tiles<L><<<(unsigned)pl->n_tiles, kDecThreads, 0, st>>>(dp);
     DKSS_CHECK_LAUNCH();
     k_decode_scan<<<1, kScanThreads, 0, st>>>(dp);

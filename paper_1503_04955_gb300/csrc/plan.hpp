@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 #include "../../include/dkss.h"
 #include "host_math.hpp"
@@ -31,7 +32,41 @@ struct dkss_plan_s {
     uint32_t* d_status = nullptr;
     uint64_t* d_stage = nullptr;  // dkss_mul_host staging: a, b, out
     uint32_t launches = 0;
+    // DKSS_PROFILE: CUDA events around each kernel group, summed by kind on read
+    struct ProfRec {
+        cudaEvent_t start, stop;
+        int kind;
+    };
+    std::vector<ProfRec> prof;
+    double prof_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    uint64_t prof_count[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
+
+namespace dkss {
+// Kernel-group kinds reported by dkss_profile_read.
+enum ProfKind { kProfFwdFirst = 0, kProfFwdLevel = 1, kProfFinal = 2, kProfInvLevel = 3, kProfDecode = 4 };
+
+// Record an event pair around a kernel group when the plan profiles.
+struct ProfScope {
+    dkss_plan_s* pl;
+    cudaStream_t st;
+    int kind;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ProfScope(dkss_plan_s* p, cudaStream_t s, int k) : pl(p), st(s), kind(k) {
+        if (!(pl->flags & DKSS_PROFILE) || pl->prof.size() >= 65536) return;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+            e0 = e1 = nullptr;
+            return;
+        }
+        cudaEventRecord(e0, st);
+    }
+    ~ProfScope() {
+        if (!e0) return;
+        cudaEventRecord(e1, st);
+        pl->prof.push_back({e0, e1, kind});
+    }
+};
+}  // namespace dkss
 
 namespace dkss {
 // Per-(m, L) launchers, explicitly instantiated in inst_m<m>_L<L>.cu.
