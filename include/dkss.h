@@ -122,8 +122,9 @@ dkss_status dkss_mul_batch(const dkss_job* jobs, size_t count, uint32_t flags, d
 /*
  * Host view of a plan's parameters (no device work).  rho_out (may be NULL)
  * receives rho's m coefficients as 2 words each; consts receives, in order:
- * 2M, 2M/2m, L (32-bit limbs per residue), transform levels, p^z low word,
- * p^z high word, generator zeta, omega low, omega high, gamma low, gamma high.
+ * 2M, 2M/2m, L (32-bit limbs per stored residue), transform levels, p^z low
+ * word, p^z high word, generator zeta, omega low, omega high, gamma low,
+ * gamma high, LR (26-bit limbs of the product arithmetic).
  */
 dkss_status dkss_plan_info(dkss_plan_t plan, uint64_t* consts, size_t n_consts, uint64_t* rho_out);
 

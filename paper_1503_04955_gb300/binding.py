@@ -91,8 +91,9 @@ def _words2_to_ints(arr):
     return [int(lo) | (int(hi) << 64) for lo, hi in zip(arr[0::2], arr[1::2])]
 
 
-N_CONSTS = 11
-CONST_NAMES = ["P2", "mu", "L", "levels", "pz_lo", "pz_hi", "zeta", "omega_lo", "omega_hi", "gamma_lo", "gamma_hi"]
+N_CONSTS = 12
+CONST_NAMES = ["P2", "mu", "L", "levels", "pz_lo", "pz_hi", "zeta", "omega_lo", "omega_hi", "gamma_lo", "gamma_hi",
+               "LR"]
 
 
 def _consts_dict(c):

@@ -2,7 +2,7 @@
 
 Translation units: the C ABI (capi.cu), the host number theory
 (host_math.cpp) and one instantiation of the stage kernels per supported
-(m, L) pair (inst.cu compiled with -DDKSS_INST_M/-DDKSS_INST_L), compiled in
+(m, L, LR) triple (inst.cu compiled with -DDKSS_INST_M/_L/_LR), compiled in
 parallel and linked into paper_1503_04955_gb300/_build/libdkss.so.
 """
 import concurrent.futures as cf
@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB_NAME = "libdkss.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-PAIRS = [(m, L) for m in (16, 32, 64) for L in (2, 3, 4)]
+# (m, L, LR): ring degree, 32-bit limbs of stored residues, 26-bit limbs of products
+TRIPLES = [(m, L, LR) for m in (16, 32, 64) for (L, LR) in ((2, 2), (2, 3), (3, 3), (3, 4), (4, 4), (4, 5))]
 
 
 def nvcc():
@@ -36,9 +37,9 @@ def _flags(extra_ptxas=False):
 def _units():
     units = [("capi.o", os.path.join(CSRC, "capi.cu"), []),
              ("host_math.o", os.path.join(CSRC, "host_math.cpp"), ["-x", "cu"])]
-    for m, L in PAIRS:
-        units.append(("inst_m%d_L%d.o" % (m, L), os.path.join(CSRC, "inst.cu"),
-                      ["-DDKSS_INST_M=%d" % m, "-DDKSS_INST_L=%d" % L]))
+    for m, L, LR in TRIPLES:
+        units.append(("inst_m%d_L%d_R%d.o" % (m, L, LR), os.path.join(CSRC, "inst.cu"),
+                      ["-DDKSS_INST_M=%d" % m, "-DDKSS_INST_L=%d" % L, "-DDKSS_INST_LR=%d" % LR]))
     return units
 
 

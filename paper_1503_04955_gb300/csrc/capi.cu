@@ -29,6 +29,16 @@ int bitlen(u128 x) {
     return n;
 }
 
+// 2^bits mod q by doubling (bits may exceed 128)
+u128 pow2_mod(int bits, u128 q) {
+    u128 r = 1 % q;
+    for (int i = 0; i < bits; ++i) {
+        r <<= 1;            // r < q < 2^126: no overflow
+        if (r >= q) r -= q;
+    }
+    return r;
+}
+
 // x < 2^bits for a 256-bit value held as 5 little-endian words
 bool below_pow2(const uint64_t t[5], int bits) {
     for (int w = 4; w >= 0; --w) {
@@ -50,17 +60,18 @@ struct Kernels {
     prep_fn prep;
 };
 
-template <int m, int L>
+template <int m, int L, int LR>
 Kernels kernels_for() {
-    return Kernels{&dkss::run_mul<m, L>, &dkss::run_forward<m, L>, &dkss::prepare<m, L>};
+    return Kernels{&dkss::run_mul<m, L, LR>, &dkss::run_forward<m, L, LR>, &dkss::prepare<m, L, LR>};
 }
 
-bool lookup(uint32_t m, uint32_t L, Kernels* k) {
-#define DKSS_CASE(M_, L_) \
-    if (m == M_ && L == L_) { *k = kernels_for<M_, L_>(); return true; }
-    DKSS_CASE(16, 2) DKSS_CASE(16, 3) DKSS_CASE(16, 4)
-    DKSS_CASE(32, 2) DKSS_CASE(32, 3) DKSS_CASE(32, 4)
-    DKSS_CASE(64, 2) DKSS_CASE(64, 3) DKSS_CASE(64, 4)
+bool lookup(uint32_t m, uint32_t L, uint32_t LR, Kernels* k) {
+#define DKSS_CASE(M_, L_, LR_) \
+    if (m == M_ && L == L_ && LR == LR_) { *k = kernels_for<M_, L_, LR_>(); return true; }
+#define DKSS_CASES(M_) \
+    DKSS_CASE(M_, 2, 2) DKSS_CASE(M_, 2, 3) DKSS_CASE(M_, 3, 3) DKSS_CASE(M_, 3, 4) DKSS_CASE(M_, 4, 4) DKSS_CASE(M_, 4, 5)
+    DKSS_CASES(16) DKSS_CASES(32) DKSS_CASES(64)
+#undef DKSS_CASES
 #undef DKSS_CASE
     return false;
 }
@@ -125,6 +136,17 @@ dkss_status plan_host(dkss_plan_s* pl, uint64_t n_bits, uint64_t M, uint32_t m, 
     }
     const int RB = 32 * (int)L;
     pl->nsub = (uint32_t)(RB >= 128 ? 0 : (uint64_t)(((u128)m * q) >> RB)) + 1;
+    // products in 26-bit limbs: m q < R' = 2^(26 LR) keeps every REDC output below 2q
+    uint32_t LR = 2;
+    while (LR <= 5 && (26 * LR < 127 && (((u128)m * q) >> (26 * LR)) != 0)) ++LR;
+    if (LR > 5 || LR < L || LR > L + 1) return DKSS_EUNSUPPORTED;
+    pl->LR = LR;
+    for (uint32_t i = 0; i < 5; ++i) pl->q_rr[i] = i < LR ? (uint32_t)(q >> (26 * i)) & ((1u << 26) - 1) : 0;
+    {
+        uint32_t q0 = (uint32_t)q, inv = q0;
+        for (int i = 0; i < 5; ++i) inv *= 2 - q0 * inv;
+        pl->nprime26 = (0u - inv) & ((1u << 26) - 1);
+    }
 
     // roots (Section 3.2.3)
     MontCtx c(q);
@@ -146,25 +168,25 @@ dkss_status plan_host(dkss_plan_s* pl, uint64_t n_bits, uint64_t M, uint32_t m, 
     }
     r.rho.resize(m);
     for (uint32_t i = 0; i < m; ++i) r.rho[i] = c.from(rho_m[i]);
-    // (2M)^-1 * R_dev^2 mod q, the scaling factor used through one Montgomery product
-    u128 rdev = RB >= 128 ? c.r1 : (((u128)1 << RB) % q);
+    // (2M)^-1 R'^2 mod q, the scaling factor applied through one Montgomery product
+    const int RRB = 26 * (int)LR;
+    u128 rdev = pow2_mod(RRB, q);
     u128 p2inv = c.pow(c.to(P2 % q), phi - 1);          // Montgomery form
     u128 rdev_m = c.to(rdev);
     u128 ks = c.from(c.mul(c.mul(p2inv, rdev_m), rdev_m));
-    for (uint32_t i = 0; i < 4; ++i) pl->kscale[i] = i < L ? (uint32_t)(ks >> (32 * i)) : 0;
+    for (uint32_t i = 0; i < 5; ++i) pl->kscale[i] = i < LR ? (uint32_t)(ks >> (26 * i)) & ((1u << 26) - 1) : 0;
     return DKSS_OK;
 }
 
-// rho^s for s < mu_top in device Montgomery form (R = 2^(32L)), m residues of L words each.
+// rho^s R' mod q for s < mu_top (R' = 2^(26 LR)), m residues of LR 26-bit limbs each.
 void build_table(const dkss_plan_s* pl, std::vector<uint32_t>& out) {
-    const uint32_t m = pl->m, L = pl->L;
+    const uint32_t m = pl->m, L = pl->LR;
     const uint64_t mu = pl->mu_top;
     out.assign(mu * m * L, 0);
     MontCtx c(pl->q);
     Relem rho_m(m);
     for (uint32_t i = 0; i < m; ++i) rho_m[i] = c.to(pl->roots.rho[i]);
-    const int RB = 32 * (int)L;
-    u128 rdev = RB >= 128 ? c.r1 : (((u128)1 << RB) % pl->q);
+    u128 rdev = pow2_mod(26 * (int)L, pl->q);
     unsigned hw = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
     uint64_t chunks = std::min<uint64_t>(hw, mu);
     std::vector<std::thread> th;
@@ -174,8 +196,9 @@ void build_table(const dkss_plan_s* pl, std::vector<uint32_t>& out) {
             Relem cur = dkss_host::r_pow(c, rho_m, s0);
             for (uint64_t s = s0; s < s1; ++s) {
                 for (uint32_t t = 0; t < m; ++t) {
-                    u128 v = c.mul(cur[t], rdev);   // rho^s_t * R_dev mod q
-                    for (uint32_t w = 0; w < L; ++w) out[(s * m + t) * L + w] = (uint32_t)(v >> (32 * w));
+                    u128 v = c.mul(cur[t], rdev);   // rho^s_t * R' mod q
+                    for (uint32_t w = 0; w < L; ++w)
+                        out[(s * m + t) * L + w] = (uint32_t)(v >> (26 * w)) & ((1u << 26) - 1);
                 }
                 if (s + 1 < s1) cur = dkss_host::r_mul(c, cur, rho_m);
             }
@@ -199,11 +222,11 @@ bool overlap(const void* a, size_t an, const void* b, size_t bn) {
 }
 
 void fill_consts(const dkss_plan_s* pl, uint64_t* consts, size_t n) {
-    uint64_t v[11] = {pl->P2, pl->mu_top, pl->L, (uint64_t)pl->col_levels + 1, (uint64_t)pl->q,
+    uint64_t v[12] = {pl->P2, pl->mu_top, pl->L, (uint64_t)pl->col_levels + 1, (uint64_t)pl->q,
                       (uint64_t)(pl->q >> 64), pl->roots.zeta, (uint64_t)pl->roots.omega,
                       (uint64_t)(pl->roots.omega >> 64), (uint64_t)pl->roots.gamma,
-                      (uint64_t)(pl->roots.gamma >> 64)};
-    for (size_t i = 0; i < n && i < 11; ++i) consts[i] = v[i];
+                      (uint64_t)(pl->roots.gamma >> 64), pl->LR};
+    for (size_t i = 0; i < n && i < 12; ++i) consts[i] = v[i];
 }
 
 }  // namespace
@@ -220,7 +243,7 @@ dkss_status dkss_plan(dkss_plan_t* plan, uint64_t n_bits, uint64_t M, uint32_t m
     pl->flags = flags;
     dkss_status s = plan_host(pl, n_bits, M, m, u, p, z);
     Kernels k;
-    if (s == DKSS_OK && !lookup(pl->m, pl->L, &k)) s = DKSS_EUNSUPPORTED;
+    if (s == DKSS_OK && !lookup(pl->m, pl->L, pl->LR, &k)) s = DKSS_EUNSUPPORTED;
     if (s != DKSS_OK) {
         delete pl;
         return s;
@@ -267,7 +290,7 @@ dkss_status dkss_mul(dkss_plan_t pl, const uint64_t* a, const uint64_t* b, uint6
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != pl->device) return DKSS_EINVAL;
     Kernels k;
-    if (!lookup(pl->m, pl->L, &k)) return DKSS_EUNSUPPORTED;
+    if (!lookup(pl->m, pl->L, pl->LR, &k)) return DKSS_EUNSUPPORTED;
     return k.mul(pl, a, b, out, (cudaStream_t)stream);
 }
 
@@ -298,7 +321,7 @@ dkss_status dkss_mul_host(dkss_plan_t pl, const uint64_t* a_host, const uint64_t
 dkss_status dkss_forward(dkss_plan_t pl, const uint64_t* a, uint64_t* out, dkss_stream_t stream) {
     if (!pl || !a || !out) return DKSS_EINVAL;
     Kernels k;
-    if (!lookup(pl->m, pl->L, &k)) return DKSS_EUNSUPPORTED;
+    if (!lookup(pl->m, pl->L, pl->LR, &k)) return DKSS_EUNSUPPORTED;
     return k.fwd(pl, a, out, (cudaStream_t)stream);
 }
 

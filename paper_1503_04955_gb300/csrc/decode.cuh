@@ -125,21 +125,10 @@ __device__ GP gp_block_scan(GP x, GP& total) {
     return gp_combine(wpre, excl_in_warp);
 }
 
-template <int L>
-__global__ void __launch_bounds__(kDecThreads) k_decode_tiles(DecodeParams p) {
-    const uint64_t j0 = (uint64_t)blockIdx.x * kDecTile + (uint64_t)threadIdx.x * kDecWPT;
-    uint64_t S_prev = j0 >= 1 && j0 - 1 < p.n_windows ? window_sum<L>(p, j0 - 1) : 0;
-    uint32_t wv[kDecWPT], gbit = 0, pbit = 0;
-#pragma unroll
-    for (int w = 0; w < kDecWPT; ++w) {
-        uint64_t j = j0 + w;
-        uint64_t S = j < p.n_windows ? window_sum<L>(p, j) : 0;
-        uint64_t T = (S & 0xffffffffull) + (S_prev >> 32);
-        wv[w] = (uint32_t)T;
-        gbit |= (uint32_t)(T >> 32) << w;
-        pbit |= (uint32_t)(wv[w] == 0xffffffffu) << w;
-        S_prev = S;
-    }
+// Carry resolution inside a tile and the tile aggregate: wv are the thread's
+// window values, gbit/pbit its generate/propagate bits (bit w = window j0+w).
+__device__ __forceinline__ void decode_tile_finish(const DecodeParams& p, uint64_t j0, const uint32_t (&wv)[kDecWPT],
+                                                   uint32_t gbit, uint32_t pbit) {
     // thread aggregate: carry out with carry-in 0, and whether a carry-in passes through
     uint32_t c = 0;
 #pragma unroll
@@ -163,6 +152,98 @@ __global__ void __launch_bounds__(kDecThreads) k_decode_tiles(DecodeParams p) {
             if (j0 + w < p.n_windows) p.out[j0 + w] = o[w];
     }
     if (threadIdx.x == 0) p.agg[blockIdx.x] = total.g | (total.p << 1);
+}
+
+template <int L>
+__global__ void __launch_bounds__(kDecThreads) k_decode_tiles(DecodeParams p) {
+    const uint64_t j0 = (uint64_t)blockIdx.x * kDecTile + (uint64_t)threadIdx.x * kDecWPT;
+    uint64_t S_prev = j0 >= 1 && j0 - 1 < p.n_windows ? window_sum<L>(p, j0 - 1) : 0;
+    uint32_t wv[kDecWPT], gbit = 0, pbit = 0;
+#pragma unroll
+    for (int w = 0; w < kDecWPT; ++w) {
+        uint64_t j = j0 + w;
+        uint64_t S = j < p.n_windows ? window_sum<L>(p, j) : 0;
+        uint64_t T = (S & 0xffffffffull) + (S_prev >> 32);
+        wv[w] = (uint32_t)T;
+        gbit |= (uint32_t)(T >> 32) << w;
+        pbit |= (uint32_t)(wv[w] == 0xffffffffu) << w;
+        S_prev = S;
+    }
+    decode_tile_finish(p, j0, wv, gbit, pbit);
+}
+
+// Same tile kernel for u = 32/R (R = 1, 2): digit k sits at bit u*k, so window
+// j takes limb t of the digits k = R(j - t) + s, shifted by u*s bits.  A thread
+// loads each digit its 9 windows (j0-1 .. j0+7) touch once into registers.
+template <int L, int R>
+__global__ void __launch_bounds__(kDecThreads) k_decode_tiles_aligned(DecodeParams p) {
+    constexpr int U = 32 / R;
+    constexpr int T = L + 2;                 // limbs a shifted digit can reach
+    constexpr int NW = kDecWPT + 1;          // windows j0-1 .. j0+7
+    constexpr int NK = R * (NW + T - 1);     // digits touching them
+    const int64_t j0 = (int64_t)blockIdx.x * kDecTile + (int64_t)threadIdx.x * kDecWPT;
+    const int64_t jb = j0 - 1;
+    const int64_t base_k = (int64_t)R * (jb - T + 1);
+    const uint32_t hshift = 31 - __clz(p.h);
+    uint32_t D[NK][L + 1];
+#pragma unroll
+    for (int n = 0; n < NK; ++n) {
+        const int64_t k = base_k + n;
+#pragma unroll
+        for (int w = 0; w <= L; ++w) D[n][w] = 0;
+        if (k < 0 || (uint64_t)k >= p.k_max) continue;
+        const uint64_t i = (uint64_t)k >> hshift;
+        const uint32_t t = (uint32_t)k & (p.h - 1);
+        if (i < p.P2) {
+            const uint32_t* s = p.c + (i * p.m + t) * L;
+#pragma unroll
+            for (int w = 0; w < L; ++w) D[n][w] = s[w];
+        }
+        if (i >= 1 && i - 1 < p.P2) {
+            const uint32_t* s = p.c + ((i - 1) * p.m + t + p.h) * L;
+            uint32_t carry = 0;
+#pragma unroll
+            for (int w = 0; w < L; ++w) {
+                uint64_t x = (uint64_t)D[n][w] + s[w] + carry;
+                D[n][w] = (uint32_t)x;
+                carry = (uint32_t)(x >> 32);
+            }
+            D[n][L] += carry;
+        }
+    }
+    uint64_t S[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        uint64_t acc = 0;
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+#pragma unroll
+            for (int s = 0; s < R; ++s) {
+                const int n = R * (w - t + T - 1) + s;
+                const int sh = 32 * t - U * s;   // bit of the digit at the window start
+                uint32_t piece;
+                if (sh < 0) {
+                    piece = D[n][0] << (-sh);
+                } else {
+                    const int lw = sh >> 5, bs = sh & 31;
+                    const uint32_t a = lw <= L ? D[n][lw] : 0u;
+                    const uint32_t b = lw + 1 <= L ? D[n][lw + 1] : 0u;
+                    piece = bs ? ((a >> bs) | (b << (32 - bs))) : a;
+                }
+                acc += piece;
+            }
+        }
+        S[w] = (jb + w >= 0 && (uint64_t)(jb + w) < p.n_windows) ? acc : 0;
+    }
+    uint32_t wv[kDecWPT], gbit = 0, pbit = 0;
+#pragma unroll
+    for (int w = 0; w < kDecWPT; ++w) {
+        uint64_t T2 = (S[w + 1] & 0xffffffffull) + (S[w] >> 32);
+        wv[w] = (uint32_t)T2;
+        gbit |= (uint32_t)(T2 >> 32) << w;
+        pbit |= (uint32_t)(wv[w] == 0xffffffffu) << w;
+    }
+    decode_tile_finish(p, (uint64_t)j0, wv, gbit, pbit);
 }
 
 // One CTA: exclusive scan of the tile aggregates into per-tile carry-ins.

@@ -18,6 +18,7 @@
 #include <cstdint>
 
 #include "arith.cuh"
+#include "rr_arith.cuh"
 
 namespace dkss {
 
@@ -32,14 +33,20 @@ struct Geo {
     static constexpr int TEAMS_PER_WARP = 32 / TEAM;
     static constexpr int NTEAMS = kWarps * TEAMS_PER_WARP;
     static constexpr int CPL = m / TEAM;                 // coefficients per lane
-    static constexpr int STAGE_W = TWO_M * L;            // words of one extended twiddle
+};
+
+// Per-team shared buffers of an R-multiplication in 26-bit limbs: the first
+// factor x (m residues) and the extended second factor E (2m residues).
+template <int m, int LR>
+struct TeamBuf {
+    static constexpr int WORDS = 3 * m * LR;
 };
 
 struct LevelParams {
     uint32_t* data;            // one or two polynomials (operand b at data + poly_words)
     const uint64_t* raw_a;     // encode source of operand a (first forward level)
     const uint64_t* raw_b;
-    const uint32_t* table;     // rho^s, s < mu_top, Montgomery form, m residues each
+    const uint32_t* table;     // rho^s R' mod p^z, s < mu_top: m residues of LR 26-bit limbs each
     uint64_t poly_words;
     uint64_t P2;               // 2M
     uint64_t mu_top;           // 2M / 2m
@@ -50,7 +57,7 @@ struct LevelParams {
     uint64_t raw_words;
     uint32_t u;
     uint32_t log2_mu_top;
-    uint32_t kscale[4];        // (2M)^-1 * R^2 mod p^z: Montgomery factor of the scaling
+    uint32_t kscale[5];        // (2M)^-1 R'^2 mod p^z in 26-bit limbs, R' = 2^(26 LR)
 };
 
 __device__ __forceinline__ uint32_t bitrev(uint32_t x, int bits) { return __brev(x) >> (32 - bits); }
@@ -205,61 +212,91 @@ __device__ void dft_dif(uint32_t* s, int n, int root, const Mod<L>& md) {
     }
 }
 
-// Stage the extended operand E of a negacyclic product into the team buffer:
-// E[t] = y_t, E[t+m] = -y_t, so that (x*y)_k = sum_i x_i E[(k - i) mod 2m].
-template <int m, int L>
-__device__ __forceinline__ void stage_ext(uint32_t* E, const uint32_t* y, const Mod<L>& md, int lane) {
-    using G = Geo<m, L>;
+// Negacyclic product in R (Section 2.9.2, eq. ncycconv) times alpha^r, in
+// 26-bit limbs: out_k = REDC(sum_i x_i E[(k - r - i) mod 2m]) where
+// E[t] = y_t and E[t+m] = -y_t, so that the wrapped terms carry their minus
+// sign.  X and E are the team's shared buffers; results stay in registers.
+template <int m, int LR>
+__device__ __forceinline__ void negacyclic_mul_rr(uint32_t (&out)[Geo<m, 1>::CPL][LR], const uint32_t* X,
+                                                  const uint32_t* E, int r, const ModRR<LR>& md, int lane) {
+    constexpr int CPL = Geo<m, 1>::CPL, TEAM = Geo<m, 1>::TEAM;
+    uint64_t col[CPL][2 * LR];
 #pragma unroll
-    for (int c = 0; c < G::CPL; ++c) {
-        int t = lane + c * G::TEAM;
-        uint32_t v[L], nv[L];
-        ld_res<L>(v, y + t * L);
-        neg_mod<L>(nv, v, md);
-        st_res<L>(E + t * L, v);
-        st_res<L>(E + (t + m) * L, nv);
-    }
-}
-
-// Negacyclic product in R by the plain convolution (Section 2.9.2, eq.
-// ncycconv), times alpha^r: out_k = REDC(sum_i x_i E[(k - r - i) mod 2m]).
-// x lives in shared memory (broadcast reads), E is the staged extended
-// operand.  Results stay in registers.
-template <int m, int L>
-__device__ __forceinline__ void negacyclic_mul(uint32_t (&out)[Geo<m, L>::CPL][L], const uint32_t* x, const uint32_t* E,
-                                               int r, const Mod<L>& md, int lane) {
-    using G = Geo<m, L>;
-    uint32_t acc[G::CPL][2 * L];
+    for (int c = 0; c < CPL; ++c)
 #pragma unroll
-    for (int c = 0; c < G::CPL; ++c)
-#pragma unroll
-        for (int i = 0; i < 2 * L; ++i) acc[c][i] = 0;
+        for (int i = 0; i < 2 * LR; ++i) col[c][i] = 0;
 #pragma unroll 4
     for (int i = 0; i < m; ++i) {
-        uint32_t xi[L];
-        ld_res<L>(xi, x + i * L);
+        uint32_t xi[LR];
+        ld_rr<LR>(xi, X + i * LR);
 #pragma unroll
-        for (int c = 0; c < G::CPL; ++c) {
-            int k = lane + c * G::TEAM;
-            uint32_t y[L];
-            ld_res<L>(y, E + ((k - r - i) & (G::TWO_M - 1)) * L);
-            mac<L>(acc[c], xi, y);
+        for (int c = 0; c < CPL; ++c) {
+            const int k = lane + c * TEAM;
+            uint32_t y[LR];
+            ld_rr<LR>(y, E + ((k - r - i) & (2 * m - 1)) * LR);
+            mac_cols<LR>(col[c], xi, y);
         }
     }
 #pragma unroll
-    for (int c = 0; c < G::CPL; ++c) redc<L>(out[c], acc[c], md, md.nsub);
+    for (int c = 0; c < CPL; ++c) redc_cols<LR>(out[c], col[c], md);
+}
+
+// Stage element x (radix-2^32 residues, L words) into X as 26-bit limbs.
+template <int m, int L, int LR>
+__device__ __forceinline__ void stage_x_rr(uint32_t* X, const uint32_t* x, int lane) {
+    constexpr int CPL = Geo<m, L>::CPL, TEAM = Geo<m, L>::TEAM;
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+        const int t = lane + c * TEAM;
+        uint32_t v[L], w[LR];
+        ld_res<L>(v, x + t * L);
+        to_rr<L, LR>(w, v);
+        st_rr<LR>(X + t * LR, w);
+    }
+}
+
+// Stage E from a factor already in 26-bit limbs (the rho^s table).
+template <int m, int LR>
+__device__ __forceinline__ void stage_ext_rr(uint32_t* E, const uint32_t* y, const ModRR<LR>& md, int lane) {
+    constexpr int CPL = Geo<m, 1>::CPL, TEAM = Geo<m, 1>::TEAM;
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+        const int t = lane + c * TEAM;
+        uint32_t v[LR], nv[LR];
+#pragma unroll
+        for (int i = 0; i < LR; ++i) v[i] = y[t * LR + i];
+        neg_rr<LR>(nv, v, md);
+        st_rr<LR>(E + t * LR, v);
+        st_rr<LR>(E + (t + m) * LR, nv);
+    }
+}
+
+// Stage E from a factor in radix-2^32 residues (a transformed operand).
+template <int m, int L, int LR>
+__device__ __forceinline__ void stage_ext_from32(uint32_t* E, const uint32_t* y, const ModRR<LR>& md, int lane) {
+    constexpr int CPL = Geo<m, L>::CPL, TEAM = Geo<m, L>::TEAM;
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+        const int t = lane + c * TEAM;
+        uint32_t v32[L], v[LR], nv[LR];
+        ld_res<L>(v32, y + t * L);
+        to_rr<L, LR>(v, v32);
+        neg_rr<LR>(nv, v, md);
+        st_rr<LR>(E + t * LR, v);
+        st_rr<LR>(E + (t + m) * LR, nv);
+    }
 }
 
 // ---------------------------------------------------------------------------
 // Forward level: inner DFT of one column (root alpha) + bad multiplications.
 // Grid: x = column (2M/2m of them), y = operand (0: a, 1: b).
 // ---------------------------------------------------------------------------
-template <int m, int L, bool FIRST>
-__global__ void __launch_bounds__(kThreads) k_fwd_level(LevelParams prm, Mod<L> md) {
+template <int m, int L, int LR, bool FIRST>
+__global__ void __launch_bounds__(kThreads) k_fwd_level(LevelParams prm, Mod<L> md, ModRR<LR> mr) {
     using G = Geo<m, L>;
     extern __shared__ __align__(16) uint32_t smem[];
     uint32_t* col = smem;                                   // 2m elements
-    uint32_t* ext = smem + G::TWO_M * G::EW;                // NTEAMS staged twiddles
+    uint32_t* tbuf = smem + G::TWO_M * G::EW;               // per-team product buffers
     constexpr int LOG2_TWO_M = ilog2<G::TWO_M>();
     const uint64_t column = blockIdx.x;
     const int op = blockIdx.y;
@@ -293,11 +330,12 @@ __global__ void __launch_bounds__(kThreads) k_fwd_level(LevelParams prm, Mod<L> 
     __syncthreads();
     dft_dit<m, L>(col, col, 1, G::TWO_M, 1, md);
 
-    // bad multiplications: output v of column l times rho^(v l bp)
+    // bad multiplications: output v of column l times rho^(v l bp) = alpha^r rho^s
     Team<m, L> tm;
-    uint32_t* E = ext + tm.id * G::STAGE_W;
+    uint32_t* X = tbuf + tm.id * TeamBuf<m, LR>::WORDS;
+    uint32_t* E = X + m * LR;
     for (int v = tm.id; v < G::TWO_M; v += G::NTEAMS) {
-        uint64_t e = ((uint64_t)v * l % prm.P2) * prm.bp % prm.P2;
+        const uint64_t e = (uint64_t)v * l * prm.bp;      // < 2M
         uint32_t* dst = poly + (base + (uint64_t)v * mu_d + l) * G::EW;
         const uint32_t* x = col + v * G::EW;
         if (e == 0) {
@@ -310,14 +348,19 @@ __global__ void __launch_bounds__(kThreads) k_fwd_level(LevelParams prm, Mod<L> 
             }
             continue;
         }
-        int r = (int)(e >> prm.log2_mu_top);
-        uint64_t s = e & (prm.mu_top - 1);
-        stage_ext<m, L>(E, prm.table + s * G::EW, md, tm.lane);
+        const int r = (int)(e >> prm.log2_mu_top);
+        const uint64_t sidx = e & (prm.mu_top - 1);
+        stage_x_rr<m, L, LR>(X, x, tm.lane);
+        stage_ext_rr<m, LR>(E, prm.table + sidx * m * LR, mr, tm.lane);
         __syncwarp(tm.mask);
-        uint32_t out[G::CPL][L];
-        negacyclic_mul<m, L>(out, x, E, r, md, tm.lane);
+        uint32_t out[G::CPL][LR];
+        negacyclic_mul_rr<m, LR>(out, X, E, r, mr, tm.lane);
 #pragma unroll
-        for (int c = 0; c < G::CPL; ++c) st_res<L>(dst + (tm.lane + c * G::TEAM) * L, out[c]);
+        for (int c = 0; c < G::CPL; ++c) {
+            uint32_t o32[L];
+            from_rr<L, LR>(o32, out[c]);
+            st_res<L>(dst + (tm.lane + c * G::TEAM) * L, o32);
+        }
         __syncwarp(tm.mask);
     }
 }
@@ -327,15 +370,15 @@ __global__ void __launch_bounds__(kThreads) k_fwd_level(LevelParams prm, Mod<L> 
 // (2M)^-1, and the first level of the backwards transform, fused.  One CTA
 // per block of r = len contiguous elements (len <= 2m, root alpha^(2m/len)).
 // ---------------------------------------------------------------------------
-template <int m, int L>
-__global__ void __launch_bounds__(kThreads) k_final_pointwise(LevelParams prm, Mod<L> md) {
+template <int m, int L, int LR>
+__global__ void __launch_bounds__(kThreads) k_final_pointwise(LevelParams prm, Mod<L> md, ModRR<LR> mr) {
     using G = Geo<m, L>;
     extern __shared__ __align__(16) uint32_t smem[];
     const int n = (int)prm.len;
     const int log2n = 31 - __clz(n);
     uint32_t* sa = smem;
     uint32_t* sb = smem + n * G::EW;
-    uint32_t* ext = sb + n * G::EW;
+    uint32_t* tbuf = sb + n * G::EW;
     const uint64_t base = (uint64_t)blockIdx.x * n;
     uint32_t* pa = prm.data;
     uint32_t* pb = prm.data + prm.poly_words;
@@ -353,20 +396,23 @@ __global__ void __launch_bounds__(kThreads) k_final_pointwise(LevelParams prm, M
     dft_dit<m, L>(sa, sb, 2, n, root, md);
     // componentwise products c_v = a_v * b_v * (2M)^-1
     Team<m, L> tm;
-    uint32_t* E = ext + tm.id * G::STAGE_W;
+    uint32_t* X = tbuf + tm.id * TeamBuf<m, LR>::WORDS;
+    uint32_t* E = X + m * LR;
+    uint32_t ks[LR];
+#pragma unroll
+    for (int w = 0; w < LR; ++w) ks[w] = prm.kscale[w];
     for (int v = tm.id; v < n; v += G::NTEAMS) {
-        stage_ext<m, L>(E, sb + v * G::EW, md, tm.lane);
+        stage_x_rr<m, L, LR>(X, sa + v * G::EW, tm.lane);
+        stage_ext_from32<m, L, LR>(E, sb + v * G::EW, mr, tm.lane);
         __syncwarp(tm.mask);
-        uint32_t out[G::CPL][L];
-        negacyclic_mul<m, L>(out, sa + v * G::EW, E, 0, md, tm.lane);
-        __syncwarp(tm.mask);
+        uint32_t out[G::CPL][LR];
+        negacyclic_mul_rr<m, LR>(out, X, E, 0, mr, tm.lane);
 #pragma unroll
         for (int c = 0; c < G::CPL; ++c) {
-            uint32_t scaled[L], ks[L];
-#pragma unroll
-            for (int w = 0; w < L; ++w) ks[w] = prm.kscale[w];
-            mont_mul<L>(scaled, out[c], ks, md);
-            st_res<L>(sa + v * G::EW + (tm.lane + c * G::TEAM) * L, scaled);
+            uint32_t scaled[LR], o32[L];
+            mont_mul_rr<LR>(scaled, out[c], ks, mr);
+            from_rr<L, LR>(o32, scaled);
+            st_res<L>(sa + v * G::EW + (tm.lane + c * G::TEAM) * L, o32);
         }
         __syncwarp(tm.mask);
     }
@@ -385,12 +431,12 @@ __global__ void __launch_bounds__(kThreads) k_final_pointwise(LevelParams prm, M
 // Backwards level (decimation in frequency): twiddle by rho^-(v l bp) first,
 // then the 2m-point DFT with root alpha^-1 over the column.
 // ---------------------------------------------------------------------------
-template <int m, int L>
-__global__ void __launch_bounds__(kThreads) k_inv_level(LevelParams prm, Mod<L> md) {
+template <int m, int L, int LR>
+__global__ void __launch_bounds__(kThreads) k_inv_level(LevelParams prm, Mod<L> md, ModRR<LR> mr) {
     using G = Geo<m, L>;
     extern __shared__ __align__(16) uint32_t smem[];
     uint32_t* col = smem;
-    uint32_t* ext = smem + G::TWO_M * G::EW;
+    uint32_t* tbuf = smem + G::TWO_M * G::EW;
     constexpr int LOG2_TWO_M = ilog2<G::TWO_M>();
     const uint64_t column = blockIdx.x;
     uint32_t* poly = prm.data;
@@ -405,20 +451,25 @@ __global__ void __launch_bounds__(kThreads) k_inv_level(LevelParams prm, Mod<L> 
     }
     __syncthreads();
     Team<m, L> tm;
-    uint32_t* E = ext + tm.id * G::STAGE_W;
+    uint32_t* X = tbuf + tm.id * TeamBuf<m, LR>::WORDS;
+    uint32_t* E = X + m * LR;
     for (int v = tm.id; v < G::TWO_M; v += G::NTEAMS) {
-        uint64_t e = ((uint64_t)v * l % prm.P2) * prm.bp % prm.P2;
+        uint64_t e = (uint64_t)v * l * prm.bp;
         if (e == 0) continue;
         e = prm.P2 - e;
-        int r = (int)(e >> prm.log2_mu_top);
-        uint64_t s = e & (prm.mu_top - 1);
-        stage_ext<m, L>(E, prm.table + s * G::EW, md, tm.lane);
+        const int r = (int)(e >> prm.log2_mu_top);
+        const uint64_t sidx = e & (prm.mu_top - 1);
+        stage_x_rr<m, L, LR>(X, col + v * G::EW, tm.lane);
+        stage_ext_rr<m, LR>(E, prm.table + sidx * m * LR, mr, tm.lane);
         __syncwarp(tm.mask);
-        uint32_t out[G::CPL][L];
-        negacyclic_mul<m, L>(out, col + v * G::EW, E, r, md, tm.lane);
-        __syncwarp(tm.mask);
+        uint32_t out[G::CPL][LR];
+        negacyclic_mul_rr<m, LR>(out, X, E, r, mr, tm.lane);
 #pragma unroll
-        for (int c = 0; c < G::CPL; ++c) st_res<L>(col + v * G::EW + (tm.lane + c * G::TEAM) * L, out[c]);
+        for (int c = 0; c < G::CPL; ++c) {
+            uint32_t o32[L];
+            from_rr<L, LR>(o32, out[c]);
+            st_res<L>(col + v * G::EW + (tm.lane + c * G::TEAM) * L, o32);
+        }
         __syncwarp(tm.mask);
     }
     __syncthreads();
@@ -431,16 +482,16 @@ __global__ void __launch_bounds__(kThreads) k_inv_level(LevelParams prm, Mod<L> 
     }
 }
 
-template <int m, int L>
+template <int m, int L, int LR>
 constexpr size_t level_smem_bytes() {
     using G = Geo<m, L>;
-    return sizeof(uint32_t) * ((size_t)G::TWO_M * G::EW + (size_t)G::NTEAMS * G::STAGE_W);
+    return sizeof(uint32_t) * ((size_t)G::TWO_M * G::EW + (size_t)G::NTEAMS * TeamBuf<m, LR>::WORDS);
 }
 
-template <int m, int L>
+template <int m, int L, int LR>
 size_t final_smem_bytes(int n) {
     using G = Geo<m, L>;
-    return sizeof(uint32_t) * (2 * (size_t)n * G::EW + (size_t)G::NTEAMS * G::STAGE_W);
+    return sizeof(uint32_t) * (2 * (size_t)n * G::EW + (size_t)G::NTEAMS * TeamBuf<m, LR>::WORDS);
 }
 
 }  // namespace dkss

@@ -15,6 +15,14 @@ static Mod<L> make_mod(const dkss_plan_s* pl) {
     return md;
 }
 
+template <int LR>
+static ModRR<LR> make_modrr(const dkss_plan_s* pl) {
+    ModRR<LR> md;
+    for (int i = 0; i < LR; ++i) md.q[i] = pl->q_rr[i];
+    md.nprime = pl->nprime26;
+    return md;
+}
+
 static LevelParams make_level(const dkss_plan_s* pl) {
     LevelParams lp{};
     lp.data = pl->d_work;
@@ -27,7 +35,7 @@ static LevelParams make_level(const dkss_plan_s* pl) {
     lp.raw_words = (pl->n_bits + 63) / 64;
     lp.u = pl->u;
     lp.log2_mu_top = pl->log2_mu_top;
-    for (int i = 0; i < 4; ++i) lp.kscale[i] = pl->kscale[i];
+    for (int i = 0; i < 5; ++i) lp.kscale[i] = pl->kscale[i];
     return lp;
 }
 
@@ -83,20 +91,20 @@ __global__ void k_unpermute(const uint32_t* src, uint64_t* dst, uint64_t P2, uin
         if (cudaGetLastError() != cudaSuccess) return DKSS_ECUDA; \
     } while (0)
 
-template <int m, int L>
+template <int m, int L, int LR>
 dkss_status prepare(dkss_plan_s* pl) {
     using G = Geo<m, L>;
-    const int lvl = (int)level_smem_bytes<m, L>();
-    const int fin = (int)final_smem_bytes<m, L>((int)pl->r_last);
+    const int lvl = (int)level_smem_bytes<m, L, LR>();
+    const int fin = (int)final_smem_bytes<m, L, LR>((int)pl->r_last);
     const int fdft = (int)(sizeof(uint32_t) * pl->r_last * G::EW);
     int optin = 0;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device) != cudaSuccess)
         return DKSS_ECUDA;
     if (lvl > optin || fin > optin) return DKSS_EUNSUPPORTED;
-    if (cudaFuncSetAttribute(k_fwd_level<m, L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lvl) ||
-        cudaFuncSetAttribute(k_fwd_level<m, L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lvl) ||
-        cudaFuncSetAttribute(k_inv_level<m, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, lvl) ||
-        cudaFuncSetAttribute(k_final_pointwise<m, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, fin) ||
+    if (cudaFuncSetAttribute(k_fwd_level<m, L, LR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lvl) ||
+        cudaFuncSetAttribute(k_fwd_level<m, L, LR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lvl) ||
+        cudaFuncSetAttribute(k_inv_level<m, L, LR>, cudaFuncAttributeMaxDynamicSharedMemorySize, lvl) ||
+        cudaFuncSetAttribute(k_final_pointwise<m, L, LR>, cudaFuncAttributeMaxDynamicSharedMemorySize, fin) ||
         cudaFuncSetAttribute(k_final_dft<m, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, fdft))
         return DKSS_ECUDA;
     // launches per dkss_mul: forward levels, fused final level, backwards levels, 3 decode
@@ -104,19 +112,20 @@ dkss_status prepare(dkss_plan_s* pl) {
     return DKSS_OK;
 }
 
-template <int m, int L>
+template <int m, int L, int LR>
 static dkss_status launch_forward_levels(dkss_plan_s* pl, LevelParams lp, int operands, cudaStream_t st) {
     using G = Geo<m, L>;
-    const size_t smem = level_smem_bytes<m, L>();
+    const size_t smem = level_smem_bytes<m, L, LR>();
     const Mod<L> md = make_mod<L>(pl);
+    const ModRR<LR> mr = make_modrr<LR>(pl);
     dim3 grid((unsigned)(pl->P2 / G::TWO_M), operands);
     uint64_t len = pl->P2, bp = 1;
     for (uint32_t d = 0; d < pl->col_levels; ++d) {
         lp.len = len;
         lp.bp = bp;
         ProfScope ps(pl, st, d == 0 ? kProfFwdFirst : kProfFwdLevel);
-        if (d == 0) k_fwd_level<m, L, true><<<grid, kThreads, smem, st>>>(lp, md);
-        else k_fwd_level<m, L, false><<<grid, kThreads, smem, st>>>(lp, md);
+        if (d == 0) k_fwd_level<m, L, LR, true><<<grid, kThreads, smem, st>>>(lp, md, mr);
+        else k_fwd_level<m, L, LR, false><<<grid, kThreads, smem, st>>>(lp, md, mr);
         DKSS_CHECK_LAUNCH();
         len /= G::TWO_M;
         bp *= G::TWO_M;
@@ -124,19 +133,20 @@ static dkss_status launch_forward_levels(dkss_plan_s* pl, LevelParams lp, int op
     return DKSS_OK;
 }
 
-template <int m, int L>
+template <int m, int L, int LR>
 dkss_status run_mul(dkss_plan_s* pl, const uint64_t* a, const uint64_t* b, uint64_t* out, cudaStream_t st) {
     using G = Geo<m, L>;
     const Mod<L> md = make_mod<L>(pl);
+    const ModRR<LR> mr = make_modrr<LR>(pl);
     LevelParams lp = make_level(pl);
     lp.raw_a = a;
     lp.raw_b = b;
-    dkss_status s = launch_forward_levels<m, L>(pl, lp, 2, st);
+    dkss_status s = launch_forward_levels<m, L, LR>(pl, lp, 2, st);
     if (s != DKSS_OK) return s;
     lp.len = pl->r_last;
     {
     ProfScope ps(pl, st, kProfFinal);
-    k_final_pointwise<m, L><<<(unsigned)(pl->P2 / pl->r_last), kThreads, final_smem_bytes<m, L>((int)pl->r_last), st>>>(lp, md);
+    k_final_pointwise<m, L, LR><<<(unsigned)(pl->P2 / pl->r_last), kThreads, final_smem_bytes<m, L, LR>((int)pl->r_last), st>>>(lp, md, mr);
     DKSS_CHECK_LAUNCH();
     }
     for (int d = (int)pl->col_levels - 1; d >= 0; --d) {
@@ -145,7 +155,7 @@ dkss_status run_mul(dkss_plan_s* pl, const uint64_t* a, const uint64_t* b, uint6
         for (int i = 0; i < d; ++i) bp *= G::TWO_M;
         lp.len = pl->P2 / bp;
         lp.bp = bp;
-        k_inv_level<m, L><<<(unsigned)(pl->P2 / G::TWO_M), kThreads, level_smem_bytes<m, L>(), st>>>(lp, md);
+        k_inv_level<m, L, LR><<<(unsigned)(pl->P2 / G::TWO_M), kThreads, level_smem_bytes<m, L, LR>(), st>>>(lp, md, mr);
         DKSS_CHECK_LAUNCH();
     }
     DecodeParams dp{};
@@ -165,7 +175,9 @@ dkss_status run_mul(dkss_plan_s* pl, const uint64_t* a, const uint64_t* b, uint6
     dp.db += 1;
     dp.out_aligned16 = ((uintptr_t)out & 15) == 0;
     ProfScope ps(pl, st, kProfDecode);
-    k_decode_tiles<L><<<(unsigned)pl->n_tiles, kDecThreads, 0, st>>>(dp);
+    if (pl->u == 32) k_decode_tiles_aligned<L, 1><<<(unsigned)pl->n_tiles, kDecThreads, 0, st>>>(dp);
+    else if (pl->u == 16) k_decode_tiles_aligned<L, 2><<<(unsigned)pl->n_tiles, kDecThreads, 0, st>>>(dp);
+    else k_decode_tiles<L><<<(unsigned)pl->n_tiles, kDecThreads, 0, st>>>(dp);
     DKSS_CHECK_LAUNCH();
     k_decode_scan<<<1, kScanThreads, 0, st>>>(dp);
     DKSS_CHECK_LAUNCH();
@@ -174,14 +186,14 @@ dkss_status run_mul(dkss_plan_s* pl, const uint64_t* a, const uint64_t* b, uint6
     return DKSS_OK;
 }
 
-template <int m, int L>
+template <int m, int L, int LR>
 dkss_status run_forward(dkss_plan_s* pl, const uint64_t* a, uint64_t* out, cudaStream_t st) {
     using G = Geo<m, L>;
     const Mod<L> md = make_mod<L>(pl);
     LevelParams lp = make_level(pl);
     lp.raw_a = a;
     lp.raw_b = a;
-    dkss_status s = launch_forward_levels<m, L>(pl, lp, 1, st);
+    dkss_status s = launch_forward_levels<m, L, LR>(pl, lp, 1, st);
     if (s != DKSS_OK) return s;
     lp.len = pl->r_last;
     k_final_dft<m, L><<<(unsigned)(pl->P2 / pl->r_last), kThreads, sizeof(uint32_t) * pl->r_last * G::EW, st>>>(lp, md);
@@ -194,8 +206,8 @@ dkss_status run_forward(dkss_plan_s* pl, const uint64_t* a, uint64_t* out, cudaS
 
 }  // namespace dkss
 
-#define DKSS_INSTANTIATE(M_, L_)                                                                            \
-    template dkss_status dkss::run_mul<M_, L_>(dkss_plan_s*, const uint64_t*, const uint64_t*, uint64_t*, \
-                                              cudaStream_t);                                               \
-    template dkss_status dkss::run_forward<M_, L_>(dkss_plan_s*, const uint64_t*, uint64_t*, cudaStream_t); \
-    template dkss_status dkss::prepare<M_, L_>(dkss_plan_s*);
+#define DKSS_INSTANTIATE(M_, L_, LR_)                                                                        \
+    template dkss_status dkss::run_mul<M_, L_, LR_>(dkss_plan_s*, const uint64_t*, const uint64_t*, uint64_t*, \
+                                                   cudaStream_t);                                               \
+    template dkss_status dkss::run_forward<M_, L_, LR_>(dkss_plan_s*, const uint64_t*, uint64_t*, cudaStream_t); \
+    template dkss_status dkss::prepare<M_, L_, LR_>(dkss_plan_s*);

@@ -20,7 +20,10 @@ struct dkss_plan_s {
     dkss_host::u128 q = 0;        // p^z
     uint32_t q_limbs[4] = {0, 0, 0, 0};
     uint32_t nprime = 0, nsub = 0;
-    uint32_t kscale[4] = {0, 0, 0, 0};
+    uint32_t LR = 0;              // 26-bit limbs of the product arithmetic
+    uint32_t q_rr[5] = {0, 0, 0, 0, 0};
+    uint32_t nprime26 = 0;        // -(p^z)^-1 mod 2^26
+    uint32_t kscale[5] = {0, 0, 0, 0, 0};  // (2M)^-1 R'^2 mod p^z, 26-bit limbs
     dkss_host::Roots roots;
     // device memory owned by the plan
     int device = 0;
@@ -69,11 +72,11 @@ struct ProfScope {
 }  // namespace dkss
 
 namespace dkss {
-// Per-(m, L) launchers, explicitly instantiated in inst_m<m>_L<L>.cu.
-template <int m, int L>
+// Per-(m, L, LR) launchers, explicitly instantiated by inst.cu.
+template <int m, int L, int LR>
 dkss_status run_mul(dkss_plan_s* pl, const uint64_t* a, const uint64_t* b, uint64_t* out, cudaStream_t st);
-template <int m, int L>
+template <int m, int L, int LR>
 dkss_status run_forward(dkss_plan_s* pl, const uint64_t* a, uint64_t* out, cudaStream_t st);
-template <int m, int L>
+template <int m, int L, int LR>
 dkss_status prepare(dkss_plan_s* pl);
 }  // namespace dkss

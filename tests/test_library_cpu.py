@@ -66,6 +66,10 @@ def test_plan_roots_match_oracle(dk, cfg):
     L = consts["L"]
     assert par.pz < 1 << (32 * L - 1)
     assert par.m * par.pz ** 2 + (1 << (32 * L)) * par.pz < 1 << (64 * L)
+    # 26-bit product limbs: m p^z < 2^(26 LR), so one subtraction ends each REDC,
+    # and a 64-bit column holds m*LR limb products of 52 bits
+    LR = consts["LR"]
+    assert par.m * par.pz < 1 << (26 * LR) and par.m * LR * (1 << 52) < 1 << 63
 
 
 @pytest.mark.parametrize("bad", [
