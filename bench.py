@@ -295,7 +295,7 @@ def oracle_product_seconds(name, A, B):
 
 def cpu_baseline(name, A, B):
     dt, c = oracle_product_seconds(name, A, B)
-    ok = syn.to_int(c[:4]) == (syn.to_int(A[:2]) * syn.to_int(B[:2])) % (1 << 256)
+    ok = syn.to_int(c[:2]) == (syn.to_int(A[:2]) * syn.to_int(B[:2])) % (1 << 128)
     n_bits = syn.WORKLOADS[name]["n_bits"]
     return {"value": round(2 * n_bits / dt / 1e9, 6), "unit": "Gbit/s", "cores": 1, "kind": "oracle",
             "sample": "one full %s product (C oracle, single thread, %.2f s)" % (name, dt),

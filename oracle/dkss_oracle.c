@@ -7,9 +7,9 @@
  * Implementation and Analysis of the DKSS Algorithm" (arXiv:1503.04955),
  * Section 3.2, in the same order and notation as the Python oracle:
  *   encode (Section 3.2.4, Fig. dkss:fig:encode), forward FFT by inner DFTs,
- *   bad multiplications and recursive outer DFTs (Section 3.2.4 i.-iii. and
- *   Section 4.2), componentwise products (Section 3.2.5), backwards transform
- *   as forward transform read at index -l and division by 2M (Sections 2.5,
+ *   bad multiplications and recursive outer DFTs (Section 3.2.5 i.-iii. and
+ *   Section 4.2), componentwise products (Section 3.2.6), backwards transform
+ *   as forward transform read at index -l and division by 2M (Sections 2.7,
  *   3.2.7, 3.2.8), decode by shifted additions (Section 3.2.8).
  *
  * Residues are unsigned __int128 values in [0, p^z) with p^z < 2^126.
@@ -107,12 +107,12 @@ static void r_mul(u128* out, const u128* x, const u128* y, const par_t* par) {
     for (uint32_t k = 0; k < m; k++) out[k] = reduce256(acc[k], par);
 }
 
-/* ---- the FFT (Section 3.2.4, Section 4.2) ------------------------------- */
+/* ---- the FFT (Section 3.2.5, Section 4.2) ------------------------------- */
 
 /* Length-n DFT of n elements of R with root alpha^step (n*step = 2m),
  * radix-2 decimation in time: X_k = E_k + w^k O_k, X_{k+n/2} = E_k - w^k O_k,
  * where E, O are the half-length DFTs of the even and odd elements
- * (Section 2.4; the thesis's inner FFT, Section 4.2). */
+ * (Section 2.6; the thesis's inner FFT, Section 4.2). */
 static void alpha_dft(u128* e, uint64_t n, uint32_t step, const par_t* par) {
     uint32_t m = par->m;
     if (n == 1) return;

@@ -195,7 +195,7 @@ def r_sub(x, y, q):
 
 def r_shift(x, k, q):
     """x * alpha^k: a cyclic shift where coefficients passing degree m wrap
-    around with changed sign, because alpha^m = -1 (Section 3.2.4, i.)."""
+    around with changed sign, because alpha^m = -1 (Section 3.2.5, i.)."""
     m = len(x)
     k %= 2 * m
     out = [0] * m
@@ -269,7 +269,7 @@ def decode(c, par):
 
 
 # ---------------------------------------------------------------------------
-# The FFT (Section 3.2.4 steps i-iii and Section 4.2)
+# The FFT (Section 3.2.5 steps i-iii and Section 4.2)
 # ---------------------------------------------------------------------------
 
 def rho_table(rho, par):
@@ -290,7 +290,7 @@ def rho_power(e, table, par):
 def alpha_dft(e, step, par):
     """Length-n DFT with root alpha^step (n * step = 2m): the plain definition
     E_v = sum_j e_j alpha^(step*j*v), using only shifts and additions
-    (inner DFTs of Section 3.2.4 i.; the last level when the length is <= 2m)."""
+    (inner DFTs of Section 3.2.5 i.; the last level when the length is <= 2m)."""
     n = len(e)
     out = []
     for v in range(n):
@@ -305,7 +305,7 @@ def dkss_fft(a, table, par, base_pow=1, dump=None):
     """DFT of the vector a (length n, a power of 2 dividing 2M) with root
     rho^base_pow, returned in natural order: out[k] = sum_j a_j rho^(base_pow*j*k).
 
-    Section 3.2.4: write a as 2m rows of mu' = n/2m columns; i. inner DFTs of the
+    Section 3.2.5: write a as 2m rows of mu' = n/2m columns; i. inner DFTs of the
     columns e_l with root alpha give abar_{v,l} = e_l(alpha^v); ii. bad
     multiplications abar_{v,l} * rho^(v*l*base_pow); iii. outer DFTs of the rows
     with root rho^(2m*base_pow) by recursion, whose output f is element 2m*f + v.
@@ -335,7 +335,7 @@ def dkss_fft(a, table, par, base_pow=1, dump=None):
 
 
 def dkss_inverse(c_hat, table, par):
-    """Backwards transform (Sections 2.5 and 3.2.7): a forward transform again,
+    """Backwards transform (Sections 2.7 and 3.2.7): a forward transform again,
     read at index (-l) mod 2M, then division by 2M."""
     y = dkss_fft(c_hat, table, par)
     inv = pow(par.P2, -1, par.pz)
@@ -368,7 +368,7 @@ def dkss_mul(a, b, par, roots=None, stages=None):
 
 
 # ---------------------------------------------------------------------------
-# Comparison multiplier (Section 2.2, OMUL): schoolbook on 64-bit words
+# Comparison multiplier (Section 2.3, OMUL): schoolbook on 64-bit words
 # ---------------------------------------------------------------------------
 
 def omul(a_words, b_words):

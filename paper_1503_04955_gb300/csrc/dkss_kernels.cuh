@@ -5,7 +5,7 @@
 // word (e*m + t)*L + l.  Every kernel below works on that layout.
 //
 // The forward 2M-point transform is the thesis's radix-2m decimation in time
-// (Section 3.2.4 i.-iii.), done in place level by level: level d splits each
+// (Section 3.2.5 i.-iii.), done in place level by level: level d splits each
 // block of len = 2M/(2m)^(d-1) elements into 2m rows of len/2m columns; one
 // CTA takes one column, runs the 2m-point inner DFT with root alpha (shifts
 // only) in shared memory and multiplies output v of column l by the bad
@@ -13,7 +13,7 @@
 // mixed-radix digit-reversed order.  Componentwise products do not care about
 // order; the backwards transform runs the same levels in reverse as
 // decimation in frequency with rho^-1 and alpha^-1 (the backwards transform
-// of Section 2.5), which returns natural order.
+// of Section 2.7), which returns natural order.
 #pragma once
 #include <cstdint>
 

@@ -60,7 +60,7 @@ def test_operand_masking_and_specials():
     assert syn.to_int(syn.special_operand(1000, "one")) == 1
 
 
-# ---- primality, generators, roots (Section 3.2.2 / 3.2.3, Section 2.7 table) --
+# ---- primality, generators, roots (Section 3.2.2 / 3.2.3, Section 2.8 table) --
 
 def test_lucas_matches_trial_division():
     def trial(n):
@@ -189,7 +189,7 @@ def test_r_shift_is_alpha_power_product():
     assert o.r_shift(x, m, q) == [(-v) % q for v in x]
 
 
-# ---- FFT (Section 3.2.4) --------------------------------------------------------
+# ---- FFT (Section 3.2.5) --------------------------------------------------------
 
 @pytest.mark.parametrize("cfg", TINY)
 def test_alpha_dft_brute_force(cfg):
