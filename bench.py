@@ -56,6 +56,8 @@ def parse_args():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(syn.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=30)
+    ap.add_argument("--form", default="ntt", choices=["ntt", "direct"],
+                    help="R-multiplications through the evaluation map of R (ntt) or the direct convolution")
     return ap.parse_args()
 
 
@@ -119,18 +121,32 @@ class ClockSampler:
 
 # ------------------------------------------------------ algorithmic counts ----
 
-def rmul_imads(m, L):
-    """32-bit multiply-adds of one R-multiplication, the negacyclic convolution
-    (thesis eq. ncycconv) with one Montgomery reduction per output: m^2 L^2
-    limb products (lo and hi halves) plus m reductions of L(L+1) products."""
-    return 2 * m * m * L * L + m * (2 * L * L + L)
+def modmul_imads(L):
+    """32-bit multiply-adds of one Montgomery product of L-limb residues: L^2
+    limb products (lo and hi halves) plus the reduction's L(L+1) products."""
+    return 2 * L * L + L * (2 * L + 1)
 
 
-def stage_work(info, m):
+def rmul_imads(m, L, form, pointwise=False):
+    """Multiply-adds of one R-multiplication.
+    direct: the negacyclic convolution (thesis eq. ncycconv), m^2 limb-level
+      products and m reductions.
+    ntt: through the evaluation map of R (forward transform of each variable
+      factor, m/2 log2 m products; m pointwise products; backwards transform,
+      m/2 (log2 m + 1) products including the final scaling)."""
+    if form == "direct":
+        return 2 * m * m * L * L + m * L * (2 * L + 1)
+    lg = m.bit_length() - 1
+    forwards = 2 if pointwise else 1
+    return (forwards * (m // 2) * lg + m + (m // 2) * (lg + 1)) * modmul_imads(L)
+
+
+def stage_work(info, m, form):
     """Per kernel group: (algorithmic 32-bit multiply-adds per step, launches
     per step).  Twiddles rho^0 = 1 are not work; every other twiddle and every
-    componentwise product is one R-multiplication; the scaling by (2M)^-1 is one
-    Montgomery product per coefficient."""
+    componentwise product is one R-multiplication (the direct form also scales
+    each product coefficient by (2M)^-1 with one Montgomery product).  The
+    inner DFTs have no products."""
     P2, L, col_levels = info["P2"], info["L"], info["levels"] - 1
     nontrivial = []
     length = P2
@@ -138,13 +154,13 @@ def stage_work(info, m):
         mu_d = length // (2 * m)
         nontrivial.append((P2 // length) * (mu_d - 1) * (2 * m - 1))
         length //= 2 * m
-    r = rmul_imads(m, L)
-    scale = 4 * L * L + 2 * L
+    r = rmul_imads(m, L, form)
+    rp = rmul_imads(m, L, form, pointwise=True)
+    scale = P2 * m * modmul_imads(L) if form == "direct" else 0
     return {
-        "fwd_first_level": (2 * nontrivial[0] * r, 1),
-        "fwd_level": (2 * sum(nontrivial[1:]) * r, col_levels - 1),
-        "final_pointwise": (P2 * r + P2 * m * scale, 1),
-        "inv_level": (sum(nontrivial) * r, col_levels),
+        "fwd_twiddle": (2 * sum(nontrivial) * r, col_levels),
+        "final_pointwise": (P2 * rp + scale, 1),
+        "inv_twiddle": (sum(nontrivial) * r, col_levels),
     }
 
 
@@ -175,7 +191,8 @@ def run_ours(args):
     cfg = syn.workload_params(args.workload)
     n_bits = cfg[0]
     A, B = syn.operand_pair(n_bits, syn.config_seed(syn.WORKLOADS[args.workload]["index"]), product=rank)
-    plan = dk.Plan(*cfg, flags=binding.FORM_PROFILE)
+    flags = binding.FORM_PROFILE | (binding.RMUL_DIRECT if args.form == "direct" else 0)
+    plan = dk.Plan(*cfg, flags=flags)
     info = plan.info()
     a = torch.from_numpy(A.view(np.int64)).to(dev)
     b = torch.from_numpy(B.view(np.int64)).to(dev)
@@ -235,7 +252,7 @@ def run_ours(args):
     e2e_value = bits_per_step / e2e_s / 1e9
 
     # roofline of the kernel group with the most device time
-    work = stage_work(info, cfg[2])
+    work = stage_work(info, cfg[2], args.form)
     dom = max((k for k in prof if k in work), key=lambda k: prof[k][0])
     dom_ms, dom_n = prof[dom]
     ops_per_step, launches_per_step = work[dom]
@@ -259,7 +276,7 @@ def run_ours(args):
             "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(ms_per_step, 5),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic: SplitMix64 uniform operands in [0, 2^N)",
-            "config": dict(workload_config(args.workload), form="imad",
+            "config": dict(workload_config(args.workload), form="imad", rmul=args.form,
                            l2="flushed between steps (256 MiB write outside the timed events)",
                            parallelism="replicas" if world > 1 else "single GPU"),
             "products_per_s": round(world / (ms_per_step * 1e-3), 3),

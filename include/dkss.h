@@ -51,7 +51,9 @@ enum {
     DKSS_FORM_IMAD = 1,    /* R-multiplications on the integer pipe (default) */
     DKSS_FORM_INT8TC = 2,  /* R-multiplications as exact INT8 tensor-core MMAs */
     DKSS_PROFILE = 4,      /* per-stage CUDA-event timing, read with dkss_profile_read */
-    DKSS_DEBUG_CHECKS = 8  /* reserved: extra device-side range checks */
+    DKSS_DEBUG_CHECKS = 8, /* reserved: extra device-side range checks */
+    DKSS_RMUL_DIRECT = 16  /* R-multiplications by the direct negacyclic convolution
+                              (Section 2.9.2) instead of through the evaluation map of R */
 };
 
 /*
@@ -62,7 +64,8 @@ enum {
  *   u       input bits per inner coefficient, 1 <= u <= 32, M*(m/2)*u >= N.
  *   p, z    p prime with 2M | p-1 (Section 3.2.2); the residue ring is
  *           Z/p^zZ; p^z must exceed the largest product coefficient
- *           M*(m/2)*(2^u-1)^2 (Section 3.2.2) and p^z < 2^126.
+ *           M*(m/2)*(2^u-1)^2 (Section 3.2.2); m*p^z < 2^127 (so that
+ *           products in 26-bit limbs stay within 5 limbs).
  *   flags   DKSS_FORM_* (IMAD when 0).
  * On the host it tests p (deterministic Miller-Rabin), finds the smallest
  * generator zeta of F_p^*, Hensel-lifts it to a (p-1)-th root of unity mod p^z,
@@ -140,9 +143,10 @@ dkss_status dkss_plan_rho(uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, u
  * Per-stage device times of the plan's calls since the last read (needs
  * DKSS_PROFILE at dkss_plan; CUDA events recorded on the caller's stream around
  * each kernel group).  Waits for those events.  Index k of ms (milliseconds
- * summed) and counts (groups timed): 0 first forward level (with encoding),
- * 1 later forward levels, 2 last forward level + componentwise products +
- * first backwards level, 3 backwards levels, 4 decoding and carry scan.
+ * summed) and counts (groups timed): 0 forward inner DFTs (the first level
+ * encodes), 1 forward bad multiplications, 2 last forward level +
+ * componentwise products + first backwards level, 3 backwards bad
+ * multiplications, 4 backwards inner DFTs, 5 decoding and carry scan.
  * Either array may be NULL; n is their length (at most 8 used).  Resets the
  * sums.  Errors: DKSS_EINVAL, DKSS_ECUDA.
  */

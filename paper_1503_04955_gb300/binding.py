@@ -25,7 +25,8 @@ EXPORTS = ["dkss_plan", "dkss_mul", "dkss_mul_host", "dkss_forward", "dkss_mul_b
            "dkss_plan_rho", "dkss_profile_read", "dkss_plan_launches", "dkss_sync_status", "dkss_plan_destroy",
            "dkss_status_str"]
 FORM_PROFILE = 4
-PROFILE_KINDS = ["fwd_first_level", "fwd_level", "final_pointwise", "inv_level", "decode"]
+RMUL_DIRECT = 16
+PROFILE_KINDS = ["fwd_dft", "fwd_twiddle", "final_pointwise", "inv_twiddle", "inv_dft", "decode"]
 
 
 class DkssError(RuntimeError):

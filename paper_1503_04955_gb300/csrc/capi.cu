@@ -93,7 +93,7 @@ dkss_status plan_host(dkss_plan_s* pl, uint64_t n_bits, uint64_t M, uint32_t m, 
     }
     const u128 umax = ((u128)1 << u) - 1;
     if (!(q > (u128)M * h * umax * umax)) return DKSS_EPARAM;  // largest coefficient M (m/2) (2^u-1)^2
-    if ((u128)m * q >= ((u128)1 << 127)) return DKSS_EPARAM;  // host sums of m products
+    if ((u128)m * q >= ((u128)1 << 127)) return DKSS_EUNSUPPORTED;  // host sums of m products; 4 m q < 2^130
     // limbs: one spare bit for sums, and m q^2 + R q < 2^(64L) for the REDC of m-term sums
     uint32_t L = (uint32_t)((bitlen(q) + 1 + 31) / 32);
     if (L < 2) L = 2;
@@ -136,9 +136,10 @@ dkss_status plan_host(dkss_plan_s* pl, uint64_t n_bits, uint64_t M, uint32_t m, 
     }
     const int RB = 32 * (int)L;
     pl->nsub = (uint32_t)(RB >= 128 ? 0 : (uint64_t)(((u128)m * q) >> RB)) + 1;
-    // products in 26-bit limbs: m q < R' = 2^(26 LR) keeps every REDC output below 2q
+    // products in 26-bit limbs: 4 m q < R' = 2^(26 LR) keeps every REDC input of the
+    // direct convolution and of the transform in R below q R'
     uint32_t LR = 2;
-    while (LR <= 5 && (26 * LR < 127 && (((u128)m * q) >> (26 * LR)) != 0)) ++LR;
+    while (LR <= 5 && (26 * LR < 127 && (((u128)m * q) >> (26 * LR - 2)) != 0)) ++LR;
     if (LR > 5 || LR < L || LR > L + 1) return DKSS_EUNSUPPORTED;
     pl->LR = LR;
     for (uint32_t i = 0; i < 5; ++i) pl->q_rr[i] = i < LR ? (uint32_t)(q >> (26 * i)) & ((1u << 26) - 1) : 0;
@@ -207,12 +208,90 @@ void build_table(const dkss_plan_s* pl, std::vector<uint32_t>& out) {
     for (auto& t : th) t.join();
 }
 
+u128 to_dev(const MontCtx& c, u128 v_m, u128 rdev) { return c.mul(v_m, rdev); }
+
+void put_rr(uint32_t* dst, u128 v, uint32_t LR) {
+    for (uint32_t w = 0; w < LR; ++w) dst[w] = (uint32_t)(v >> (26 * w)) & ((1u << 26) - 1);
+}
+
+uint32_t brv(uint32_t x, uint32_t bits) {
+    uint32_t r = 0;
+    for (uint32_t i = 0; i < bits; ++i) r |= ((x >> i) & 1u) << (bits - 1 - i);
+    return r;
+}
+
+// Constants of the transform in R (ntt_rmul.cuh, NttLayout): psi = gamma.
+void build_ntt_consts(const dkss_plan_s* pl, std::vector<uint32_t>& out) {
+    const uint32_t m = pl->m, LR = pl->LR;
+    uint32_t lg = 0;
+    while ((1u << lg) < m) ++lg;
+    const uint32_t Q = 2 * m + lg, COUNT = Q + 5;
+    out.assign((size_t)COUNT * LR, 0);
+    MontCtx c(pl->q);
+    const u128 rdev = pow2_mod(26 * (int)LR, pl->q);
+    const u128 phi = pl->q / pl->p * (pl->p - 1);
+    const u128 psi = c.to(pl->roots.gamma);
+    const u128 psi_inv = c.pow(psi, phi - 1);
+    for (uint32_t k = 1; k < m; ++k) {
+        put_rr(&out[(size_t)k * LR], to_dev(c, c.pow(psi, brv(k, lg)), rdev), LR);
+        put_rr(&out[(size_t)(m + k) * LR], to_dev(c, c.pow(psi_inv, brv(k, lg)), rdev), LR);
+    }
+    for (uint32_t b = 0; b < lg; ++b) put_rr(&out[(size_t)(2 * m + b) * LR], pl->q << b, LR);
+    put_rr(&out[(size_t)Q * LR], pl->q, LR);
+    const u128 minv = c.pow(c.to(m), phi - 1);
+    const u128 p2inv = c.pow(c.to(pl->P2 % pl->q), phi - 1);
+    const u128 zlast = c.pow(psi_inv, brv(1, lg));
+    put_rr(&out[(size_t)(Q + 1) * LR], to_dev(c, minv, rdev), LR);
+    put_rr(&out[(size_t)(Q + 2) * LR], to_dev(c, c.mul(zlast, minv), rdev), LR);
+    // componentwise products multiply two normal-form factors, so their scaling
+    // constants carry one more R' to cancel the product's R'^-1
+    const u128 rdev_m = c.to(rdev);
+    put_rr(&out[(size_t)(Q + 3) * LR], to_dev(c, c.mul(c.mul(minv, p2inv), rdev_m), rdev), LR);
+    put_rr(&out[(size_t)(Q + 4) * LR], to_dev(c, c.mul(c.mul(c.mul(zlast, minv), p2inv), rdev_m), rdev), LR);
+}
+
+// Evaluations of the bad twiddles: rho^s(gamma^(2j+1)) = omega^(s(2j+1)), stored
+// for s < mu_top at index i with j = brv(i), in device Montgomery form.
+void build_eval_table(const dkss_plan_s* pl, std::vector<uint32_t>& out) {
+    const uint32_t m = pl->m, LR = pl->LR;
+    uint32_t lg = 0;
+    while ((1u << lg) < m) ++lg;
+    const uint64_t mu = pl->mu_top;
+    out.assign(mu * m * LR, 0);
+    MontCtx c(pl->q);
+    const u128 rdev = pow2_mod(26 * (int)LR, pl->q);
+    const u128 om = c.to(pl->roots.omega);
+    unsigned hw = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    uint64_t chunks = std::min<uint64_t>(hw, mu);
+    std::vector<std::thread> th;
+    for (uint64_t ci = 0; ci < chunks; ++ci) {
+        th.emplace_back([&, ci]() {
+            uint64_t s0 = mu * ci / chunks, s1 = mu * (ci + 1) / chunks;
+            u128 ws = c.pow(om, s0);
+            std::vector<u128> val(m);
+            for (uint64_t s = s0; s < s1; ++s) {
+                u128 w2 = c.mul(ws, ws), cur = ws;
+                for (uint32_t j = 0; j < m; ++j) {
+                    val[j] = cur;
+                    cur = c.mul(cur, w2);
+                }
+                for (uint32_t i = 0; i < m; ++i)
+                    put_rr(&out[(s * m + i) * LR], to_dev(c, val[brv(i, lg)], rdev), LR);
+                ws = c.mul(ws, om);
+            }
+        });
+    }
+    for (auto& t : th) t.join();
+}
+
 void free_device(dkss_plan_s* pl) {
     cudaFree(pl->d_table);
     cudaFree(pl->d_work);
     cudaFree(pl->d_agg);
     cudaFree(pl->d_status);
     cudaFree(pl->d_stage);
+    cudaFree(pl->d_ntt);
+    pl->d_ntt = nullptr;
     pl->d_table = nullptr; pl->d_work = nullptr; pl->d_agg = nullptr; pl->d_status = nullptr; pl->d_stage = nullptr;
 }
 
@@ -252,15 +331,18 @@ dkss_status dkss_plan(dkss_plan_t* plan, uint64_t n_bits, uint64_t M, uint32_t m
         delete pl;
         return DKSS_ECUDA;
     }
-    std::vector<uint32_t> table;
-    build_table(pl, table);
+    std::vector<uint32_t> table, ntt;
+    if (pl->flags & DKSS_RMUL_DIRECT) build_table(pl, table);
+    else build_eval_table(pl, table);
+    build_ntt_consts(pl, ntt);
     pl->poly_words = pl->P2 * pl->m * pl->L;
     const uint64_t nw = (n_bits + 63) / 64;
     pl->n_tiles = (4 * nw + 2047) / 2048;
     bool ok = cudaMalloc(&pl->d_table, table.size() * sizeof(uint32_t)) == cudaSuccess &&
               cudaMalloc(&pl->d_work, 2 * pl->poly_words * sizeof(uint32_t)) == cudaSuccess &&
               cudaMalloc(&pl->d_agg, pl->n_tiles * sizeof(uint32_t)) == cudaSuccess &&
-              cudaMalloc(&pl->d_status, sizeof(uint32_t)) == cudaSuccess;
+              cudaMalloc(&pl->d_status, sizeof(uint32_t)) == cudaSuccess &&
+              cudaMalloc(&pl->d_ntt, ntt.size() * sizeof(uint32_t)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_device(pl);
@@ -268,6 +350,7 @@ dkss_status dkss_plan(dkss_plan_t* plan, uint64_t n_bits, uint64_t M, uint32_t m
         return DKSS_ENOMEM;
     }
     if (cudaMemcpy(pl->d_table, table.data(), table.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(pl->d_ntt, ntt.data(), ntt.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(pl->d_status, 0, sizeof(uint32_t)) != cudaSuccess) {
         free_device(pl);
         delete pl;

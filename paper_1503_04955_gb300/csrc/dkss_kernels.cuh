@@ -7,9 +7,10 @@
 // The forward 2M-point transform is the thesis's radix-2m decimation in time
 // (Section 3.2.5 i.-iii.), done in place level by level: level d splits each
 // block of len = 2M/(2m)^(d-1) elements into 2m rows of len/2m columns; one
-// CTA takes one column, runs the 2m-point inner DFT with root alpha (shifts
-// only) in shared memory and multiplies output v of column l by the bad
-// twiddle rho^(v*l*(2m)^(d-1)).  After the last level the elements sit in
+// CTA takes one column and runs the 2m-point inner DFT with root alpha (shifts
+// only) in shared memory, then an element-parallel kernel multiplies output v
+// of column l by the bad twiddle rho^(v*l*(2m)^(d-1)), one team of m/2 lanes
+// per element.  After the last level the elements sit in
 // mixed-radix digit-reversed order.  Componentwise products do not care about
 // order; the backwards transform runs the same levels in reverse as
 // decimation in frequency with rho^-1 and alpha^-1 (the backwards transform
@@ -18,6 +19,7 @@
 #include <cstdint>
 
 #include "arith.cuh"
+#include "ntt_rmul.cuh"
 #include "rr_arith.cuh"
 
 namespace dkss {
@@ -29,7 +31,7 @@ template <int m, int L>
 struct Geo {
     static constexpr int TWO_M = 2 * m;
     static constexpr int EW = m * L;                     // words per element of R
-    static constexpr int TEAM = m < 32 ? m : 32;         // lanes per element
+    static constexpr int TEAM = m / 2;                   // lanes per element (2 coefficients each)
     static constexpr int TEAMS_PER_WARP = 32 / TEAM;
     static constexpr int NTEAMS = kWarps * TEAMS_PER_WARP;
     static constexpr int CPL = m / TEAM;                 // coefficients per lane
@@ -58,6 +60,8 @@ struct LevelParams {
     uint32_t u;
     uint32_t log2_mu_top;
     uint32_t kscale[5];        // (2M)^-1 R'^2 mod p^z in 26-bit limbs, R' = 2^(26 LR)
+    const uint32_t* table_eval;  // rho^s(gamma^(2 brv(i)+1)) R', s < mu_top, i < m: LR words each
+    const uint32_t* ntt_cst;     // NttLayout<m> constants, LR words each
 };
 
 __device__ __forceinline__ uint32_t bitrev(uint32_t x, int bits) { return __brev(x) >> (32 - bits); }
@@ -215,30 +219,31 @@ __device__ void dft_dif(uint32_t* s, int n, int root, const Mod<L>& md) {
 // Negacyclic product in R (Section 2.9.2, eq. ncycconv) times alpha^r, in
 // 26-bit limbs: out_k = REDC(sum_i x_i E[(k - r - i) mod 2m]) where
 // E[t] = y_t and E[t+m] = -y_t, so that the wrapped terms carry their minus
-// sign.  X and E are the team's shared buffers; results stay in registers.
+// sign.  X and E are the team's shared buffers.  Lane l computes the two
+// consecutive outputs k = 2l and 2l+1: the factor E[k - r - i] used for
+// output k at step i is the one output k+1 needs at step i+1, so each step
+// loads one x_i (broadcast) and one E value for two outputs.
 template <int m, int LR>
-__device__ __forceinline__ void negacyclic_mul_rr(uint32_t (&out)[Geo<m, 1>::CPL][LR], const uint32_t* X,
-                                                  const uint32_t* E, int r, const ModRR<LR>& md, int lane) {
-    constexpr int CPL = Geo<m, 1>::CPL, TEAM = Geo<m, 1>::TEAM;
-    uint64_t col[CPL][2 * LR];
+__device__ __forceinline__ void negacyclic_mul_rr(uint32_t (&out)[2][LR], const uint32_t* X, const uint32_t* E, int r,
+                                                  const ModRR<LR>& md, int lane) {
+    const int k0 = 2 * lane;
+    uint64_t c0[2 * LR], c1[2 * LR];
 #pragma unroll
-    for (int c = 0; c < CPL; ++c)
-#pragma unroll
-        for (int i = 0; i < 2 * LR; ++i) col[c][i] = 0;
+    for (int i = 0; i < 2 * LR; ++i) c0[i] = c1[i] = 0;
+    uint32_t prev[LR];
+    ld_rr<LR>(prev, E + ((k0 + 1 - r) & (2 * m - 1)) * LR);
 #pragma unroll 4
     for (int i = 0; i < m; ++i) {
-        uint32_t xi[LR];
+        uint32_t xi[LR], cur[LR];
         ld_rr<LR>(xi, X + i * LR);
+        ld_rr<LR>(cur, E + ((k0 - r - i) & (2 * m - 1)) * LR);
+        mac_cols<LR>(c0, xi, cur);
+        mac_cols<LR>(c1, xi, prev);
 #pragma unroll
-        for (int c = 0; c < CPL; ++c) {
-            const int k = lane + c * TEAM;
-            uint32_t y[LR];
-            ld_rr<LR>(y, E + ((k - r - i) & (2 * m - 1)) * LR);
-            mac_cols<LR>(col[c], xi, y);
-        }
+        for (int w = 0; w < LR; ++w) prev[w] = cur[w];
     }
-#pragma unroll
-    for (int c = 0; c < CPL; ++c) redc_cols<LR>(out[c], col[c], md);
+    redc_cols<LR>(out[0], c0, md);
+    redc_cols<LR>(out[1], c1, md);
 }
 
 // Stage element x (radix-2^32 residues, L words) into X as 26-bit limbs.
@@ -288,15 +293,16 @@ __device__ __forceinline__ void stage_ext_from32(uint32_t* E, const uint32_t* y,
 }
 
 // ---------------------------------------------------------------------------
-// Forward level: inner DFT of one column (root alpha) + bad multiplications.
-// Grid: x = column (2M/2m of them), y = operand (0: a, 1: b).
+// Forward level d, step i.: the 2m-point inner DFT of one column with root
+// alpha (shifts and additions only), in shared memory.  Grid: x = column
+// (2M/2m of them), y = operand (0: a, 1: b).  The first level reads the
+// operand words and encodes them (Section 3.2.4) on the fly.
 // ---------------------------------------------------------------------------
-template <int m, int L, int LR, bool FIRST>
-__global__ void __launch_bounds__(kThreads) k_fwd_level(LevelParams prm, Mod<L> md, ModRR<LR> mr) {
+template <int m, int L, bool FIRST>
+__global__ void __launch_bounds__(kThreads) k_dft_fwd(LevelParams prm, Mod<L> md) {
     using G = Geo<m, L>;
     extern __shared__ __align__(16) uint32_t smem[];
-    uint32_t* col = smem;                                   // 2m elements
-    uint32_t* tbuf = smem + G::TWO_M * G::EW;               // per-team product buffers
+    uint32_t* col = smem;
     constexpr int LOG2_TWO_M = ilog2<G::TWO_M>();
     const uint64_t column = blockIdx.x;
     const int op = blockIdx.y;
@@ -304,8 +310,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd_level(LevelParams prm, Mod<L> 
     const uint64_t mu_d = prm.len / G::TWO_M;
     const uint64_t blk = column / mu_d, l = column % mu_d;
     const uint64_t base = blk * prm.len;
-
-    // load the column e_l: element j at position base + j*mu_d + l, into slot bitrev(j)
+    // element j of the column sits at base + j*mu_d + l; load it into slot bitrev(j)
     if constexpr (FIRST) {
         const uint64_t* raw = op ? prm.raw_b : prm.raw_a;
         const int h = m / 2;
@@ -329,48 +334,121 @@ __global__ void __launch_bounds__(kThreads) k_fwd_level(LevelParams prm, Mod<L> 
     }
     __syncthreads();
     dft_dit<m, L>(col, col, 1, G::TWO_M, 1, md);
-
-    // bad multiplications: output v of column l times rho^(v l bp) = alpha^r rho^s
-    Team<m, L> tm;
-    uint32_t* X = tbuf + tm.id * TeamBuf<m, LR>::WORDS;
-    uint32_t* E = X + m * LR;
-    for (int v = tm.id; v < G::TWO_M; v += G::NTEAMS) {
-        const uint64_t e = (uint64_t)v * l * prm.bp;      // < 2M
-        uint32_t* dst = poly + (base + (uint64_t)v * mu_d + l) * G::EW;
-        const uint32_t* x = col + v * G::EW;
-        if (e == 0) {
-#pragma unroll
-            for (int c = 0; c < G::CPL; ++c) {
-                int t = tm.lane + c * G::TEAM;
-                uint32_t y[L];
-                ld_res<L>(y, x + t * L);
-                st_res<L>(dst + t * L, y);
-            }
-            continue;
-        }
-        const int r = (int)(e >> prm.log2_mu_top);
-        const uint64_t sidx = e & (prm.mu_top - 1);
-        stage_x_rr<m, L, LR>(X, x, tm.lane);
-        stage_ext_rr<m, LR>(E, prm.table + sidx * m * LR, mr, tm.lane);
-        __syncwarp(tm.mask);
-        uint32_t out[G::CPL][LR];
-        negacyclic_mul_rr<m, LR>(out, X, E, r, mr, tm.lane);
-#pragma unroll
-        for (int c = 0; c < G::CPL; ++c) {
-            uint32_t o32[L];
-            from_rr<L, LR>(o32, out[c]);
-            st_res<L>(dst + (tm.lane + c * G::TEAM) * L, o32);
-        }
-        __syncwarp(tm.mask);
+    for (int idx = threadIdx.x; idx < G::TWO_M * m; idx += kThreads) {
+        int v = idx / m, t = idx % m;
+        uint32_t x[L];
+        ld_res<L>(x, col + v * G::EW + t * L);
+        st_res<L>(poly + ((base + (uint64_t)v * mu_d + l) * m + t) * L, x);
     }
 }
 
 // ---------------------------------------------------------------------------
-// Last level of both forward transforms, componentwise products scaled by
-// (2M)^-1, and the first level of the backwards transform, fused.  One CTA
-// per block of r = len contiguous elements (len <= 2m, root alpha^(2m/len)).
+// Bad multiplications of level d (Section 3.2.5 ii.): element (v, l) of every
+// block times rho^(+-v l bp) = alpha^r rho^s, in place.  Element-parallel: one
+// team per element, only the (2m-1)(mu_d-1) elements per block whose twiddle
+// is not 1.  Grid: x = element groups, y = operand.
 // ---------------------------------------------------------------------------
+template <int m, int L, int LR, bool INV>
+__global__ void __launch_bounds__(kThreads) k_twiddle(LevelParams prm, ModRR<LR> mr) {
+    using G = Geo<m, L>;
+    extern __shared__ __align__(16) uint32_t smem[];
+    Team<m, L> tm;
+    uint32_t* X = smem + tm.id * TeamBuf<m, LR>::WORDS;
+    uint32_t* E = X + m * LR;
+    uint32_t* poly = prm.data + (blockIdx.y ? prm.poly_words : 0);
+    const uint64_t mu_d = prm.len / G::TWO_M;
+    const uint64_t per_blk = (uint64_t)(G::TWO_M - 1) * (mu_d - 1);
+    const uint64_t total = per_blk * (prm.P2 / prm.len);
+    const uint64_t idx = (uint64_t)blockIdx.x * G::NTEAMS + tm.id;
+    if (idx >= total) return;
+    const uint64_t blk = idx / per_blk, rem = idx % per_blk;
+    const uint64_t v = 1 + rem / (mu_d - 1), l = 1 + rem % (mu_d - 1);
+    uint64_t e = v * l * prm.bp;                          // in (0, 2M)
+    if (INV) e = prm.P2 - e;
+    const int r = (int)(e >> prm.log2_mu_top);
+    const uint64_t sidx = e & (prm.mu_top - 1);
+    uint32_t* x = poly + (blk * prm.len + v * mu_d + l) * G::EW;
+    stage_x_rr<m, L, LR>(X, x, tm.lane);
+    stage_ext_rr<m, LR>(E, prm.table + sidx * m * LR, mr, tm.lane);
+    __syncwarp(tm.mask);
+    uint32_t out[2][LR];
+    negacyclic_mul_rr<m, LR>(out, X, E, r, mr, tm.lane);
+    uint32_t o32[2][L];
+    from_rr<L, LR>(o32[0], out[0]);
+    from_rr<L, LR>(o32[1], out[1]);
+    st_res<L>(x + (2 * tm.lane) * L, o32[0]);
+    st_res<L>(x + (2 * tm.lane + 1) * L, o32[1]);
+}
+
+// Coefficients l and l + m/2 of alpha^r x (x: m residues of L words) in
+// 26-bit limbs: coefficient t of alpha^r x is +-x[(t - r) mod m].
 template <int m, int L, int LR>
+__device__ __forceinline__ void load_shifted_rr(uint32_t (&out)[LR], const uint32_t* x, int t, int r,
+                                                const ModRR<LR>& md) {
+    int src = t - r;
+    bool neg = false;
+    if (src < 0) {
+        src += m;
+        neg = true;
+        if (src < 0) {
+            src += m;
+            neg = false;
+        }
+    }
+    uint32_t v[L];
+    ld_res<L>(v, x + src * L);
+    to_rr<L, LR>(out, v);
+    if (neg) neg_rr<LR>(out, out, md);
+}
+
+// ---------------------------------------------------------------------------
+// Bad multiplications of level d through the evaluation map of R
+// (ntt_rmul.cuh): same element set and grid as k_twiddle, no shared memory.
+// ---------------------------------------------------------------------------
+template <int m, int L, int LR, bool INV>
+__global__ void __launch_bounds__(kThreads) k_twiddle_ntt(LevelParams prm, ModRR<LR> mr) {
+    using G = Geo<m, L>;
+    Team<m, L> tm;
+    uint32_t* poly = prm.data + (blockIdx.y ? prm.poly_words : 0);
+    const uint64_t mu_d = prm.len / G::TWO_M;
+    const uint64_t per_blk = (uint64_t)(G::TWO_M - 1) * (mu_d - 1);
+    const uint64_t total = per_blk * (prm.P2 / prm.len);
+    const uint64_t idx = (uint64_t)blockIdx.x * G::NTEAMS + tm.id;
+    if (idx >= total) return;
+    const uint64_t blk = idx / per_blk, rem = idx % per_blk;
+    const uint64_t v = 1 + rem / (mu_d - 1), l = 1 + rem % (mu_d - 1);
+    uint64_t e = v * l * prm.bp;                          // in (0, 2M)
+    if (INV) e = prm.P2 - e;
+    const int r = (int)(e >> prm.log2_mu_top);
+    const uint64_t sidx = e & (prm.mu_top - 1);
+    uint32_t* x = poly + (blk * prm.len + v * mu_d + l) * G::EW;
+    const int lane = tm.lane;
+    uint32_t lo[LR], hi[LR];
+    load_shifted_rr<m, L, LR>(lo, x, lane, r, mr);
+    load_shifted_rr<m, L, LR>(hi, x, lane + m / 2, r, mr);
+    ntt_forward<m, LR>(lo, hi, lane, tm.mask, prm.ntt_cst, mr);
+    uint32_t t0[LR], t1[LR];
+    const uint32_t* tw = prm.table_eval + (sidx * m + 2 * lane) * LR;
+    ldg_rr<LR>(t0, tw);
+    ldg_rr<LR>(t1, tw + LR);
+    mmul<LR>(lo, lo, t0, mr);
+    mmul<LR>(hi, hi, t1, mr);
+    ntt_backward<m, LR>(lo, hi, lane, tm.mask, prm.ntt_cst, NttLayout<m>::TW_LO, NttLayout<m>::TW_HI, mr);
+    __syncwarp(tm.mask);   // every lane has read its shifted inputs before any write
+    uint32_t o[L];
+    from_rr<L, LR>(o, lo);
+    st_res<L>(x + lane * L, o);
+    from_rr<L, LR>(o, hi);
+    st_res<L>(x + (lane + m / 2) * L, o);
+}
+
+// ---------------------------------------------------------------------------
+// Last level of both forward transforms, componentwise products scaled by
+// (2M)^-1 (Section 3.2.6), and the first level of the backwards transform,
+// fused.  One CTA per block of n = len contiguous elements (len <= 2m, root
+// alpha^(2m/len)).
+// ---------------------------------------------------------------------------
+template <int m, int L, int LR, bool NTT>
 __global__ void __launch_bounds__(kThreads) k_final_pointwise(LevelParams prm, Mod<L> md, ModRR<LR> mr) {
     using G = Geo<m, L>;
     extern __shared__ __align__(16) uint32_t smem[];
@@ -396,25 +474,49 @@ __global__ void __launch_bounds__(kThreads) k_final_pointwise(LevelParams prm, M
     dft_dit<m, L>(sa, sb, 2, n, root, md);
     // componentwise products c_v = a_v * b_v * (2M)^-1
     Team<m, L> tm;
-    uint32_t* X = tbuf + tm.id * TeamBuf<m, LR>::WORDS;
-    uint32_t* E = X + m * LR;
-    uint32_t ks[LR];
-#pragma unroll
-    for (int w = 0; w < LR; ++w) ks[w] = prm.kscale[w];
-    for (int v = tm.id; v < n; v += G::NTEAMS) {
-        stage_x_rr<m, L, LR>(X, sa + v * G::EW, tm.lane);
-        stage_ext_from32<m, L, LR>(E, sb + v * G::EW, mr, tm.lane);
-        __syncwarp(tm.mask);
-        uint32_t out[G::CPL][LR];
-        negacyclic_mul_rr<m, LR>(out, X, E, 0, mr, tm.lane);
-#pragma unroll
-        for (int c = 0; c < G::CPL; ++c) {
-            uint32_t scaled[LR], o32[L];
-            mont_mul_rr<LR>(scaled, out[c], ks, mr);
-            from_rr<L, LR>(o32, scaled);
-            st_res<L>(sa + v * G::EW + (tm.lane + c * G::TEAM) * L, o32);
+    if constexpr (NTT) {
+        for (int v = tm.id; v < n; v += G::NTEAMS) {
+            const int lane = tm.lane;
+            uint32_t alo[LR], ahi[LR], blo[LR], bhi[LR], w[L];
+            ld_res<L>(w, sa + v * G::EW + lane * L);
+            to_rr<L, LR>(alo, w);
+            ld_res<L>(w, sa + v * G::EW + (lane + m / 2) * L);
+            to_rr<L, LR>(ahi, w);
+            ld_res<L>(w, sb + v * G::EW + lane * L);
+            to_rr<L, LR>(blo, w);
+            ld_res<L>(w, sb + v * G::EW + (lane + m / 2) * L);
+            to_rr<L, LR>(bhi, w);
+            ntt_forward<m, LR>(alo, ahi, lane, tm.mask, prm.ntt_cst, mr);
+            ntt_forward<m, LR>(blo, bhi, lane, tm.mask, prm.ntt_cst, mr);
+            mmul<LR>(alo, alo, blo, mr);
+            mmul<LR>(ahi, ahi, bhi, mr);
+            ntt_backward<m, LR>(alo, ahi, lane, tm.mask, prm.ntt_cst, NttLayout<m>::PW_LO, NttLayout<m>::PW_HI, mr);
+            from_rr<L, LR>(w, alo);
+            st_res<L>(sa + v * G::EW + lane * L, w);
+            from_rr<L, LR>(w, ahi);
+            st_res<L>(sa + v * G::EW + (lane + m / 2) * L, w);
         }
-        __syncwarp(tm.mask);
+    } else {
+        uint32_t* X = tbuf + tm.id * TeamBuf<m, LR>::WORDS;
+        uint32_t* E = X + m * LR;
+        uint32_t ks[LR];
+#pragma unroll
+        for (int w = 0; w < LR; ++w) ks[w] = prm.kscale[w];
+        for (int v = tm.id; v < n; v += G::NTEAMS) {
+            stage_x_rr<m, L, LR>(X, sa + v * G::EW, tm.lane);
+            stage_ext_from32<m, L, LR>(E, sb + v * G::EW, mr, tm.lane);
+            __syncwarp(tm.mask);
+            uint32_t out[2][LR];
+            negacyclic_mul_rr<m, LR>(out, X, E, 0, mr, tm.lane);
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                uint32_t scaled[LR], o32[L];
+                mont_mul_rr<LR>(scaled, out[c], ks, mr);
+                from_rr<L, LR>(o32, scaled);
+                st_res<L>(sa + v * G::EW + (2 * tm.lane + c) * L, o32);
+            }
+            __syncwarp(tm.mask);
+        }
     }
     __syncthreads();
     // first backwards level: DFT with root alpha^(-2m/n), natural in, bit-reversed out
@@ -428,15 +530,15 @@ __global__ void __launch_bounds__(kThreads) k_final_pointwise(LevelParams prm, M
 }
 
 // ---------------------------------------------------------------------------
-// Backwards level (decimation in frequency): twiddle by rho^-(v l bp) first,
-// then the 2m-point DFT with root alpha^-1 over the column.
+// Backwards level d, after its twiddles: the 2m-point DFT with root alpha^-1
+// over each column (decimation in frequency: natural in, bit-reversed out),
+// written back in natural element order.
 // ---------------------------------------------------------------------------
-template <int m, int L, int LR>
-__global__ void __launch_bounds__(kThreads) k_inv_level(LevelParams prm, Mod<L> md, ModRR<LR> mr) {
+template <int m, int L>
+__global__ void __launch_bounds__(kThreads) k_dft_inv(LevelParams prm, Mod<L> md) {
     using G = Geo<m, L>;
     extern __shared__ __align__(16) uint32_t smem[];
     uint32_t* col = smem;
-    uint32_t* tbuf = smem + G::TWO_M * G::EW;
     constexpr int LOG2_TWO_M = ilog2<G::TWO_M>();
     const uint64_t column = blockIdx.x;
     uint32_t* poly = prm.data;
@@ -450,29 +552,6 @@ __global__ void __launch_bounds__(kThreads) k_inv_level(LevelParams prm, Mod<L> 
         st_res<L>(col + j * G::EW + t * L, x);
     }
     __syncthreads();
-    Team<m, L> tm;
-    uint32_t* X = tbuf + tm.id * TeamBuf<m, LR>::WORDS;
-    uint32_t* E = X + m * LR;
-    for (int v = tm.id; v < G::TWO_M; v += G::NTEAMS) {
-        uint64_t e = (uint64_t)v * l * prm.bp;
-        if (e == 0) continue;
-        e = prm.P2 - e;
-        const int r = (int)(e >> prm.log2_mu_top);
-        const uint64_t sidx = e & (prm.mu_top - 1);
-        stage_x_rr<m, L, LR>(X, col + v * G::EW, tm.lane);
-        stage_ext_rr<m, LR>(E, prm.table + sidx * m * LR, mr, tm.lane);
-        __syncwarp(tm.mask);
-        uint32_t out[G::CPL][LR];
-        negacyclic_mul_rr<m, LR>(out, X, E, r, mr, tm.lane);
-#pragma unroll
-        for (int c = 0; c < G::CPL; ++c) {
-            uint32_t o32[L];
-            from_rr<L, LR>(o32, out[c]);
-            st_res<L>(col + v * G::EW + (tm.lane + c * G::TEAM) * L, o32);
-        }
-        __syncwarp(tm.mask);
-    }
-    __syncthreads();
     dft_dif<m, L>(col, G::TWO_M, G::TWO_M - 1, md);
     for (int idx = threadIdx.x; idx < G::TWO_M * m; idx += kThreads) {
         int j = idx / m, t = idx % m;
@@ -482,10 +561,14 @@ __global__ void __launch_bounds__(kThreads) k_inv_level(LevelParams prm, Mod<L> 
     }
 }
 
+template <int m, int L>
+constexpr size_t column_smem_bytes() {
+    return sizeof(uint32_t) * (size_t)Geo<m, L>::TWO_M * Geo<m, L>::EW;
+}
+
 template <int m, int L, int LR>
-constexpr size_t level_smem_bytes() {
-    using G = Geo<m, L>;
-    return sizeof(uint32_t) * ((size_t)G::TWO_M * G::EW + (size_t)G::NTEAMS * TeamBuf<m, LR>::WORDS);
+constexpr size_t twiddle_smem_bytes() {
+    return sizeof(uint32_t) * (size_t)Geo<m, L>::NTEAMS * TeamBuf<m, LR>::WORDS;
 }
 
 template <int m, int L, int LR>

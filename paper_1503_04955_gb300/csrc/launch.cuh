@@ -36,6 +36,8 @@ static LevelParams make_level(const dkss_plan_s* pl) {
     lp.u = pl->u;
     lp.log2_mu_top = pl->log2_mu_top;
     for (int i = 0; i < 5; ++i) lp.kscale[i] = pl->kscale[i];
+    lp.table_eval = pl->d_table;
+    lp.ntt_cst = pl->d_ntt;
     return lp;
 }
 
@@ -94,41 +96,69 @@ __global__ void k_unpermute(const uint32_t* src, uint64_t* dst, uint64_t P2, uin
 template <int m, int L, int LR>
 dkss_status prepare(dkss_plan_s* pl) {
     using G = Geo<m, L>;
-    const int lvl = (int)level_smem_bytes<m, L, LR>();
+    const int colb = (int)column_smem_bytes<m, L>();
+    const int twb = (int)twiddle_smem_bytes<m, L, LR>();
     const int fin = (int)final_smem_bytes<m, L, LR>((int)pl->r_last);
     const int fdft = (int)(sizeof(uint32_t) * pl->r_last * G::EW);
     int optin = 0;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device) != cudaSuccess)
         return DKSS_ECUDA;
-    if (lvl > optin || fin > optin) return DKSS_EUNSUPPORTED;
-    if (cudaFuncSetAttribute(k_fwd_level<m, L, LR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lvl) ||
-        cudaFuncSetAttribute(k_fwd_level<m, L, LR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lvl) ||
-        cudaFuncSetAttribute(k_inv_level<m, L, LR>, cudaFuncAttributeMaxDynamicSharedMemorySize, lvl) ||
-        cudaFuncSetAttribute(k_final_pointwise<m, L, LR>, cudaFuncAttributeMaxDynamicSharedMemorySize, fin) ||
+    if (colb > optin || twb > optin || fin > optin) return DKSS_EUNSUPPORTED;
+    if (cudaFuncSetAttribute(k_dft_fwd<m, L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, colb) ||
+        cudaFuncSetAttribute(k_dft_fwd<m, L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, colb) ||
+        cudaFuncSetAttribute(k_dft_inv<m, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, colb) ||
+        cudaFuncSetAttribute(k_twiddle<m, L, LR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, twb) ||
+        cudaFuncSetAttribute(k_twiddle<m, L, LR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, twb) ||
+        cudaFuncSetAttribute(k_final_pointwise<m, L, LR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fin) ||
+        cudaFuncSetAttribute(k_final_pointwise<m, L, LR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fin) ||
         cudaFuncSetAttribute(k_final_dft<m, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, fdft))
         return DKSS_ECUDA;
-    // launches per dkss_mul: forward levels, fused final level, backwards levels, 3 decode
-    pl->launches = pl->col_levels + 1 + pl->col_levels + 3;
+    // launches per dkss_mul: per radix-2m level a DFT and a twiddle launch forward
+    // and backwards, the fused last level, three decode kernels
+    pl->launches = 4 * pl->col_levels + 1 + 3;
+    return DKSS_OK;
+}
+
+// Block length and twiddle base power of radix-2m level d (0-based).
+static inline void level_geometry(const dkss_plan_s* pl, uint32_t d, uint64_t* len, uint64_t* bp) {
+    uint64_t b = 1;
+    for (uint32_t i = 0; i < d; ++i) b *= 2 * pl->m;
+    *bp = b;
+    *len = pl->P2 / b;
+}
+
+template <int m, int L, int LR, bool INV>
+static dkss_status launch_twiddle(dkss_plan_s* pl, LevelParams lp, int operands, cudaStream_t st) {
+    using G = Geo<m, L>;
+    const ModRR<LR> mr = make_modrr<LR>(pl);
+    const uint64_t mu_d = lp.len / G::TWO_M;
+    const uint64_t total = (uint64_t)(G::TWO_M - 1) * (mu_d - 1) * (pl->P2 / lp.len);
+    if (total == 0) return DKSS_OK;
+    dim3 grid((unsigned)((total + G::NTEAMS - 1) / G::NTEAMS), operands);
+    if (pl->flags & DKSS_RMUL_DIRECT)
+        k_twiddle<m, L, LR, INV><<<grid, kThreads, twiddle_smem_bytes<m, L, LR>(), st>>>(lp, mr);
+    else
+        k_twiddle_ntt<m, L, LR, INV><<<grid, kThreads, 0, st>>>(lp, mr);
+    DKSS_CHECK_LAUNCH();
     return DKSS_OK;
 }
 
 template <int m, int L, int LR>
 static dkss_status launch_forward_levels(dkss_plan_s* pl, LevelParams lp, int operands, cudaStream_t st) {
     using G = Geo<m, L>;
-    const size_t smem = level_smem_bytes<m, L, LR>();
     const Mod<L> md = make_mod<L>(pl);
-    const ModRR<LR> mr = make_modrr<LR>(pl);
     dim3 grid((unsigned)(pl->P2 / G::TWO_M), operands);
-    uint64_t len = pl->P2, bp = 1;
     for (uint32_t d = 0; d < pl->col_levels; ++d) {
-        lp.len = len;
-        lp.bp = bp;
-        ProfScope ps(pl, st, d == 0 ? kProfFwdFirst : kProfFwdLevel);
-        if (d == 0) k_fwd_level<m, L, LR, true><<<grid, kThreads, smem, st>>>(lp, md, mr);
-        else k_fwd_level<m, L, LR, false><<<grid, kThreads, smem, st>>>(lp, md, mr);
-        DKSS_CHECK_LAUNCH();
-        len /= G::TWO_M;
-        bp *= G::TWO_M;
+        level_geometry(pl, d, &lp.len, &lp.bp);
+        {
+            ProfScope ps(pl, st, kProfFwdDft);
+            if (d == 0) k_dft_fwd<m, L, true><<<grid, kThreads, column_smem_bytes<m, L>(), st>>>(lp, md);
+            else k_dft_fwd<m, L, false><<<grid, kThreads, column_smem_bytes<m, L>(), st>>>(lp, md);
+            DKSS_CHECK_LAUNCH();
+        }
+        ProfScope ps(pl, st, kProfFwdTwiddle);
+        dkss_status s = launch_twiddle<m, L, LR, false>(pl, lp, operands, st);
+        if (s != DKSS_OK) return s;
     }
     return DKSS_OK;
 }
@@ -145,17 +175,25 @@ dkss_status run_mul(dkss_plan_s* pl, const uint64_t* a, const uint64_t* b, uint6
     if (s != DKSS_OK) return s;
     lp.len = pl->r_last;
     {
-    ProfScope ps(pl, st, kProfFinal);
-    k_final_pointwise<m, L, LR><<<(unsigned)(pl->P2 / pl->r_last), kThreads, final_smem_bytes<m, L, LR>((int)pl->r_last), st>>>(lp, md, mr);
-    DKSS_CHECK_LAUNCH();
+        ProfScope ps(pl, st, kProfFinal);
+        const unsigned blocks = (unsigned)(pl->P2 / pl->r_last);
+        if (pl->flags & DKSS_RMUL_DIRECT)
+            k_final_pointwise<m, L, LR, false><<<blocks, kThreads, final_smem_bytes<m, L, LR>((int)pl->r_last), st>>>(
+                lp, md, mr);
+        else
+            k_final_pointwise<m, L, LR, true><<<blocks, kThreads, final_smem_bytes<m, L, LR>((int)pl->r_last), st>>>(
+                lp, md, mr);
+        DKSS_CHECK_LAUNCH();
     }
     for (int d = (int)pl->col_levels - 1; d >= 0; --d) {
-        ProfScope ps(pl, st, kProfInvLevel);
-        uint64_t bp = 1;
-        for (int i = 0; i < d; ++i) bp *= G::TWO_M;
-        lp.len = pl->P2 / bp;
-        lp.bp = bp;
-        k_inv_level<m, L, LR><<<(unsigned)(pl->P2 / G::TWO_M), kThreads, level_smem_bytes<m, L, LR>(), st>>>(lp, md, mr);
+        level_geometry(pl, (uint32_t)d, &lp.len, &lp.bp);
+        {
+            ProfScope ps(pl, st, kProfInvTwiddle);
+            s = launch_twiddle<m, L, LR, true>(pl, lp, 1, st);
+            if (s != DKSS_OK) return s;
+        }
+        ProfScope ps(pl, st, kProfInvDft);
+        k_dft_inv<m, L><<<(unsigned)(pl->P2 / G::TWO_M), kThreads, column_smem_bytes<m, L>(), st>>>(lp, md);
         DKSS_CHECK_LAUNCH();
     }
     DecodeParams dp{};

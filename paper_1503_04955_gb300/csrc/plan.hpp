@@ -27,7 +27,8 @@ struct dkss_plan_s {
     dkss_host::Roots roots;
     // device memory owned by the plan
     int device = 0;
-    uint32_t* d_table = nullptr;  // rho^s (s < mu_top), Montgomery form
+    uint32_t* d_table = nullptr;  // rho^s (s < mu_top): coefficients, or evaluations (default)
+    uint32_t* d_ntt = nullptr;    // constants of the transform in R
     uint32_t* d_work = nullptr;   // two transformed polynomials
     uint64_t poly_words = 0;
     uint32_t* d_agg = nullptr;    // carry-scan tile aggregates
@@ -47,7 +48,14 @@ struct dkss_plan_s {
 
 namespace dkss {
 // Kernel-group kinds reported by dkss_profile_read.
-enum ProfKind { kProfFwdFirst = 0, kProfFwdLevel = 1, kProfFinal = 2, kProfInvLevel = 3, kProfDecode = 4 };
+enum ProfKind {
+    kProfFwdDft = 0,      // forward inner DFTs (first level encodes)
+    kProfFwdTwiddle = 1,  // forward bad multiplications
+    kProfFinal = 2,       // last forward level + products + first backwards level
+    kProfInvTwiddle = 3,  // backwards bad multiplications
+    kProfInvDft = 4,      // backwards inner DFTs
+    kProfDecode = 5       // decoding and carry scan
+};
 
 // Record an event pair around a kernel group when the plan profiles.
 struct ProfScope {

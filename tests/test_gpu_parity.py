@@ -44,10 +44,10 @@ def oc():
     return oracle_c
 
 
-def check_product(dk, oc, cfg, A, B, with_oracle=True, with_forward=True):
+def check_product(dk, oc, cfg, A, B, with_oracle=True, with_forward=True, flags=0):
     par = o.Params(*cfg).check()
     roots = o.compute_roots(par)
-    with dk.Plan(*cfg) as plan:
+    with dk.Plan(*cfg, flags=flags) as plan:
         c = plan.mul(to_dev(A), to_dev(B))
         fwd = plan.forward(to_dev(A)) if with_forward else None
         plan.sync_status()
@@ -61,18 +61,25 @@ def check_product(dk, oc, cfg, A, B, with_oracle=True, with_forward=True):
             assert residues(fwd_host) == residues(dumps["a_hat"])
 
 
+# R-multiplications through the evaluation map of R (default) and by the
+# direct negacyclic convolution (DKSS_RMUL_DIRECT)
+FORMS = [0, 16]
+
+
+@pytest.mark.parametrize("flags", FORMS)
 @pytest.mark.parametrize("cfg", SMALL)
-def test_small_configs_random(dk, oc, cfg):
+def test_small_configs_random(dk, oc, cfg, flags):
     A, B = syn.operand_pair(cfg[0], 1234, product=SMALL.index(cfg))
-    check_product(dk, oc, cfg, A, B)
+    check_product(dk, oc, cfg, A, B, flags=flags)
 
 
+@pytest.mark.parametrize("flags", FORMS)
 @pytest.mark.parametrize("kind", ["zero", "one", "ones", "top"])
 @pytest.mark.parametrize("cfg", [SMALL[0], SMALL[4], SMALL[6]])
-def test_small_configs_special_operands(dk, oc, cfg, kind):
+def test_small_configs_special_operands(dk, oc, cfg, kind, flags):
     A = syn.special_operand(cfg[0], kind)
     B = syn.special_operand(cfg[0], "ones")
-    check_product(dk, oc, cfg, A, B, with_forward=(kind == "ones"))
+    check_product(dk, oc, cfg, A, B, with_forward=(kind == "ones"), flags=flags)
 
 
 def test_65536_bits_full_parity(dk, oc):
@@ -87,10 +94,11 @@ def test_65536_bits_all_ones_reaches_bound(dk, oc):
     check_product(dk, oc, cfg, A, A)
 
 
-def test_2p24_bits_full_parity(dk, oc):
+@pytest.mark.parametrize("flags", FORMS)
+def test_2p24_bits_full_parity(dk, oc, flags):
     cfg = syn.workload_params("dkss_2p24b")
     A, B = syn.operand_pair(cfg[0], syn.config_seed(1))
-    check_product(dk, oc, cfg, A, B)
+    check_product(dk, oc, cfg, A, B, flags=flags)
 
 
 def test_mul_host_matches_device_path(dk):
@@ -128,11 +136,11 @@ def test_aliasing_output_rejected(dk):
         assert e.value.code == 1
 
 
-def large_checks(dk, oc, name, n_alpha_points):
+def large_checks(dk, oc, name, n_alpha_points, flags=0):
     cfg = syn.workload_params(name)
     par = o.Params(*cfg).check()
     A, B = syn.operand_pair(par.n_bits, syn.config_seed(syn.WORKLOADS[name]["index"]))
-    with dk.Plan(*cfg) as plan:
+    with dk.Plan(*cfg, flags=flags) as plan:
         da, db = to_dev(A), to_dev(B)
         c = plan.mul(da, db)
         plan.sync_status()
@@ -152,8 +160,9 @@ def large_checks(dk, oc, name, n_alpha_points):
         assert residues(row) == oc.fft_alpha_point(A, par, k)
 
 
-def test_2p28_bits_properties(dk, oc):
-    large_checks(dk, oc, "dkss_2p28b", 8)
+@pytest.mark.parametrize("flags", FORMS)
+def test_2p28_bits_properties(dk, oc, flags):
+    large_checks(dk, oc, "dkss_2p28b", 8, flags)
 
 
 def test_2p32_bits_properties(dk, oc):
