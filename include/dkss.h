@@ -152,6 +152,43 @@ dkss_status dkss_plan_rho(uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, u
  */
 dkss_status dkss_profile_read(dkss_plan_t plan, double* ms, uint64_t* counts, size_t n);
 
+/*
+ * Largest product dkss_decode_static handles: its scratch holds one word per
+ * tile of 2048 32-bit output windows, so 2*ceil(N/64) <= 2^27 words (N <= 2^33).
+ */
+#define DKSS_DECODE_STATIC_MAX_TILES 262144
+
+/*
+ * Decoding and carry propagation (the last step of a product) that allocates
+ * nothing.  The thesis has no counterpart: this exists for callers that cannot
+ * allocate device memory at the time of the call -- for example code running
+ * while a stream is being captured into a CUDA graph, where cudaMalloc and
+ * cudaFree are not allowed, or a real-time loop whose memory is fixed before
+ * it starts.  They still need the carry scan's scratch; here it is a
+ * file-scope device array of DKSS_DECODE_STATIC_MAX_TILES + 1 words (1 MiB)
+ * that every GPU which loads the library holds until the process exits.
+ *
+ *   c       device pointer: the product polynomial, 2M elements x m residues
+ *           x L 32-bit limbs (word (e*m + t)*L + l), natural order, each
+ *           residue the exact nonnegative coefficient (below 2^(32L)); the
+ *           layout dkss_mul uses internally after the backwards transform.
+ *   n_bits  N of the operands; out receives 2*ceil(N/64) words (device).
+ *   M, m, u the encoding parameters (powers of two M, m with m <= 64,
+ *           u <= 32, M*(m/2)*u >= N); L in [2, 4].
+ * Result: out = sum over elements e and residues t of c[e][t] * 2^(u(e*m/2+t)),
+ * the value decoded in Section 3.2.8 of a product of two N-bit operands.
+ * Queued on `stream`.  Errors: DKSS_EINVAL (bad argument), DKSS_EUNSUPPORTED
+ * (N beyond the static scratch), DKSS_ECUDA.  The first call on a device looks
+ * up the scratch array's device address (cudaGetSymbolAddress), so make one
+ * call on each device before capturing a stream.  All calls share the scratch:
+ * calls whose work overlaps on the GPU (different streams, or different host
+ * threads) race and must be serialised by the caller.  A carry out of 2N bits
+ * (impossible for a true product) is recorded in the scratch's status word
+ * and not reported.
+ */
+dkss_status dkss_decode_static(const uint32_t* c, uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, uint32_t L,
+                               uint64_t* out, dkss_stream_t stream);
+
 /* Kernel launches one dkss_mul call queues (for launch accounting). */
 uint32_t dkss_plan_launches(dkss_plan_t plan);
 

@@ -23,7 +23,7 @@ FORM_INT8TC = 2
 # Names exported by libdkss.so (include/dkss.h)
 EXPORTS = ["dkss_plan", "dkss_mul", "dkss_mul_host", "dkss_forward", "dkss_mul_batch", "dkss_plan_info",
            "dkss_plan_rho", "dkss_profile_read", "dkss_plan_launches", "dkss_sync_status", "dkss_plan_destroy",
-           "dkss_status_str"]
+           "dkss_status_str", "dkss_decode_static"]
 FORM_PROFILE = 4
 RMUL_DIRECT = 16
 PROFILE_KINDS = ["fwd_dft", "fwd_twiddle", "final_pointwise", "inv_twiddle", "inv_dft", "decode"]
@@ -60,6 +60,8 @@ def load():
     lib.dkss_plan_info.argtypes = [P, P, sz, P]
     lib.dkss_plan_rho.argtypes = [u64, u64, u32, u32, u64, u32, P, P, sz]
     lib.dkss_profile_read.argtypes = [P, P, P, sz]
+    lib.dkss_decode_static.argtypes = [P, u64, u64, u32, u32, u32, P, P]
+    lib.dkss_decode_static.restype = ctypes.c_int
     lib.dkss_plan_launches.argtypes = [P]
     lib.dkss_plan_launches.restype = u32
     lib.dkss_sync_status.argtypes = [P, P]
@@ -199,3 +201,20 @@ class Plan:
 
     def sync_status(self, stream=None):
         _check(load().dkss_sync_status(self._h, _stream_handle(stream)), "device status")
+
+
+def decode_static(c, n_bits, M, m, u, L, out=None, stream=None):
+    """dkss_decode_static: product words from a product polynomial without any
+    allocation inside the library.  c: CUDA tensor of 2M*m*L 32-bit words
+    (int32/uint32); out: CUDA tensor of 2*ceil(N/64) 64-bit words."""
+    import torch
+    words = (n_bits + 63) // 64
+    if out is None:
+        out = torch.empty(2 * words, dtype=torch.int64, device=c.device)
+    if not c.is_cuda or c.element_size() != 4 or not c.is_contiguous() or c.numel() != 2 * M * m * L:
+        raise ValueError("c must be a contiguous CUDA tensor of 2M*m*L 32-bit words")
+    if not out.is_cuda or out.element_size() != 8 or not out.is_contiguous() or out.numel() != 2 * words:
+        raise ValueError("out must be a contiguous CUDA tensor of 2*ceil(N/64) 64-bit words")
+    _check(load().dkss_decode_static(c.data_ptr(), n_bits, M, m, u, L, out.data_ptr(), _stream_handle(stream)),
+           "dkss_decode_static")
+    return out
