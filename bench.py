@@ -45,6 +45,10 @@ L2_FLUSH_BYTES = 256 << 20
 SM_COUNT_GB300 = 152
 IMAD_PER_SM_PER_CLK = 64          # 32-bit integer multiply-add lanes per SM per clock
 SM_MAX_MHZ = 2070.0
+HBM_GBS = 6782.1                  # measured copy bandwidth of the GB300s (MEASURED_PEAKS.json)
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture
+# (profiles/stage_kernels_dkss_2p24b.md); valid only for the kernel version captured.
+NCU_TRAFFIC_BYTES = {("dkss_2p24b", "ntt", "fwd_twiddle"): 65.9e6}
 
 
 def parse_args():
@@ -260,10 +264,31 @@ def run_ours(args):
     avg_launch_ms = dom_ms / max(1, dom_n)
     achieved = ops_per_launch / (avg_launch_ms * 1e-3) / 1e12
     peak = SM_COUNT_GB300 * IMAD_PER_SM_PER_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    # memory-bound groups: algorithmic bytes = one read and one write of the
+    # polynomials they pass over (DFT levels), or of the product polynomial and
+    # the product words (decode)
+    poly_bytes = info["P2"] * cfg[2] * info["L"] * 4
+    mem_bytes = {"fwd_dft": 2 * 2 * poly_bytes * (info["levels"] - 1),
+                 "inv_dft": 2 * poly_bytes * (info["levels"] - 1),
+                 "decode": poly_bytes + 4 * A.nbytes}
+    stages = {}
+    for k, (ms_tot, _) in prof.items():
+        ms = ms_tot / args.steps
+        if ms <= 0:
+            continue
+        if k in work:
+            a = work[k][0] / (ms * 1e-3) / 1e12
+            stages[k] = {"bound": "alu", "ms": round(ms, 4), "achieved": round(a, 3), "unit": "TIMAD/s",
+                         "frac": round(a / peak, 4)}
+        elif k in mem_bytes:
+            a = mem_bytes[k] / (ms * 1e-3) / 1e9
+            stages[k] = {"bound": "hbm", "ms": round(ms, 4), "achieved": round(a, 1), "unit": "GB/s",
+                         "frac": round(a / HBM_GBS, 4)}
     roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 3),
-                "unit": "TIMAD/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "unit": "TIMAD/s", "frac": round(achieved / peak, 4),
+                "traffic": NCU_TRAFFIC_BYTES.get((args.workload, args.form, dom)),
+                "stages": stages,
                 "avg_launch_ms": round(avg_launch_ms, 4), "ops_per_launch": int(ops_per_launch),
-                "stage_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items()},
                 "peak_basis": "152 SMs x 64 IMAD/clk x 2070 MHz (recipe unit counts and max clock)"}
 
     cpu = None
