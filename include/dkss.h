@@ -115,10 +115,53 @@ typedef struct {
     uint64_t n_bits;
 } dkss_job;
 
+typedef struct dkss_batch_s* dkss_batch_t;
+
+enum {
+    DKSS_BATCH_RULE = 32,     /* size-class parameters by rule instead of measurement */
+    DKSS_BATCH_NO_GRAPH = 64  /* launch the persistent kernel directly, not from a graph */
+};
+
 /*
- * Multiply `count` independent pairs of any sizes in one call (thesis
- * Section 3.2 applied per job).  Reserved: returns DKSS_EUNSUPPORTED in this
- * build.
+ * Plan a batch of `count` independent products whose operands have the given
+ * bit lengths (each job is Section 3.2 on its own).  Jobs are grouped into
+ * size classes (operands up to the next power of two, at least 2^12 bits)
+ * that share the ring m = 32, p = 65537, z = 5 and differ in M and u; each
+ * class's (M, u) comes from an autotuner that times one product of the class
+ * with u = 32 and with u = 16 on the current device (cached per device and
+ * class; DKSS_BATCH_RULE takes the largest valid u instead, the thesis's own
+ * rule of Section 4.1).  The plan owns every job's workspace and the class
+ * tables, and records one cooperative persistent-kernel launch in a CUDA
+ * graph.  Operands up to 2^21 bits; count <= 2^20.
+ * Errors: DKSS_EINVAL, DKSS_EUNSUPPORTED (operand too long), DKSS_ENOMEM,
+ * DKSS_ECUDA.  On error *batch is NULL.
+ */
+dkss_status dkss_batch_plan(dkss_batch_t* batch, const uint64_t* n_bits, size_t count, uint32_t flags);
+
+/*
+ * Run a planned batch: jobs is a host array of count entries whose n_bits
+ * match the plan, in order; a, b, out are device pointers as for dkss_mul.
+ * Copies the job pointers to the device (host-to-device copy on `stream`)
+ * and launches the graph: one persistent kernel for all jobs.  Asynchronous;
+ * calls on one batch plan must not overlap.  Errors: DKSS_EINVAL, DKSS_ECUDA.
+ */
+dkss_status dkss_batch_run(dkss_batch_t batch, const dkss_job* jobs, dkss_stream_t stream);
+
+/*
+ * Parameters chosen for job `job`: params[0..8] = M, m, u, p, z, the class's
+ * largest operand bits, transform levels, persistent grid size, 1 if the
+ * launch is a graph.  n is the length of params.
+ */
+dkss_status dkss_batch_job_params(dkss_batch_t batch, size_t job, uint64_t* params, size_t n);
+
+/* Free a batch plan (waits for the device).  NULL is a no-op. */
+dkss_status dkss_batch_destroy(dkss_batch_t batch);
+
+/*
+ * Multiply `count` independent pairs of any sizes in one call: plans a batch
+ * for these lengths (kept and reused while the lengths and flags stay the
+ * same) and runs it.  jobs: host array.  Errors: as dkss_batch_plan and
+ * dkss_batch_run.
  */
 dkss_status dkss_mul_batch(const dkss_job* jobs, size_t count, uint32_t flags, dkss_stream_t stream);
 

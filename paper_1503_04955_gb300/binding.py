@@ -23,7 +23,8 @@ FORM_INT8TC = 2
 # Names exported by libdkss.so (include/dkss.h)
 EXPORTS = ["dkss_plan", "dkss_mul", "dkss_mul_host", "dkss_forward", "dkss_mul_batch", "dkss_plan_info",
            "dkss_plan_rho", "dkss_profile_read", "dkss_plan_launches", "dkss_sync_status", "dkss_plan_destroy",
-           "dkss_status_str", "dkss_decode_static"]
+           "dkss_status_str", "dkss_decode_static", "dkss_batch_plan", "dkss_batch_run", "dkss_batch_job_params",
+           "dkss_batch_destroy"]
 FORM_PROFILE = 4
 RMUL_DIRECT = 16
 PROFILE_KINDS = ["fwd_dft", "fwd_twiddle", "final_pointwise", "inv_twiddle", "inv_dft", "decode"]
@@ -218,3 +219,85 @@ def decode_static(c, n_bits, M, m, u, L, out=None, stream=None):
     _check(load().dkss_decode_static(c.data_ptr(), n_bits, M, m, u, L, out.data_ptr(), _stream_handle(stream)),
            "dkss_decode_static")
     return out
+
+
+BATCH_RULE = 32
+BATCH_NO_GRAPH = 64
+
+
+class _Job(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_void_p), ("b", ctypes.c_void_p), ("out", ctypes.c_void_p), ("n_bits", ctypes.c_uint64)]
+
+
+def _load_batch():
+    lib = load()
+    if not getattr(lib, "_batch_ready", False):
+        P = ctypes.c_void_p
+        lib.dkss_batch_plan.argtypes = [ctypes.POINTER(P), P, ctypes.c_size_t, ctypes.c_uint32]
+        lib.dkss_batch_run.argtypes = [P, P, P]
+        lib.dkss_batch_job_params.argtypes = [P, ctypes.c_size_t, P, ctypes.c_size_t]
+        lib.dkss_batch_destroy.argtypes = [P]
+        lib.dkss_mul_batch.argtypes = [P, ctypes.c_size_t, ctypes.c_uint32, P]
+        for f in (lib.dkss_batch_plan, lib.dkss_batch_run, lib.dkss_batch_job_params, lib.dkss_batch_destroy,
+                  lib.dkss_mul_batch):
+            f.restype = ctypes.c_int
+        lib._batch_ready = True
+    return lib
+
+
+def _jobs_array(a_list, b_list, out_list, n_bits):
+    jobs = (_Job * len(n_bits))()
+    for j, (a, b, o, n) in enumerate(zip(a_list, b_list, out_list, n_bits)):
+        jobs[j].a, jobs[j].b, jobs[j].out, jobs[j].n_bits = a.data_ptr(), b.data_ptr(), o.data_ptr(), int(n)
+    return jobs
+
+
+class Batch:
+    """A planned batch of products of uneven sizes (dkss_batch_plan)."""
+
+    PARAM_NAMES = ["M", "m", "u", "p", "z", "class_bits", "levels", "grid", "graph"]
+
+    def __init__(self, n_bits, flags=0):
+        lib = _load_batch()
+        self.n_bits = [int(n) for n in n_bits]
+        arr = (ctypes.c_uint64 * len(self.n_bits))(*self.n_bits)
+        h = ctypes.c_void_p()
+        _check(lib.dkss_batch_plan(ctypes.byref(h), ctypes.cast(arr, ctypes.c_void_p), len(self.n_bits), flags),
+               "dkss_batch_plan")
+        self._h = h
+
+    def job_params(self, j):
+        v = np.zeros(9, dtype=np.uint64)
+        _check(_load_batch().dkss_batch_job_params(self._h, j, v.ctypes.data, 9), "dkss_batch_job_params")
+        return dict(zip(self.PARAM_NAMES, [int(x) for x in v]))
+
+    def run(self, a_list, b_list, out_list, stream=None):
+        """out_list[j] = a_list[j] * b_list[j] (CUDA tensors of 64-bit words)."""
+        jobs = _jobs_array(a_list, b_list, out_list, self.n_bits)
+        self._jobs = jobs   # keep alive until the host-to-device copy is done
+        _check(_load_batch().dkss_batch_run(self._h, ctypes.cast(jobs, ctypes.c_void_p), _stream_handle(stream)),
+               "dkss_batch_run")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _load_batch().dkss_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def mul_batch(a_list, b_list, out_list, n_bits, flags=0, stream=None):
+    """dkss_mul_batch: plan (cached while the lengths repeat) and run in one call."""
+    jobs = _jobs_array(a_list, b_list, out_list, n_bits)
+    _check(_load_batch().dkss_mul_batch(ctypes.cast(jobs, ctypes.c_void_p), len(n_bits), flags,
+                                        _stream_handle(stream)), "dkss_mul_batch")

@@ -1,0 +1,137 @@
+// Many products of uneven sizes in one persistent kernel launch.
+//
+// A batch groups its jobs into size classes that share the residue ring (m,
+// p, z, hence L and LR) and differ in M and u.  The persistent kernel walks a
+// host-built list of stages (forward inner DFTs and twiddles per level, the
+// fused last level with the componentwise products, backwards twiddles and
+// DFTs per level, decode tiles, carry scan, carry fix-up).  In each stage
+// every CTA takes work items -- a column, a group of elements, a block, a
+// tile -- from all jobs at once, then the grid synchronises (a cooperative
+// launch keeps every CTA resident, so the grid barrier cannot wait on a CTA
+// that is not running).  Each job's stages keep the order of a single
+// product; a job with fewer levels simply has no items in the others.
+#pragma once
+#include <cooperative_groups.h>
+
+#include <cstdint>
+
+#include "decode.cuh"
+#include "dkss_kernels.cuh"
+
+namespace dkss {
+
+enum BatchStageType : uint32_t {
+    kStFwdDft = 0,
+    kStFwdTwiddle = 1,
+    kStFinal = 2,
+    kStInvTwiddle = 3,
+    kStInvDft = 4,
+    kStDecTiles = 5,
+    kStDecScan = 6,
+    kStDecFix = 7
+};
+
+// Per-job parameters (device copy).  lp.len / lp.bp are set per stage.
+struct BatchJob {
+    LevelParams lp;
+    DecodeParams dp;
+    uint32_t col_levels;
+    uint32_t r_last;
+};
+
+struct BatchStage {
+    uint32_t type;
+    uint32_t level;          // radix-2m level for DFT / twiddle stages
+    uint64_t total;          // work items over all jobs
+    const uint64_t* offs;    // count + 1 exclusive prefix sums of per-job items
+};
+
+// Work items of one job in one stage (host and device agree on this count).
+template <int m>
+__host__ __device__ inline uint64_t batch_items(uint32_t type, uint32_t level, uint64_t P2, uint32_t col_levels,
+                                                uint64_t r_last, uint64_t n_tiles, int nteams) {
+    const uint64_t cols = P2 / (2 * m);
+    uint64_t len = P2;
+    for (uint32_t i = 0; i < level; ++i) len /= 2 * m;
+    const uint64_t mu_d = len / (2 * m);
+    const uint64_t tw = (uint64_t)(2 * m - 1) * (mu_d > 0 ? mu_d - 1 : 0) * (len ? P2 / len : 0);
+    const uint64_t groups = (tw + nteams - 1) / nteams;
+    switch (type) {
+        case kStFwdDft: return level < col_levels ? 2 * cols : 0;
+        case kStFwdTwiddle: return level < col_levels ? 2 * groups : 0;
+        case kStFinal: return P2 / r_last;
+        case kStInvTwiddle: return level < col_levels ? groups : 0;
+        case kStInvDft: return level < col_levels ? cols : 0;
+        case kStDecTiles: return n_tiles;
+        case kStDecScan: return 1;
+        case kStDecFix: return (n_tiles + kThreads - 1) / kThreads;
+    }
+    return 0;
+}
+
+template <int m, int L, int LR>
+__global__ void __launch_bounds__(kThreads, 2) k_batch(const BatchJob* __restrict__ jobs, const BatchStage* __restrict__ stages,
+                                                    uint32_t n_stages, uint32_t count, Mod<L> md, ModRR<LR> mr) {
+    using G = Geo<m, L>;
+    namespace cg = cooperative_groups;
+    extern __shared__ __align__(16) uint32_t smem[];
+    cg::grid_group grid = cg::this_grid();
+    for (uint32_t s = 0; s < n_stages; ++s) {
+        const BatchStage st = stages[s];
+        for (uint64_t item = blockIdx.x; item < st.total; item += gridDim.x) {
+            uint32_t lo = 0, hi = count;   // last job with offs[job] <= item
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) / 2;
+                if (st.offs[mid] <= item) lo = mid;
+                else hi = mid;
+            }
+            const BatchJob& jb = jobs[lo];
+            const uint64_t local = item - st.offs[lo];
+            LevelParams lp = jb.lp;
+            uint64_t bp = 1;
+            for (uint32_t i = 0; i < st.level; ++i) bp *= G::TWO_M;
+            lp.bp = bp;
+            lp.len = lp.P2 / bp;
+            const uint64_t cols = lp.P2 / G::TWO_M;
+            switch (st.type) {
+                case kStFwdDft:
+                    if (st.level == 0) dft_fwd_column<m, L, true>(lp, md, smem, local % cols, (int)(local / cols));
+                    else dft_fwd_column<m, L, false>(lp, md, smem, local % cols, (int)(local / cols));
+                    break;
+                case kStFwdTwiddle:
+                case kStInvTwiddle: {
+                    const uint64_t mu_d = lp.len / G::TWO_M;
+                    const uint64_t tw = (uint64_t)(G::TWO_M - 1) * (mu_d - 1) * (lp.P2 / lp.len);
+                    const uint64_t groups = (tw + G::NTEAMS - 1) / G::NTEAMS;
+                    if (st.type == kStFwdTwiddle)
+                        twiddle_ntt_group<m, L, LR, false>(lp, mr, local % groups, (int)(local / groups));
+                    else
+                        twiddle_ntt_group<m, L, LR, true>(lp, mr, local, 0);
+                    break;
+                }
+                case kStFinal:
+                    lp.len = jb.r_last;
+                    final_block<m, L, LR, true>(lp, md, mr, smem, local);
+                    break;
+                case kStInvDft:
+                    dft_inv_column<m, L>(lp, md, smem, local);
+                    break;
+                case kStDecTiles:
+                    if (jb.dp.u == 32) decode_tile_aligned<L, 1>(jb.dp, local);
+                    else if (jb.dp.u == 16) decode_tile_aligned<L, 2>(jb.dp, local);
+                    else decode_tile<L>(jb.dp, local);
+                    break;
+                case kStDecScan:
+                    decode_scan_block<kThreads>(jb.dp);
+                    break;
+                case kStDecFix:
+                    decode_fix_tile(jb.dp, local * kThreads + threadIdx.x);
+                    break;
+            }
+            __syncthreads();   // shared memory is reused by the next item
+        }
+        grid.sync();
+    }
+}
+
+}  // namespace dkss

@@ -13,7 +13,7 @@ using dkss_host::MontCtx;
 using dkss_host::Relem;
 using dkss_host::u128;
 
-namespace {
+namespace dkss_planning {
 
 bool is_pow2(uint64_t x) { return x && !(x & (x - 1)); }
 
@@ -50,6 +50,11 @@ bool below_pow2(const uint64_t t[5], int bits) {
     return true;
 }
 
+}  // namespace dkss_planning
+
+namespace {
+using namespace dkss_planning;
+
 typedef dkss_status (*run_mul_fn)(dkss_plan_s*, const uint64_t*, const uint64_t*, uint64_t*, cudaStream_t);
 typedef dkss_status (*run_fwd_fn)(dkss_plan_s*, const uint64_t*, uint64_t*, cudaStream_t);
 typedef dkss_status (*prep_fn)(dkss_plan_s*);
@@ -75,6 +80,10 @@ bool lookup(uint32_t m, uint32_t L, uint32_t LR, Kernels* k) {
 #undef DKSS_CASE
     return false;
 }
+
+}  // namespace
+
+namespace dkss_planning {
 
 // Everything of a plan that needs no device: parameter checks (Section 3.2
 // steps 1-2), roots (Section 3.2.3) and the limb layout.
@@ -284,6 +293,11 @@ void build_eval_table(const dkss_plan_s* pl, std::vector<uint32_t>& out) {
     for (auto& t : th) t.join();
 }
 
+}  // namespace dkss_planning
+
+namespace {
+using namespace dkss_planning;
+
 void free_device(dkss_plan_s* pl) {
     cudaFree(pl->d_table);
     cudaFree(pl->d_work);
@@ -406,11 +420,6 @@ dkss_status dkss_forward(dkss_plan_t pl, const uint64_t* a, uint64_t* out, dkss_
     Kernels k;
     if (!lookup(pl->m, pl->L, pl->LR, &k)) return DKSS_EUNSUPPORTED;
     return k.fwd(pl, a, out, (cudaStream_t)stream);
-}
-
-dkss_status dkss_mul_batch(const dkss_job* jobs, size_t count, uint32_t flags, dkss_stream_t stream) {
-    (void)jobs; (void)count; (void)flags; (void)stream;
-    return DKSS_EUNSUPPORTED;
 }
 
 dkss_status dkss_plan_info(dkss_plan_t pl, uint64_t* consts, size_t n_consts, uint64_t* rho_out) {

@@ -128,7 +128,7 @@ __device__ GP gp_block_scan(GP x, GP& total) {
 // Carry resolution inside a tile and the tile aggregate: wv are the thread's
 // window values, gbit/pbit its generate/propagate bits (bit w = window j0+w).
 __device__ __forceinline__ void decode_tile_finish(const DecodeParams& p, uint64_t j0, const uint32_t (&wv)[kDecWPT],
-                                                   uint32_t gbit, uint32_t pbit) {
+                                                   uint32_t gbit, uint32_t pbit, uint64_t tile) {
     // thread aggregate: carry out with carry-in 0, and whether a carry-in passes through
     uint32_t c = 0;
 #pragma unroll
@@ -151,12 +151,12 @@ __device__ __forceinline__ void decode_tile_finish(const DecodeParams& p, uint64
         for (int w = 0; w < kDecWPT; ++w)
             if (j0 + w < p.n_windows) p.out[j0 + w] = o[w];
     }
-    if (threadIdx.x == 0) p.agg[blockIdx.x] = total.g | (total.p << 1);
+    if (threadIdx.x == 0) p.agg[tile] = total.g | (total.p << 1);
 }
 
 template <int L>
-__global__ void __launch_bounds__(kDecThreads) k_decode_tiles(DecodeParams p) {
-    const uint64_t j0 = (uint64_t)blockIdx.x * kDecTile + (uint64_t)threadIdx.x * kDecWPT;
+__device__ __forceinline__ void decode_tile(const DecodeParams& p, uint64_t tile) {
+    const uint64_t j0 = tile * kDecTile + (uint64_t)threadIdx.x * kDecWPT;
     uint64_t S_prev = j0 >= 1 && j0 - 1 < p.n_windows ? window_sum<L>(p, j0 - 1) : 0;
     uint32_t wv[kDecWPT], gbit = 0, pbit = 0;
 #pragma unroll
@@ -169,19 +169,24 @@ __global__ void __launch_bounds__(kDecThreads) k_decode_tiles(DecodeParams p) {
         pbit |= (uint32_t)(wv[w] == 0xffffffffu) << w;
         S_prev = S;
     }
-    decode_tile_finish(p, j0, wv, gbit, pbit);
+    decode_tile_finish(p, j0, wv, gbit, pbit, tile);
+}
+
+template <int L>
+__global__ void __launch_bounds__(kDecThreads) k_decode_tiles(DecodeParams p) {
+    decode_tile<L>(p, blockIdx.x);
 }
 
 // Same tile kernel for u = 32/R (R = 1, 2): digit k sits at bit u*k, so window
 // j takes limb t of the digits k = R(j - t) + s, shifted by u*s bits.  A thread
 // loads each digit its 9 windows (j0-1 .. j0+7) touch once into registers.
 template <int L, int R>
-__global__ void __launch_bounds__(kDecThreads) k_decode_tiles_aligned(DecodeParams p) {
+__device__ __forceinline__ void decode_tile_aligned(const DecodeParams& p, uint64_t tile) {
     constexpr int U = 32 / R;
     constexpr int T = L + 2;                 // limbs a shifted digit can reach
     constexpr int NW = kDecWPT + 1;          // windows j0-1 .. j0+7
     constexpr int NK = R * (NW + T - 1);     // digits touching them
-    const int64_t j0 = (int64_t)blockIdx.x * kDecTile + (int64_t)threadIdx.x * kDecWPT;
+    const int64_t j0 = (int64_t)tile * kDecTile + (int64_t)threadIdx.x * kDecWPT;
     const int64_t jb = j0 - 1;
     const int64_t base_k = (int64_t)R * (jb - T + 1);
     const uint32_t hshift = 31 - __clz(p.h);
@@ -243,26 +248,36 @@ __global__ void __launch_bounds__(kDecThreads) k_decode_tiles_aligned(DecodePara
         gbit |= (uint32_t)(T2 >> 32) << w;
         pbit |= (uint32_t)(wv[w] == 0xffffffffu) << w;
     }
-    decode_tile_finish(p, (uint64_t)j0, wv, gbit, pbit);
+    decode_tile_finish(p, (uint64_t)j0, wv, gbit, pbit, tile);
 }
 
-// One CTA: exclusive scan of the tile aggregates into per-tile carry-ins.
-static __global__ void __launch_bounds__(kScanThreads) k_decode_scan(DecodeParams p) {
+template <int L, int R>
+__global__ void __launch_bounds__(kDecThreads) k_decode_tiles_aligned(DecodeParams p) {
+    decode_tile_aligned<L, R>(p, blockIdx.x);
+}
+
+// One CTA of THREADS threads: exclusive scan of the tile aggregates into
+// per-tile carry-ins.
+template <int THREADS>
+__device__ __forceinline__ void decode_scan_block(const DecodeParams& p) {
     uint32_t carry = 0;
-    for (uint64_t base = 0; base < p.n_tiles; base += kScanThreads) {
+    for (uint64_t base = 0; base < p.n_tiles; base += THREADS) {
         uint64_t t = base + threadIdx.x;
         uint32_t a = t < p.n_tiles ? p.agg[t] : 2u;
         GP total;
-        GP pre = gp_block_scan<kScanThreads>(GP{a & 1u, (a >> 1) & 1u}, total);
+        GP pre = gp_block_scan<THREADS>(GP{a & 1u, (a >> 1) & 1u}, total);
         if (t < p.n_tiles) p.agg[t] = pre.g | (pre.p & carry);
         carry = total.g | (total.p & carry);
     }
     if (threadIdx.x == 0 && carry) atomicOr(p.status, kStatusCarryOut);
 }
 
-// Add each tile's carry-in at its first window and ripple it while windows wrap.
-static __global__ void k_decode_fix(DecodeParams p) {
-    uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+static __global__ void __launch_bounds__(kScanThreads) k_decode_scan(DecodeParams p) {
+    decode_scan_block<kScanThreads>(p);
+}
+
+// Add tile t's carry-in at its first window and ripple it while windows wrap.
+__device__ __forceinline__ void decode_fix_tile(const DecodeParams& p, uint64_t t) {
     if (t >= p.n_tiles || !p.agg[t]) return;
     uint64_t end = (t + 1) * kDecTile;
     if (end > p.n_windows) end = p.n_windows;
@@ -271,6 +286,10 @@ static __global__ void k_decode_fix(DecodeParams p) {
         p.out[j] = v;
         if (v != 0u) break;
     }
+}
+
+static __global__ void k_decode_fix(DecodeParams p) {
+    decode_fix_tile(p, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 }  // namespace dkss

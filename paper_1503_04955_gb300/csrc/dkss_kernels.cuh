@@ -299,13 +299,10 @@ __device__ __forceinline__ void stage_ext_from32(uint32_t* E, const uint32_t* y,
 // operand words and encodes them (Section 3.2.4) on the fly.
 // ---------------------------------------------------------------------------
 template <int m, int L, bool FIRST>
-__global__ void __launch_bounds__(kThreads) k_dft_fwd(LevelParams prm, Mod<L> md) {
+__device__ __forceinline__ void dft_fwd_column(const LevelParams& prm, const Mod<L>& md, uint32_t* col, uint64_t column,
+                                               int op) {
     using G = Geo<m, L>;
-    extern __shared__ __align__(16) uint32_t smem[];
-    uint32_t* col = smem;
     constexpr int LOG2_TWO_M = ilog2<G::TWO_M>();
-    const uint64_t column = blockIdx.x;
-    const int op = blockIdx.y;
     uint32_t* poly = prm.data + (op ? prm.poly_words : 0);
     const uint64_t mu_d = prm.len / G::TWO_M;
     const uint64_t blk = column / mu_d, l = column % mu_d;
@@ -340,6 +337,12 @@ __global__ void __launch_bounds__(kThreads) k_dft_fwd(LevelParams prm, Mod<L> md
         ld_res<L>(x, col + v * G::EW + t * L);
         st_res<L>(poly + ((base + (uint64_t)v * mu_d + l) * m + t) * L, x);
     }
+}
+
+template <int m, int L, bool FIRST>
+__global__ void __launch_bounds__(kThreads) k_dft_fwd(LevelParams prm, Mod<L> md) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    dft_fwd_column<m, L, FIRST>(prm, md, smem, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -406,14 +409,14 @@ __device__ __forceinline__ void load_shifted_rr(uint32_t (&out)[LR], const uint3
 // (ntt_rmul.cuh): same element set and grid as k_twiddle, no shared memory.
 // ---------------------------------------------------------------------------
 template <int m, int L, int LR, bool INV>
-__global__ void __launch_bounds__(kThreads) k_twiddle_ntt(LevelParams prm, ModRR<LR> mr) {
+__device__ __forceinline__ void twiddle_ntt_group(const LevelParams& prm, const ModRR<LR>& mr, uint64_t group, int op) {
     using G = Geo<m, L>;
     Team<m, L> tm;
-    uint32_t* poly = prm.data + (blockIdx.y ? prm.poly_words : 0);
+    uint32_t* poly = prm.data + (op ? prm.poly_words : 0);
     const uint64_t mu_d = prm.len / G::TWO_M;
     const uint64_t per_blk = (uint64_t)(G::TWO_M - 1) * (mu_d - 1);
     const uint64_t total = per_blk * (prm.P2 / prm.len);
-    const uint64_t idx = (uint64_t)blockIdx.x * G::NTEAMS + tm.id;
+    const uint64_t idx = group * G::NTEAMS + tm.id;
     if (idx >= total) return;
     const uint64_t blk = idx / per_blk, rem = idx % per_blk;
     const uint64_t v = 1 + rem / (mu_d - 1), l = 1 + rem % (mu_d - 1);
@@ -442,6 +445,11 @@ __global__ void __launch_bounds__(kThreads) k_twiddle_ntt(LevelParams prm, ModRR
     st_res<L>(x + (lane + m / 2) * L, o);
 }
 
+template <int m, int L, int LR, bool INV>
+__global__ void __launch_bounds__(kThreads) k_twiddle_ntt(LevelParams prm, ModRR<LR> mr) {
+    twiddle_ntt_group<m, L, LR, INV>(prm, mr, blockIdx.x, blockIdx.y);
+}
+
 // ---------------------------------------------------------------------------
 // Last level of both forward transforms, componentwise products scaled by
 // (2M)^-1 (Section 3.2.6), and the first level of the backwards transform,
@@ -449,15 +457,15 @@ __global__ void __launch_bounds__(kThreads) k_twiddle_ntt(LevelParams prm, ModRR
 // alpha^(2m/len)).
 // ---------------------------------------------------------------------------
 template <int m, int L, int LR, bool NTT>
-__global__ void __launch_bounds__(kThreads) k_final_pointwise(LevelParams prm, Mod<L> md, ModRR<LR> mr) {
+__device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>& md, const ModRR<LR>& mr,
+                                            uint32_t* smem, uint64_t block) {
     using G = Geo<m, L>;
-    extern __shared__ __align__(16) uint32_t smem[];
     const int n = (int)prm.len;
     const int log2n = 31 - __clz(n);
     uint32_t* sa = smem;
     uint32_t* sb = smem + n * G::EW;
     uint32_t* tbuf = sb + n * G::EW;
-    const uint64_t base = (uint64_t)blockIdx.x * n;
+    const uint64_t base = block * n;
     uint32_t* pa = prm.data;
     uint32_t* pb = prm.data + prm.poly_words;
     for (int idx = threadIdx.x; idx < n * m; idx += kThreads) {
@@ -529,18 +537,21 @@ __global__ void __launch_bounds__(kThreads) k_final_pointwise(LevelParams prm, M
     }
 }
 
+template <int m, int L, int LR, bool NTT>
+__global__ void __launch_bounds__(kThreads) k_final_pointwise(LevelParams prm, Mod<L> md, ModRR<LR> mr) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    final_block<m, L, LR, NTT>(prm, md, mr, smem, blockIdx.x);
+}
+
 // ---------------------------------------------------------------------------
 // Backwards level d, after its twiddles: the 2m-point DFT with root alpha^-1
 // over each column (decimation in frequency: natural in, bit-reversed out),
 // written back in natural element order.
 // ---------------------------------------------------------------------------
 template <int m, int L>
-__global__ void __launch_bounds__(kThreads) k_dft_inv(LevelParams prm, Mod<L> md) {
+__device__ __forceinline__ void dft_inv_column(const LevelParams& prm, const Mod<L>& md, uint32_t* col, uint64_t column) {
     using G = Geo<m, L>;
-    extern __shared__ __align__(16) uint32_t smem[];
-    uint32_t* col = smem;
     constexpr int LOG2_TWO_M = ilog2<G::TWO_M>();
-    const uint64_t column = blockIdx.x;
     uint32_t* poly = prm.data;
     const uint64_t mu_d = prm.len / G::TWO_M;
     const uint64_t blk = column / mu_d, l = column % mu_d;
@@ -559,6 +570,12 @@ __global__ void __launch_bounds__(kThreads) k_dft_inv(LevelParams prm, Mod<L> md
         ld_res<L>(x, col + bitrev(j, LOG2_TWO_M) * G::EW + t * L);
         st_res<L>(poly + ((base + (uint64_t)j * mu_d + l) * m + t) * L, x);
     }
+}
+
+template <int m, int L>
+__global__ void __launch_bounds__(kThreads) k_dft_inv(LevelParams prm, Mod<L> md) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    dft_inv_column<m, L>(prm, md, smem, blockIdx.x);
 }
 
 template <int m, int L>

@@ -46,6 +46,14 @@ struct dkss_plan_s {
     uint64_t prof_count[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
 
+namespace dkss_planning {
+// Host parts of a plan, shared by single plans and batches (capi.cu).
+dkss_status plan_host(dkss_plan_s* pl, uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, uint64_t p, uint32_t z);
+void build_table(const dkss_plan_s* pl, std::vector<uint32_t>& out);
+void build_eval_table(const dkss_plan_s* pl, std::vector<uint32_t>& out);
+void build_ntt_consts(const dkss_plan_s* pl, std::vector<uint32_t>& out);
+}  // namespace dkss_planning
+
 namespace dkss {
 // Kernel-group kinds reported by dkss_profile_read.
 enum ProfKind {
