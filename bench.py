@@ -60,6 +60,8 @@ def parse_args():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(syn.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=30)
+    ap.add_argument("--no-batched", action="store_true", help="skip the 4096-product batched workload")
+    ap.add_argument("--batched-steps", type=int, default=10)
     ap.add_argument("--form", default="ntt", choices=["ntt", "direct"],
                     help="R-multiplications through the evaluation map of R (ntt) or the direct convolution")
     return ap.parse_args()
@@ -291,6 +293,8 @@ def run_ours(args):
                 "avg_launch_ms": round(avg_launch_ms, 4), "ops_per_launch": int(ops_per_launch),
                 "peak_basis": "152 SMs x 64 IMAD/clk x 2070 MHz (recipe unit counts and max clock)"}
 
+    batched = run_batched(args, dev, flush) if (rank == 0 and not args.no_batched) else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload, A, B)
@@ -311,6 +315,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": 4 * A.nbytes},
             "roofline": roofline,
             "cpu_baseline": cpu,
+            "batched": batched,
             "clocks": clocks,
             "wall_s": round(wall, 3),
         }
@@ -318,6 +323,97 @@ def run_ours(args):
     plan.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_batched(args, dev, flush):
+    """4096 products, operand lengths 2^x with x uniform in [14, 20] rounded to
+    64-bit limbs: one persistent-kernel launch under a CUDA graph per step,
+    against plain per-product dkss_mul launches with the same parameters."""
+    import torch
+
+    import paper_1503_04955_gb300 as dk
+
+    w = syn.BATCH_WORKLOAD
+    seed = syn.config_seed(w["index"])
+    lengths = [int(n) for n in syn.log_uniform_lengths(w["count"], seed, w["lo_exp"], w["hi_exp"])]
+    words = [syn.n_limbs(n) for n in lengths]
+    total = sum(words)
+    a_all = torch.empty(total, dtype=torch.int64, device=dev)
+    b_all = torch.empty(total, dtype=torch.int64, device=dev)
+    o_all = torch.zeros(2 * total, dtype=torch.int64, device=dev)
+    a_l, b_l, o_l, ops = [], [], [], []
+    off = 0
+    for j, (n, wd) in enumerate(zip(lengths, words)):
+        A, B = syn.operand_pair(n, seed, product=j)
+        ops.append((A, B))
+        a_all[off:off + wd] = torch.from_numpy(A.view(np.int64)).to(dev)
+        b_all[off:off + wd] = torch.from_numpy(B.view(np.int64)).to(dev)
+        a_l.append(a_all[off:off + wd])
+        b_l.append(b_all[off:off + wd])
+        o_l.append(o_all[2 * off:2 * off + 2 * wd])
+        off += wd
+    t0 = time.perf_counter()
+    bt = dk.Batch(lengths)
+    plan_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(3):
+        bt.run(a_l, b_l, o_l)
+    torch.cuda.synchronize(dev)
+    steps = max(1, args.batched_steps)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for e0, e1 in ev:
+        flush.fill_(1)
+        e0.record(stream)
+        bt.run(a_l, b_l, o_l)
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / steps
+    ok = all(check_product(o.cpu().numpy().view(np.uint64), A, B)
+             for o, (A, B) in zip(o_l[::64], ops[::64]))
+    classes = {}
+    for j in range(len(lengths)):
+        prm = bt.job_params(j)
+        key = prm["class_bits"]
+        if key not in classes:
+            classes[key] = {"M": prm["M"], "u": prm["u"], "levels": prm["levels"], "jobs": 0}
+        classes[key]["jobs"] += 1
+    graph = bool(bt.job_params(0)["graph"])
+    grid = bt.job_params(0)["grid"]
+    # plain per-product launches with each class's parameters
+    plans = {}
+    for key, c in classes.items():
+        plans[key] = dk.Plan(key, c["M"], 32, c["u"], 65537, 5)
+    job_plan = [plans[bt.job_params(j)["class_bits"]] for j in range(len(lengths))]
+    bt.close()
+    # a plan is fixed to one N: one plan per distinct length for the plain loop
+    plain_plans = {}
+    for j, n in enumerate(lengths):
+        if n not in plain_plans:
+            jp = job_plan[j]
+            plain_plans[n] = dk.Plan(n, jp.M, jp.m, jp.u, jp.p, jp.z)
+    for _ in range(2):
+        for j, n in enumerate(lengths):
+            plain_plans[n].mul(a_l[j], b_l[j], o_l[j])
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.fill_(1)
+    e0.record(stream)
+    for j, n in enumerate(lengths):
+        plain_plans[n].mul(a_l[j], b_l[j], o_l[j])
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    plain_ms = e0.elapsed_time(e1)
+    for p in list(plans.values()) + list(plain_plans.values()):
+        p.close()
+    bits = 2 * sum(lengths)
+    return {"workload": "dkss_batch_4096_log_uniform_2p14_2p20", "products": len(lengths),
+            "operand_bits": bits, "ms_per_batch": round(ms, 4),
+            "products_per_s": round(len(lengths) / (ms * 1e-3), 1),
+            "operand_gbit_s": round(bits / (ms * 1e-3) / 1e9, 3),
+            "plain_launches_ms": round(plain_ms, 4),
+            "speedup_vs_plain_launches": round(plain_ms / ms, 3),
+            "graph": graph, "persistent_grid": grid, "plan_s": round(plan_s, 3), "bit_exact_sampled": bool(ok),
+            "classes": {str(k): v for k, v in sorted(classes.items())}}
 
 
 # ------------------------------------------------------------- reference ----

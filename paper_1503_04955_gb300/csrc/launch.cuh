@@ -1,5 +1,6 @@
 // Host launchers of the DKSS_MUL kernels for one (m, L) pair.
 #pragma once
+#include <algorithm>
 #include "decode.cuh"
 #include "dkss_kernels.cuh"
 #include "plan.hpp"
@@ -99,19 +100,23 @@ dkss_status prepare(dkss_plan_s* pl) {
     const int colb = (int)column_smem_bytes<m, L>();
     const int twb = (int)twiddle_smem_bytes<m, L, LR>();
     const int fin = (int)final_smem_bytes<m, L, LR>((int)pl->r_last);
-    const int fdft = (int)(sizeof(uint32_t) * pl->r_last * G::EW);
     int optin = 0;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device) != cudaSuccess)
         return DKSS_ECUDA;
     if (colb > optin || twb > optin || fin > optin) return DKSS_EUNSUPPORTED;
+    // The limit is a property of the kernel, shared by every plan of this
+    // (m, L, LR): set it to the most any plan can ask for (last level of
+    // length 2m), capped by the device, so that no plan lowers another's.
+    const int fin_max = (int)std::min<size_t>(final_smem_bytes<m, L, LR>(G::TWO_M), (size_t)optin);
+    const int fdft_max = (int)std::min<size_t>(sizeof(uint32_t) * G::TWO_M * G::EW, (size_t)optin);
     if (cudaFuncSetAttribute(k_dft_fwd<m, L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, colb) ||
         cudaFuncSetAttribute(k_dft_fwd<m, L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, colb) ||
         cudaFuncSetAttribute(k_dft_inv<m, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, colb) ||
         cudaFuncSetAttribute(k_twiddle<m, L, LR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, twb) ||
         cudaFuncSetAttribute(k_twiddle<m, L, LR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, twb) ||
-        cudaFuncSetAttribute(k_final_pointwise<m, L, LR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fin) ||
-        cudaFuncSetAttribute(k_final_pointwise<m, L, LR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fin) ||
-        cudaFuncSetAttribute(k_final_dft<m, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, fdft))
+        cudaFuncSetAttribute(k_final_pointwise<m, L, LR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fin_max) ||
+        cudaFuncSetAttribute(k_final_pointwise<m, L, LR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fin_max) ||
+        cudaFuncSetAttribute(k_final_dft<m, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, fdft_max))
         return DKSS_ECUDA;
     // launches per dkss_mul: per radix-2m level a DFT and a twiddle launch forward
     // and backwards, the fused last level, three decode kernels

@@ -167,3 +167,18 @@ def test_2p28_bits_properties(dk, oc, flags):
 
 def test_2p32_bits_properties(dk, oc):
     large_checks(dk, oc, "dkss_2p32b", 4)
+
+
+def test_plans_of_one_kind_do_not_interfere(dk):
+    """Two live plans of the same (m, L) with different last-level lengths:
+    the second plan's set-up must not break the first (kernel attributes are
+    shared by all plans of a kind)."""
+    big = (1 << 20, 2048, 32, 32, 65537, 5)      # last level 2m = 64
+    small = (16384, 64, 32, 16, 65537, 5)        # last level 2
+    A, B = syn.operand_pair(big[0], 8)
+    with dk.Plan(*big) as p1:
+        with dk.Plan(*small) as p2:
+            a2, b2 = syn.operand_pair(small[0], 9)
+            assert syn.to_int(to_host(p2.mul(to_dev(a2), to_dev(b2)))) == syn.to_int(a2) * syn.to_int(b2)
+        c = to_host(p1.mul(to_dev(A), to_dev(B)))
+    assert syn.to_int(c) == syn.to_int(A) * syn.to_int(B)
