@@ -49,7 +49,8 @@ typedef enum {
 
 enum {
     DKSS_FORM_IMAD = 1,    /* R-multiplications on the integer pipe (default) */
-    DKSS_FORM_INT8TC = 2,  /* R-multiplications as exact INT8 tensor-core MMAs */
+    DKSS_FORM_INT8TC = 2,  /* R-multiplications as exact INT8 tensor-core products
+                              (mma.sync u8, byte slices of the residues); m >= 32 */
     DKSS_PROFILE = 4,      /* per-stage CUDA-event timing, read with dkss_profile_read */
     DKSS_DEBUG_CHECKS = 8, /* reserved: extra device-side range checks */
     DKSS_RMUL_DIRECT = 16  /* R-multiplications by the direct negacyclic convolution
@@ -66,7 +67,10 @@ enum {
  *           Z/p^zZ; p^z must exceed the largest product coefficient
  *           M*(m/2)*(2^u-1)^2 (Section 3.2.2); m*p^z < 2^127 (so that
  *           products in 26-bit limbs stay within 5 limbs).
- *   flags   DKSS_FORM_* (IMAD when 0).
+ *   flags   0 (R-multiplications through the evaluation map of R on the
+ *           integer pipe), DKSS_RMUL_DIRECT (direct convolution, integer pipe)
+ *           or DKSS_FORM_INT8TC (INT8 tensor cores; DKSS_EUNSUPPORTED if
+ *           m < 32), optionally | DKSS_PROFILE.
  * On the host it tests p (deterministic Miller-Rabin), finds the smallest
  * generator zeta of F_p^*, Hensel-lifts it to a (p-1)-th root of unity mod p^z,
  * forms omega = zeta_z^((p-1)/2M), gamma = omega^(2M/2m) and rho by Lagrange

@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(const BatchJob* __restric
                 }
                 case kStFinal:
                     lp.len = jb.r_last;
-                    final_block<m, L, LR, true>(lp, md, mr, smem, local);
+                    final_block<m, L, LR, kFormNtt>(lp, md, mr, smem, local);
                     break;
                 case kStInvDft:
                     dft_inv_column<m, L>(lp, md, smem, local);

@@ -151,6 +151,7 @@ dkss_status plan_host(dkss_plan_s* pl, uint64_t n_bits, uint64_t M, uint32_t m, 
     while (LR <= 5 && (26 * LR < 127 && (((u128)m * q) >> (26 * LR - 2)) != 0)) ++LR;
     if (LR > 5 || LR < L || LR > L + 1) return DKSS_EUNSUPPORTED;
     pl->LR = LR;
+    pl->i8_S = (uint32_t)((bitlen(q) + 7) / 8);   // bytes of a residue (INT8 form)
     for (uint32_t i = 0; i < 5; ++i) pl->q_rr[i] = i < LR ? (uint32_t)(q >> (26 * i)) & ((1u << 26) - 1) : 0;
     {
         uint32_t q0 = (uint32_t)q, inv = q0;
@@ -330,13 +331,14 @@ dkss_status dkss_plan(dkss_plan_t* plan, uint64_t n_bits, uint64_t M, uint32_t m
                       uint32_t flags) {
     if (!plan) return DKSS_EINVAL;
     *plan = nullptr;
-    if (flags & DKSS_FORM_INT8TC) return DKSS_EUNSUPPORTED;
     dkss_plan_s* pl = new (std::nothrow) dkss_plan_s;
     if (!pl) return DKSS_ENOMEM;
     pl->flags = flags;
     dkss_status s = plan_host(pl, n_bits, M, m, u, p, z);
     Kernels k;
     if (s == DKSS_OK && !lookup(pl->m, pl->L, pl->LR, &k)) s = DKSS_EUNSUPPORTED;
+    // the INT8 tensor-core form needs a warp per element and at most 16 bytes per residue
+    if (s == DKSS_OK && (flags & DKSS_FORM_INT8TC) && (pl->m < 32 || pl->i8_S > 16)) s = DKSS_EUNSUPPORTED;
     if (s != DKSS_OK) {
         delete pl;
         return s;
@@ -346,7 +348,7 @@ dkss_status dkss_plan(dkss_plan_t* plan, uint64_t n_bits, uint64_t M, uint32_t m
         return DKSS_ECUDA;
     }
     std::vector<uint32_t> table, ntt;
-    if (pl->flags & DKSS_RMUL_DIRECT) build_table(pl, table);
+    if (pl->flags & (DKSS_RMUL_DIRECT | DKSS_FORM_INT8TC)) build_table(pl, table);
     else build_eval_table(pl, table);
     build_ntt_consts(pl, ntt);
     pl->poly_words = pl->P2 * pl->m * pl->L;

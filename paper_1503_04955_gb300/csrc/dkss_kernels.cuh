@@ -19,6 +19,7 @@
 #include <cstdint>
 
 #include "arith.cuh"
+#include "i8_rmul.cuh"
 #include "ntt_rmul.cuh"
 #include "rr_arith.cuh"
 
@@ -62,7 +63,24 @@ struct LevelParams {
     uint32_t kscale[5];        // (2M)^-1 R'^2 mod p^z in 26-bit limbs, R' = 2^(26 LR)
     const uint32_t* table_eval;  // rho^s(gamma^(2 brv(i)+1)) R', s < mu_top, i < m: LR words each
     const uint32_t* ntt_cst;     // NttLayout<m> constants, LR words each
+    uint32_t i8_S;               // bytes per residue (INT8 tensor-core form)
 };
+
+// How R-multiplications are computed.
+enum : int {
+    kFormDirect = 0,   // negacyclic convolution on the integer pipe (26-bit limbs)
+    kFormNtt = 1,      // through the evaluation map of R (ntt_rmul.cuh)
+    kFormI8 = 2        // as INT8 tensor-core products (i8_rmul.cuh)
+};
+
+// Per-warp shared words of an INT8 R-multiplication: x and E in 26-bit
+// limbs, then the byte planes and diagonal sums of i8_rmul.cuh.  Rounded up
+// to 4 words so that every warp's buffer starts 16-byte aligned (residues of
+// 4 limbs are stored with 16-byte vector accesses).
+template <int m, int LR>
+__host__ __device__ constexpr int i8_warp_words(int S) {
+    return (3 * m * LR + i8_warp_bytes<m>(S) / 4 + 3) & ~3;
+}
 
 __device__ __forceinline__ uint32_t bitrev(uint32_t x, int bits) { return __brev(x) >> (32 - bits); }
 
@@ -292,6 +310,43 @@ __device__ __forceinline__ void stage_ext_from32(uint32_t* E, const uint32_t* y,
     }
 }
 
+// Warp-owned staging (one warp per element, INT8 form): x from radix-2^32
+// residues; E = (y, -y) from 26-bit limbs (the coefficient table) or from
+// radix-2^32 residues (a transformed operand).
+template <int m, int L, int LR>
+__device__ __forceinline__ void i8_stage_x_from32(uint32_t* X, const uint32_t* x, int lane) {
+    for (int t = lane; t < m; t += 32) {
+        uint32_t v[L], w[LR];
+        ld_res<L>(v, x + t * L);
+        to_rr<L, LR>(w, v);
+        st_rr<LR>(X + t * LR, w);
+    }
+}
+
+template <int m, int LR>
+__device__ __forceinline__ void i8_stage_ext_rr(uint32_t* E, const uint32_t* y, const ModRR<LR>& md, int lane) {
+    for (int t = lane; t < m; t += 32) {
+        uint32_t v[LR], nv[LR];
+#pragma unroll
+        for (int i = 0; i < LR; ++i) v[i] = y[t * LR + i];
+        neg_rr<LR>(nv, v, md);
+        st_rr<LR>(E + t * LR, v);
+        st_rr<LR>(E + (t + m) * LR, nv);
+    }
+}
+
+template <int m, int L, int LR>
+__device__ __forceinline__ void i8_stage_ext_from32(uint32_t* E, const uint32_t* y, const ModRR<LR>& md, int lane) {
+    for (int t = lane; t < m; t += 32) {
+        uint32_t v32[L], v[LR], nv[LR];
+        ld_res<L>(v32, y + t * L);
+        to_rr<L, LR>(v, v32);
+        neg_rr<LR>(nv, v, md);
+        st_rr<LR>(E + t * LR, v);
+        st_rr<LR>(E + (t + m) * LR, nv);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Forward level d, step i.: the 2m-point inner DFT of one column with root
 // alpha (shifts and additions only), in shared memory.  Grid: x = column
@@ -456,7 +511,7 @@ __global__ void __launch_bounds__(kThreads) k_twiddle_ntt(LevelParams prm, ModRR
 // fused.  One CTA per block of n = len contiguous elements (len <= 2m, root
 // alpha^(2m/len)).
 // ---------------------------------------------------------------------------
-template <int m, int L, int LR, bool NTT>
+template <int m, int L, int LR, int FORM>
 __device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>& md, const ModRR<LR>& mr,
                                             uint32_t* smem, uint64_t block) {
     using G = Geo<m, L>;
@@ -482,7 +537,34 @@ __device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>
     dft_dit<m, L>(sa, sb, 2, n, root, md);
     // componentwise products c_v = a_v * b_v * (2M)^-1
     Team<m, L> tm;
-    if constexpr (NTT) {
+    if constexpr (FORM == kFormI8) {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        uint32_t* X = tbuf + warp * i8_warp_words<m, LR>((int)prm.i8_S);
+        uint32_t* E = X + m * LR;
+        uint8_t* xb = reinterpret_cast<uint8_t*>(E + 2 * m * LR);
+        uint8_t* fb = xb + ((prm.i8_S * m + 3) / 4) * 4;
+        uint32_t* D = reinterpret_cast<uint32_t*>(fb + ((prm.i8_S * (2 * m + 4) + 3) / 4) * 4);
+        uint32_t ks[LR];
+#pragma unroll
+        for (int w = 0; w < LR; ++w) ks[w] = prm.kscale[w];
+        for (int v = warp; v < n; v += kWarps) {
+            i8_stage_x_from32<m, L, LR>(X, sa + v * G::EW, lane);
+            i8_stage_ext_from32<m, L, LR>(E, sb + v * G::EW, mr, lane);
+            __syncwarp();
+            i8_stage<m, LR>(xb, fb, (int)prm.i8_S, X, E, lane);
+            __syncwarp();
+            uint32_t out[m / 32][LR];
+            i8_rmul_warp<m, LR>(out, xb, fb, D, (int)prm.i8_S, 0, mr, lane);
+#pragma unroll
+            for (int c = 0; c < m / 32; ++c) {
+                uint32_t scaled[LR], o32[L];
+                mont_mul_rr<LR>(scaled, out[c], ks, mr);
+                from_rr<L, LR>(o32, scaled);
+                st_res<L>(sa + v * G::EW + (lane + 32 * c) * L, o32);
+            }
+            __syncwarp();
+        }
+    } else if constexpr (FORM == kFormNtt) {
         for (int v = tm.id; v < n; v += G::NTEAMS) {
             const int lane = tm.lane;
             uint32_t alo[LR], ahi[LR], blo[LR], bhi[LR], w[L];
@@ -537,10 +619,53 @@ __device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>
     }
 }
 
-template <int m, int L, int LR, bool NTT>
+template <int m, int L, int LR, int FORM>
 __global__ void __launch_bounds__(kThreads) k_final_pointwise(LevelParams prm, Mod<L> md, ModRR<LR> mr) {
     extern __shared__ __align__(16) uint32_t smem[];
-    final_block<m, L, LR, NTT>(prm, md, mr, smem, blockIdx.x);
+    final_block<m, L, LR, FORM>(prm, md, mr, smem, blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// Bad multiplications of level d as INT8 tensor-core products: one warp per
+// element (same element set as k_twiddle), twiddles from the coefficient
+// table.  Grid: x = groups of kWarps elements, y = operand.
+// ---------------------------------------------------------------------------
+template <int m, int L, int LR, bool INV>
+__global__ void __launch_bounds__(kThreads) k_twiddle_i8(LevelParams prm, ModRR<LR> mr) {
+    using G = Geo<m, L>;
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t* X = smem + warp * i8_warp_words<m, LR>((int)prm.i8_S);
+    uint32_t* E = X + m * LR;
+    uint8_t* xb = reinterpret_cast<uint8_t*>(E + 2 * m * LR);
+    uint8_t* fb = xb + ((prm.i8_S * m + 3) / 4) * 4;
+    uint32_t* D = reinterpret_cast<uint32_t*>(fb + ((prm.i8_S * (2 * m + 4) + 3) / 4) * 4);
+    uint32_t* poly = prm.data + (blockIdx.y ? prm.poly_words : 0);
+    const uint64_t mu_d = prm.len / G::TWO_M;
+    const uint64_t per_blk = (uint64_t)(G::TWO_M - 1) * (mu_d - 1);
+    const uint64_t total = per_blk * (prm.P2 / prm.len);
+    const uint64_t idx = (uint64_t)blockIdx.x * kWarps + warp;
+    if (idx >= total) return;
+    const uint64_t blk = idx / per_blk, rem = idx % per_blk;
+    const uint64_t v = 1 + rem / (mu_d - 1), l = 1 + rem % (mu_d - 1);
+    uint64_t e = v * l * prm.bp;
+    if (INV) e = prm.P2 - e;
+    const int r = (int)(e >> prm.log2_mu_top);
+    const uint64_t sidx = e & (prm.mu_top - 1);
+    uint32_t* x = poly + (blk * prm.len + v * mu_d + l) * G::EW;
+    i8_stage_x_from32<m, L, LR>(X, x, lane);
+    i8_stage_ext_rr<m, LR>(E, prm.table + sidx * m * LR, mr, lane);
+    __syncwarp();
+    i8_stage<m, LR>(xb, fb, (int)prm.i8_S, X, E, lane);
+    __syncwarp();
+    uint32_t out[m / 32][LR];
+    i8_rmul_warp<m, LR>(out, xb, fb, D, (int)prm.i8_S, r, mr, lane);
+#pragma unroll
+    for (int c = 0; c < m / 32; ++c) {
+        uint32_t o32[L];
+        from_rr<L, LR>(o32, out[c]);
+        st_res<L>(x + (lane + 32 * c) * L, o32);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -589,9 +714,16 @@ constexpr size_t twiddle_smem_bytes() {
 }
 
 template <int m, int L, int LR>
-size_t final_smem_bytes(int n) {
+size_t final_smem_bytes(int n, int form = kFormDirect, int S = 0) {
     using G = Geo<m, L>;
-    return sizeof(uint32_t) * (2 * (size_t)n * G::EW + (size_t)G::NTEAMS * TeamBuf<m, LR>::WORDS);
+    const size_t tb = form == kFormI8 ? (size_t)kWarps * i8_warp_words<m, LR>(S)
+                                      : (size_t)G::NTEAMS * TeamBuf<m, LR>::WORDS;
+    return sizeof(uint32_t) * (2 * (size_t)n * G::EW + tb);
+}
+
+template <int m, int L, int LR>
+size_t twiddle_i8_smem_bytes(int S) {
+    return sizeof(uint32_t) * (size_t)kWarps * i8_warp_words<m, LR>(S);
 }
 
 }  // namespace dkss

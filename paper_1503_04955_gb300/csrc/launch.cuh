@@ -39,6 +39,7 @@ static LevelParams make_level(const dkss_plan_s* pl) {
     for (int i = 0; i < 5; ++i) lp.kscale[i] = pl->kscale[i];
     lp.table_eval = pl->d_table;
     lp.ntt_cst = pl->d_ntt;
+    lp.i8_S = pl->i8_S;
     return lp;
 }
 
@@ -104,6 +105,22 @@ dkss_status prepare(dkss_plan_s* pl) {
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device) != cudaSuccess)
         return DKSS_ECUDA;
     if (colb > optin || twb > optin || fin > optin) return DKSS_EUNSUPPORTED;
+    if (pl->flags & DKSS_FORM_INT8TC) {
+        if constexpr (m >= 32) {
+            // INT8 form: sized for the largest byte count (16), shared by all plans of this kind
+            const int i8tw = (int)twiddle_i8_smem_bytes<m, L, LR>(16);
+            const int i8fin = (int)final_smem_bytes<m, L, LR>((int)pl->r_last, kFormI8, (int)pl->i8_S);
+            const int i8fin_max = (int)std::min<size_t>(final_smem_bytes<m, L, LR>(G::TWO_M, kFormI8, 16), (size_t)optin);
+            if (i8tw > optin || i8fin > optin) return DKSS_EUNSUPPORTED;
+            if (cudaFuncSetAttribute(k_twiddle_i8<m, L, LR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, i8tw) ||
+                cudaFuncSetAttribute(k_twiddle_i8<m, L, LR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, i8tw) ||
+                cudaFuncSetAttribute(k_final_pointwise<m, L, LR, kFormI8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     i8fin_max))
+                return DKSS_ECUDA;
+        } else {
+            return DKSS_EUNSUPPORTED;   // the INT8 form needs a warp per element (m >= 32)
+        }
+    }
     // The limit is a property of the kernel, shared by every plan of this
     // (m, L, LR): set it to the most any plan can ask for (last level of
     // length 2m), capped by the device, so that no plan lowers another's.
@@ -114,8 +131,10 @@ dkss_status prepare(dkss_plan_s* pl) {
         cudaFuncSetAttribute(k_dft_inv<m, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, colb) ||
         cudaFuncSetAttribute(k_twiddle<m, L, LR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, twb) ||
         cudaFuncSetAttribute(k_twiddle<m, L, LR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, twb) ||
-        cudaFuncSetAttribute(k_final_pointwise<m, L, LR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fin_max) ||
-        cudaFuncSetAttribute(k_final_pointwise<m, L, LR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fin_max) ||
+        cudaFuncSetAttribute(k_final_pointwise<m, L, LR, kFormDirect>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             fin_max) ||
+        cudaFuncSetAttribute(k_final_pointwise<m, L, LR, kFormNtt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             fin_max) ||
         cudaFuncSetAttribute(k_final_dft<m, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, fdft_max))
         return DKSS_ECUDA;
     // launches per dkss_mul: per radix-2m level a DFT and a twiddle launch forward
@@ -140,7 +159,12 @@ static dkss_status launch_twiddle(dkss_plan_s* pl, LevelParams lp, int operands,
     const uint64_t total = (uint64_t)(G::TWO_M - 1) * (mu_d - 1) * (pl->P2 / lp.len);
     if (total == 0) return DKSS_OK;
     dim3 grid((unsigned)((total + G::NTEAMS - 1) / G::NTEAMS), operands);
-    if (pl->flags & DKSS_RMUL_DIRECT)
+    if (pl->flags & DKSS_FORM_INT8TC) {
+        if constexpr (m >= 32) {
+            dim3 g8((unsigned)((total + kWarps - 1) / kWarps), operands);
+            k_twiddle_i8<m, L, LR, INV><<<g8, kThreads, twiddle_i8_smem_bytes<m, L, LR>((int)pl->i8_S), st>>>(lp, mr);
+        }
+    } else if (pl->flags & DKSS_RMUL_DIRECT)
         k_twiddle<m, L, LR, INV><<<grid, kThreads, twiddle_smem_bytes<m, L, LR>(), st>>>(lp, mr);
     else
         k_twiddle_ntt<m, L, LR, INV><<<grid, kThreads, 0, st>>>(lp, mr);
@@ -182,12 +206,18 @@ dkss_status run_mul(dkss_plan_s* pl, const uint64_t* a, const uint64_t* b, uint6
     {
         ProfScope ps(pl, st, kProfFinal);
         const unsigned blocks = (unsigned)(pl->P2 / pl->r_last);
-        if (pl->flags & DKSS_RMUL_DIRECT)
-            k_final_pointwise<m, L, LR, false><<<blocks, kThreads, final_smem_bytes<m, L, LR>((int)pl->r_last), st>>>(
+        if (pl->flags & DKSS_FORM_INT8TC) {
+            if constexpr (m >= 32)
+                k_final_pointwise<m, L, LR, kFormI8>
+                    <<<blocks, kThreads, final_smem_bytes<m, L, LR>((int)pl->r_last, kFormI8, (int)pl->i8_S), st>>>(
+                        lp, md, mr);
+        } else if (pl->flags & DKSS_RMUL_DIRECT) {
+            k_final_pointwise<m, L, LR, kFormDirect><<<blocks, kThreads, final_smem_bytes<m, L, LR>((int)pl->r_last), st>>>(
                 lp, md, mr);
-        else
-            k_final_pointwise<m, L, LR, true><<<blocks, kThreads, final_smem_bytes<m, L, LR>((int)pl->r_last), st>>>(
+        } else {
+            k_final_pointwise<m, L, LR, kFormNtt><<<blocks, kThreads, final_smem_bytes<m, L, LR>((int)pl->r_last), st>>>(
                 lp, md, mr);
+        }
         DKSS_CHECK_LAUNCH();
     }
     for (int d = (int)pl->col_levels - 1; d >= 0; --d) {

@@ -21,6 +21,7 @@ struct dkss_plan_s {
     uint32_t q_limbs[4] = {0, 0, 0, 0};
     uint32_t nprime = 0, nsub = 0;
     uint32_t LR = 0;              // 26-bit limbs of the product arithmetic
+    uint32_t i8_S = 0;            // bytes per residue for the INT8 tensor-core form
     uint32_t q_rr[5] = {0, 0, 0, 0, 0};
     uint32_t nprime26 = 0;        // -(p^z)^-1 mod 2^26
     uint32_t kscale[5] = {0, 0, 0, 0, 0};  // (2M)^-1 R'^2 mod p^z, 26-bit limbs

@@ -182,3 +182,25 @@ def test_plans_of_one_kind_do_not_interfere(dk):
             assert syn.to_int(to_host(p2.mul(to_dev(a2), to_dev(b2)))) == syn.to_int(a2) * syn.to_int(b2)
         c = to_host(p1.mul(to_dev(A), to_dev(B)))
     assert syn.to_int(c) == syn.to_int(A) * syn.to_int(B)
+
+
+# INT8 tensor-core form (DKSS_FORM_INT8TC): m >= 32, byte counts 6 .. 15
+I8_CFGS = [SMALL[1], SMALL[2], SMALL[4], SMALL[5], SMALL[6]]
+
+
+@pytest.mark.parametrize("cfg", I8_CFGS)
+def test_int8_form_small_configs(dk, oc, cfg):
+    A, B = syn.operand_pair(cfg[0], 4321, product=I8_CFGS.index(cfg))
+    check_product(dk, oc, cfg, A, B, flags=2)
+    A = syn.special_operand(cfg[0], "ones")
+    check_product(dk, oc, cfg, A, A, with_forward=False, flags=2)
+
+
+def test_int8_form_2p24_bits(dk, oc):
+    cfg = syn.workload_params("dkss_2p24b")
+    A, B = syn.operand_pair(cfg[0], syn.config_seed(1))
+    check_product(dk, oc, cfg, A, B, flags=2)
+
+
+def test_int8_form_2p28_bits_properties(dk, oc):
+    large_checks(dk, oc, "dkss_2p28b", 8, flags=2)

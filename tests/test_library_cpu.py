@@ -94,7 +94,9 @@ def test_plan_unsupported_m(dk):
     assert e.value.code in (2, 4)
 
 
-def test_int8_form_reports_unsupported(dk):
+def test_int8_form_needs_m_32(dk):
+    # the INT8 tensor-core form gives each element a warp: m = 16 is rejected
+    # before any device work
     h = ctypes.c_void_p()
     rc = dk.load().dkss_plan(ctypes.byref(h), 1 << 16, 512, 16, 16, 12289, 4, 2)
     assert rc == 4 and not h.value
