@@ -62,6 +62,8 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--no-batched", action="store_true", help="skip the 4096-product batched workload")
     ap.add_argument("--batched-steps", type=int, default=10)
+    ap.add_argument("--no-forms", action="store_true", help="skip the R-multiplication form comparison")
+    ap.add_argument("--form-steps", type=int, default=20)
     ap.add_argument("--form", default="ntt", choices=["ntt", "direct"],
                     help="R-multiplications through the evaluation map of R (ntt) or the direct convolution")
     return ap.parse_args()
@@ -294,6 +296,7 @@ def run_ours(args):
                 "peak_basis": "152 SMs x 64 IMAD/clk x 2070 MHz (recipe unit counts and max clock)"}
 
     batched = run_batched(args, dev, flush) if (rank == 0 and not args.no_batched) else None
+    forms = compare_forms(args, dev, flush, a, b, out, ms_per_step) if (rank == 0 and not args.no_forms) else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -316,6 +319,7 @@ def run_ours(args):
             "roofline": roofline,
             "cpu_baseline": cpu,
             "batched": batched,
+            "forms": forms,
             "clocks": clocks,
             "wall_s": round(wall, 3),
         }
@@ -323,6 +327,45 @@ def run_ours(args):
     plan.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def compare_forms(args, dev, flush, a, b, out, ms_main):
+    """Device time per product of the same workload with each R-multiplication
+    form: through the evaluation map of R and the direct convolution on the
+    integer pipe (IMAD), and INT8 tensor-core byte-slice products (TC)."""
+    import torch
+
+    import paper_1503_04955_gb300 as dk
+    from paper_1503_04955_gb300 import binding
+
+    cfg = syn.workload_params(args.workload)
+    res = {}
+    stream = torch.cuda.current_stream(dev)
+    for name, flags in (("ntt", 0), ("direct", binding.RMUL_DIRECT), ("int8tc", binding.FORM_INT8TC)):
+        if name == args.form:
+            res[name] = {"ms_per_step": round(ms_main, 5)}
+            continue
+        try:
+            plan = dk.Plan(*cfg, flags=flags)
+        except dk.DkssError as e:
+            res[name] = {"unsupported": str(e)}
+            continue
+        for _ in range(3):
+            plan.mul(a, b, out)
+        steps = max(1, args.form_steps)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for e0, e1 in ev:
+            flush.fill_(1)
+            e0.record(stream)
+            plan.mul(a, b, out)
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        plan.close()
+        res[name] = {"ms_per_step": round(sum(e0.elapsed_time(e1) for e0, e1 in ev) / steps, 5)}
+    if all("ms_per_step" in res.get(k, {}) for k in ("int8tc", "direct", "ntt")):
+        res["tc_vs_imad_direct"] = round(res["direct"]["ms_per_step"] / res["int8tc"]["ms_per_step"], 3)
+        res["tc_vs_imad_ntt"] = round(res["ntt"]["ms_per_step"] / res["int8tc"]["ms_per_step"], 3)
+    return res
 
 
 def run_batched(args, dev, flush):

@@ -236,6 +236,55 @@ dkss_status dkss_profile_read(dkss_plan_t plan, double* ms, uint64_t* counts, si
 dkss_status dkss_decode_static(const uint32_t* c, uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, uint32_t L,
                                uint64_t* out, dkss_stream_t stream);
 
+/*
+ * Valid parameter sets for N-bit operands (host only, no device work): for
+ * m in {16, 32, 64}, u in {8, 16, 24, 32}, the smallest M with M (m/2) u >= N
+ * and 2M > 2m, each p of a fixed list of primes with 2M | p-1 (12289, 40961,
+ * 65537, 786433, 7340033, 23068673, 104857601, 167772161, 469762049,
+ * 998244353) and the smallest z with p^z above the coefficient bound
+ * (Section 3.2.2), every set dkss_plan accepts and this build has kernels for.
+ * rows receives up to max_rows rows of 10 words: M, m, u, p, z, L, LR,
+ * transform levels, last-level length, 2M; *n_rows the number of valid sets
+ * (may exceed max_rows; rows may be NULL to count).  The search space of the
+ * autotuner.  Errors: DKSS_EINVAL.
+ */
+dkss_status dkss_plan_candidates(uint64_t n_bits, uint64_t* rows, size_t max_rows, size_t* n_rows);
+
+/*
+ * Cost model of the autotuner (the thesis has no counterpart; its Section 4.1
+ * picks parameters by a fixed rule and notes that calibration should smooth
+ * out the resulting staircase of run times).  A multilayer perceptron maps
+ * DKSS_MLP_FEATURES features of a parameter set to a predicted log2 of the
+ * product's device time: relu(W1 x + b1) -> relu(W2 h1 + b2) -> w3 . h2 + b3,
+ * hidden width DKSS_MLP_HIDDEN.  params: DKSS_MLP_PARAMS floats, in order
+ * W1[H][F], b1[H], W2[H][H], b2[H], w3[H], b3.  All pointers are device
+ * pointers; work is queued on `stream`.  This is the only floating point in
+ * the library and it never enters a product.
+ */
+#define DKSS_MLP_FEATURES 12
+#define DKSS_MLP_HIDDEN 32
+#define DKSS_MLP_PARAMS 1505
+
+/* y[n] = network(x[n]) for n < B; x is B rows of DKSS_MLP_FEATURES floats. */
+dkss_status dkss_mlp_forward(const float* params, const float* x, size_t B, float* y, dkss_stream_t stream);
+
+/*
+ * grad (DKSS_MLP_PARAMS floats) = gradient of the mean squared error
+ * mean_n (network(x[n]) - t[n])^2 with respect to params; *loss = that mean.
+ * grad and loss are overwritten.  Summation order across samples is not fixed
+ * (float atomics), so repeated calls agree to rounding only.
+ */
+dkss_status dkss_mlp_grad(const float* params, const float* x, const float* t, size_t B, float* grad, float* loss,
+                          dkss_stream_t stream);
+
+/*
+ * One Adam step (beta1 = 0.9, beta2 = 0.999, eps = 1e-8; Kingma and Ba,
+ * 2015) with learning rate lr; m1, m2 are the moment arrays (zero before step
+ * 1) and step counts from 1.
+ */
+dkss_status dkss_mlp_adam(float* params, const float* grad, float* m1, float* m2, float lr, uint32_t step,
+                          dkss_stream_t stream);
+
 /* Kernel launches one dkss_mul call queues (for launch accounting). */
 uint32_t dkss_plan_launches(dkss_plan_t plan);
 

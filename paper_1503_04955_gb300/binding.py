@@ -24,7 +24,7 @@ FORM_INT8TC = 2
 EXPORTS = ["dkss_plan", "dkss_mul", "dkss_mul_host", "dkss_forward", "dkss_mul_batch", "dkss_plan_info",
            "dkss_plan_rho", "dkss_profile_read", "dkss_plan_launches", "dkss_sync_status", "dkss_plan_destroy",
            "dkss_status_str", "dkss_decode_static", "dkss_batch_plan", "dkss_batch_run", "dkss_batch_job_params",
-           "dkss_batch_destroy"]
+           "dkss_batch_destroy", "dkss_plan_candidates", "dkss_mlp_forward", "dkss_mlp_grad", "dkss_mlp_adam"]
 FORM_PROFILE = 4
 RMUL_DIRECT = 16
 PROFILE_KINDS = ["fwd_dft", "fwd_twiddle", "final_pointwise", "inv_twiddle", "inv_dft", "decode"]
@@ -62,6 +62,13 @@ def load():
     lib.dkss_plan_rho.argtypes = [u64, u64, u32, u32, u64, u32, P, P, sz]
     lib.dkss_profile_read.argtypes = [P, P, P, sz]
     lib.dkss_decode_static.argtypes = [P, u64, u64, u32, u32, u32, P, P]
+    lib.dkss_plan_candidates.argtypes = [u64, P, sz, P]
+    lib.dkss_plan_candidates.restype = ctypes.c_int
+    lib.dkss_mlp_forward.argtypes = [P, P, sz, P, P]
+    lib.dkss_mlp_grad.argtypes = [P, P, P, sz, P, P, P]
+    lib.dkss_mlp_adam.argtypes = [P, P, P, P, ctypes.c_float, u32, P]
+    for f in (lib.dkss_mlp_forward, lib.dkss_mlp_grad, lib.dkss_mlp_adam):
+        f.restype = ctypes.c_int
     lib.dkss_decode_static.restype = ctypes.c_int
     lib.dkss_plan_launches.argtypes = [P]
     lib.dkss_plan_launches.restype = u32
@@ -301,3 +308,16 @@ def mul_batch(a_list, b_list, out_list, n_bits, flags=0, stream=None):
     jobs = _jobs_array(a_list, b_list, out_list, n_bits)
     _check(_load_batch().dkss_mul_batch(ctypes.cast(jobs, ctypes.c_void_p), len(n_bits), flags,
                                         _stream_handle(stream)), "dkss_mul_batch")
+
+
+CANDIDATE_FIELDS = ["M", "m", "u", "p", "z", "L", "LR", "levels", "r_last", "P2"]
+
+
+def plan_candidates(n_bits):
+    """dkss_plan_candidates: list of dicts of valid parameter sets for N-bit operands."""
+    lib = load()
+    n = ctypes.c_size_t()
+    _check(lib.dkss_plan_candidates(n_bits, None, 0, ctypes.byref(n)), "dkss_plan_candidates")
+    rows = np.zeros(10 * max(1, n.value), dtype=np.uint64)
+    _check(lib.dkss_plan_candidates(n_bits, rows.ctypes.data, n.value, ctypes.byref(n)), "dkss_plan_candidates")
+    return [dict(zip(CANDIDATE_FIELDS, [int(v) for v in rows[10 * i:10 * i + 10]])) for i in range(n.value)]

@@ -38,6 +38,7 @@ def _units():
     units = [("capi.o", os.path.join(CSRC, "capi.cu"), []),
              ("decode_static.o", os.path.join(CSRC, "decode_static.cu"), []),
              ("batch.o", os.path.join(CSRC, "batch.cu"), []),
+             ("mlp.o", os.path.join(CSRC, "mlp.cu"), []),
              ("host_math.o", os.path.join(CSRC, "host_math.cpp"), ["-x", "cu"])]
     for m, L, LR in TRIPLES:
         units.append(("inst_m%d_L%d_R%d.o" % (m, L, LR), os.path.join(CSRC, "inst.cu"),

@@ -443,6 +443,41 @@ dkss_status dkss_plan_rho(uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, u
     return dkss_plan_info(&pl, consts, n_consts, rho_out);
 }
 
+dkss_status dkss_plan_candidates(uint64_t n_bits, uint64_t* rows, size_t max_rows, size_t* n_rows) {
+    static const uint64_t primes[] = {12289, 40961, 65537, 786433, 7340033, 23068673, 104857601, 167772161,
+                                      469762049, 998244353};
+    static const uint32_t ms[] = {16, 32, 64};
+    static const uint32_t us[] = {8, 16, 24, 32};
+    if (!n_rows || n_bits == 0) return DKSS_EINVAL;
+    size_t n = 0;
+    for (uint32_t m : ms)
+        for (uint32_t u : us) {
+            const uint64_t per = (uint64_t)(m / 2) * u;
+            uint64_t M = 1;
+            while (M * per < n_bits || M <= m) M <<= 1;
+            for (uint64_t p : primes) {
+                if ((p - 1) % (2 * M) != 0) continue;
+                for (uint32_t z = 1; z <= 8; ++z) {
+                    dkss_plan_s pl;
+                    const dkss_status s = plan_host(&pl, n_bits, M, m, u, p, z);
+                    if (s == DKSS_EPARAM) continue;     // p^z below the bound: try the next z
+                    Kernels k;
+                    if (s == DKSS_OK && lookup(pl.m, pl.L, pl.LR, &k)) {
+                        if (rows && n < max_rows) {
+                            const uint64_t v[10] = {M, m, u, p, z, pl.L, pl.LR, (uint64_t)pl.col_levels + 1,
+                                                    pl.r_last, pl.P2};
+                            for (int i = 0; i < 10; ++i) rows[10 * n + i] = v[i];
+                        }
+                        ++n;
+                    }
+                    break;   // the smallest z that passes the bound (or an unsupported one) ends the search
+                }
+            }
+        }
+    *n_rows = n;
+    return DKSS_OK;
+}
+
 uint32_t dkss_plan_launches(dkss_plan_t pl) { return pl ? pl->launches : 0; }
 
 dkss_status dkss_sync_status(dkss_plan_t pl, dkss_stream_t stream) {

@@ -361,3 +361,49 @@ def test_c_oracle_alpha_points_match_full_transform(cfg):
     limbs = syn.from_int(a, syn.n_limbs(par.n_bits))
     for k in range(2 * par.m):
         assert oc.fft_alpha_point(limbs, par, k) == full[k * par.mu]
+
+
+# ---- cost model of the autotuner (float, outside the product path) ----------
+
+def test_mlp_oracle_gradient_matches_finite_differences():
+    import mlp_oracle as mo
+    rng = np.random.default_rng(0)
+    p = rng.normal(0, 0.3, mo.NPARAM)
+    x = rng.normal(0, 1, (7, mo.F))
+    t = rng.normal(0, 1, 7)
+    g = mo.grad(p, x, t)
+    h = 1e-6
+    for i in rng.choice(mo.NPARAM, 60, replace=False).tolist() + [mo.NPARAM - 1]:
+        e = np.zeros(mo.NPARAM)
+        e[i] = h
+        fd = (mo.loss(p + e, x, t) - mo.loss(p - e, x, t)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 + 1e-5 * abs(fd)
+
+
+def test_mlp_oracle_forward_closed_form():
+    import mlp_oracle as mo
+    # W1 = identity on the first F hidden units, W2 = identity, w3 = ones:
+    # y = sum_i relu(x_i + b1_i) + b3 with b2 = 0
+    p = np.zeros(mo.NPARAM)
+    W1, b1, W2, b2, w3, _ = [a for a in mo.unpack(p)]
+    o = 0
+    for j in range(mo.F):
+        p[o + j * mo.F + j] = 1.0
+    o_b1 = mo.H * mo.F
+    p[o_b1:o_b1 + mo.H] = 0.5
+    o_w2 = o_b1 + mo.H
+    for j in range(mo.H):
+        p[o_w2 + j * mo.H + j] = 1.0
+    o_w3 = o_w2 + mo.H * mo.H + mo.H
+    p[o_w3:o_w3 + mo.H] = 1.0
+    p[-1] = -2.0
+    x = np.array([np.linspace(-1, 1, mo.F)])
+    want = np.maximum(x[0] + 0.5, 0).sum() + 0.5 * (mo.H - mo.F) - 2.0
+    assert abs(mo.forward(p, x)[0] - want) < 1e-12
+
+
+def test_mlp_oracle_first_adam_step():
+    import mlp_oracle as mo
+    g = np.array([0.3, -2.0, 1e-3, 0.0])
+    p, m1, m2 = mo.adam_step(np.zeros(4), g, np.zeros(4), np.zeros(4), 0.01, 1)
+    assert np.allclose(p, -0.01 * g / (np.abs(g) + 1e-8))
