@@ -281,13 +281,13 @@ def run_ours(args):
         if ms <= 0:
             continue
         if k in work:
-            a = work[k][0] / (ms * 1e-3) / 1e12
-            stages[k] = {"bound": "alu", "ms": round(ms, 4), "achieved": round(a, 3), "unit": "TIMAD/s",
-                         "frac": round(a / peak, 4)}
+            ach = work[k][0] / (ms * 1e-3) / 1e12
+            stages[k] = {"bound": "alu", "ms": round(ms, 4), "achieved": round(ach, 3), "unit": "TIMAD/s",
+                         "frac": round(ach / peak, 4)}
         elif k in mem_bytes:
-            a = mem_bytes[k] / (ms * 1e-3) / 1e9
-            stages[k] = {"bound": "hbm", "ms": round(ms, 4), "achieved": round(a, 1), "unit": "GB/s",
-                         "frac": round(a / HBM_GBS, 4)}
+            ach = mem_bytes[k] / (ms * 1e-3) / 1e9
+            stages[k] = {"bound": "hbm", "ms": round(ms, 4), "achieved": round(ach, 1), "unit": "GB/s",
+                         "frac": round(ach / HBM_GBS, 4)}
     roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 3),
                 "unit": "TIMAD/s", "frac": round(achieved / peak, 4),
                 "traffic": NCU_TRAFFIC_BYTES.get((args.workload, args.form, dom)),
