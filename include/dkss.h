@@ -174,7 +174,11 @@ dkss_status dkss_mul_batch(const dkss_job* jobs, size_t count, uint32_t flags, d
  * receives rho's m coefficients as 2 words each; consts receives, in order:
  * 2M, 2M/2m, L (32-bit limbs per stored residue), transform levels, p^z low
  * word, p^z high word, generator zeta, omega low, omega high, gamma low,
- * gamma high, LR (26-bit limbs of the product arithmetic).
+ * gamma high, LR (26-bit limbs of the product arithmetic), the form of the
+ * R-multiplications (0 through the evaluation map, 1 direct convolution,
+ * 2 INT8 tensor cores; a ring outside the evaluation-map form's limits on its
+ * unreduced sums gets 1 unless the flags ask for 2), and 1 when that form
+ * scales one factor of each componentwise product first (else 0).
  */
 dkss_status dkss_plan_info(dkss_plan_t plan, uint64_t* consts, size_t n_consts, uint64_t* rho_out);
 

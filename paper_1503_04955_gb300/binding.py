@@ -102,9 +102,10 @@ def _words2_to_ints(arr):
     return [int(lo) | (int(hi) << 64) for lo, hi in zip(arr[0::2], arr[1::2])]
 
 
-N_CONSTS = 12
+N_CONSTS = 14
 CONST_NAMES = ["P2", "mu", "L", "levels", "pz_lo", "pz_hi", "zeta", "omega_lo", "omega_hi", "gamma_lo", "gamma_hi",
-               "LR"]
+               "LR", "rmul", "prescale"]
+RMUL_FORMS = ("ntt", "direct", "int8tc")     # consts["rmul"] indexes this
 
 
 def _consts_dict(c):

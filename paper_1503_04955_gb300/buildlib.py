@@ -39,7 +39,8 @@ def _units():
              ("decode_static.o", os.path.join(CSRC, "decode_static.cu"), []),
              ("batch.o", os.path.join(CSRC, "batch.cu"), []),
              ("mlp.o", os.path.join(CSRC, "mlp.cu"), []),
-             ("host_math.o", os.path.join(CSRC, "host_math.cpp"), ["-x", "cu"])]
+             ("host_math.o", os.path.join(CSRC, "host_math.cpp"), ["-x", "cu"]),
+             ("ntt_bounds.o", os.path.join(CSRC, "ntt_bounds.cpp"), ["-x", "cu"])]
     for m, L, LR in TRIPLES:
         units.append(("inst_m%d_L%d_R%d.o" % (m, L, LR), os.path.join(CSRC, "inst.cu"),
                       ["-DDKSS_INST_M=%d" % m, "-DDKSS_INST_L=%d" % L, "-DDKSS_INST_LR=%d" % LR]))

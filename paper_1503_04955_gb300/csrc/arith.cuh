@@ -59,23 +59,146 @@ __device__ __forceinline__ void cond_sub(uint32_t (&x)[L], const Mod<L>& md) {
     for (int i = 0; i < L; ++i) x[i] = borrow ? x[i] : d[i];
 }
 
-// r = (a + b) mod q for a, b in [0, q)
+// Modular addition and subtraction with the limb carries in the condition-code
+// chain (add.cc / addc / sub.cc / subc in one asm block, so nothing can come
+// between the instructions of a chain): a + b, then a - q with its borrow
+// choosing the result; a - b, then + (q & borrow mask).
+template <int L>
+__device__ __forceinline__ void add_mod_ptx(uint32_t (&r)[L], const uint32_t (&a)[L], const uint32_t (&b)[L],
+                                            const uint32_t (&q)[L]);
+template <int L>
+__device__ __forceinline__ void sub_mod_ptx(uint32_t (&r)[L], const uint32_t (&a)[L], const uint32_t (&b)[L],
+                                            const uint32_t (&q)[L]);
+
+template <>
+__device__ __forceinline__ void add_mod_ptx<2>(uint32_t (&r)[2], const uint32_t (&a)[2], const uint32_t (&b)[2],
+                                          const uint32_t (&q)[2]) {
+    asm("{\n\t.reg .u32 s0,s1,d0,d1,bw;\n\t.reg .pred p;\n\t"
+        "add.cc.u32 s0, %2, %4;\n\t"
+        "addc.u32 s1, %3, %5;\n\t"
+        "sub.cc.u32 d0, s0, %6;\n\t"
+        "subc.cc.u32 d1, s1, %7;\n\t"
+        "subc.u32 bw, 0, 0;\n\t"
+        "setp.ne.u32 p, bw, 0;\n\t"
+        "selp.b32 %0, s0, d0, p;\n\t"
+        "selp.b32 %1, s1, d1, p;\n\t"
+        "}"
+        : "=r"(r[0]), "=r"(r[1])
+        : "r"(a[0]), "r"(a[1]), "r"(b[0]), "r"(b[1]), "r"(q[0]), "r"(q[1]));
+}
+
+template <>
+__device__ __forceinline__ void add_mod_ptx<3>(uint32_t (&r)[3], const uint32_t (&a)[3], const uint32_t (&b)[3],
+                                          const uint32_t (&q)[3]) {
+    asm("{\n\t.reg .u32 s0,s1,s2,d0,d1,d2,bw;\n\t.reg .pred p;\n\t"
+        "add.cc.u32 s0, %3, %6;\n\t"
+        "addc.cc.u32 s1, %4, %7;\n\t"
+        "addc.u32 s2, %5, %8;\n\t"
+        "sub.cc.u32 d0, s0, %9;\n\t"
+        "subc.cc.u32 d1, s1, %10;\n\t"
+        "subc.cc.u32 d2, s2, %11;\n\t"
+        "subc.u32 bw, 0, 0;\n\t"
+        "setp.ne.u32 p, bw, 0;\n\t"
+        "selp.b32 %0, s0, d0, p;\n\t"
+        "selp.b32 %1, s1, d1, p;\n\t"
+        "selp.b32 %2, s2, d2, p;\n\t"
+        "}"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(q[0]), "r"(q[1]), "r"(q[2]));
+}
+
+template <>
+__device__ __forceinline__ void add_mod_ptx<4>(uint32_t (&r)[4], const uint32_t (&a)[4], const uint32_t (&b)[4],
+                                          const uint32_t (&q)[4]) {
+    asm("{\n\t.reg .u32 s0,s1,s2,s3,d0,d1,d2,d3,bw;\n\t.reg .pred p;\n\t"
+        "add.cc.u32 s0, %4, %8;\n\t"
+        "addc.cc.u32 s1, %5, %9;\n\t"
+        "addc.cc.u32 s2, %6, %10;\n\t"
+        "addc.u32 s3, %7, %11;\n\t"
+        "sub.cc.u32 d0, s0, %12;\n\t"
+        "subc.cc.u32 d1, s1, %13;\n\t"
+        "subc.cc.u32 d2, s2, %14;\n\t"
+        "subc.cc.u32 d3, s3, %15;\n\t"
+        "subc.u32 bw, 0, 0;\n\t"
+        "setp.ne.u32 p, bw, 0;\n\t"
+        "selp.b32 %0, s0, d0, p;\n\t"
+        "selp.b32 %1, s1, d1, p;\n\t"
+        "selp.b32 %2, s2, d2, p;\n\t"
+        "selp.b32 %3, s3, d3, p;\n\t"
+        "}"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(q[0]), "r"(q[1]), "r"(q[2]), "r"(q[3]));
+}
+
+template <>
+__device__ __forceinline__ void sub_mod_ptx<2>(uint32_t (&r)[2], const uint32_t (&a)[2], const uint32_t (&b)[2],
+                                          const uint32_t (&q)[2]) {
+    asm("{\n\t.reg .u32 d0,d1,t0,t1,bw;\n\t.reg .pred p;\n\t"
+        "sub.cc.u32 d0, %2, %4;\n\t"
+        "subc.cc.u32 d1, %3, %5;\n\t"
+        "subc.u32 bw, 0, 0;\n\t"
+        "and.b32 t0, %6, bw;\n\t"
+        "and.b32 t1, %7, bw;\n\t"
+        "add.cc.u32 %0, d0, t0;\n\t"
+        "addc.u32 %1, d1, t1;\n\t"
+        "}"
+        : "=r"(r[0]), "=r"(r[1])
+        : "r"(a[0]), "r"(a[1]), "r"(b[0]), "r"(b[1]), "r"(q[0]), "r"(q[1]));
+}
+
+template <>
+__device__ __forceinline__ void sub_mod_ptx<3>(uint32_t (&r)[3], const uint32_t (&a)[3], const uint32_t (&b)[3],
+                                          const uint32_t (&q)[3]) {
+    asm("{\n\t.reg .u32 d0,d1,d2,t0,t1,t2,bw;\n\t.reg .pred p;\n\t"
+        "sub.cc.u32 d0, %3, %6;\n\t"
+        "subc.cc.u32 d1, %4, %7;\n\t"
+        "subc.cc.u32 d2, %5, %8;\n\t"
+        "subc.u32 bw, 0, 0;\n\t"
+        "and.b32 t0, %9, bw;\n\t"
+        "and.b32 t1, %10, bw;\n\t"
+        "and.b32 t2, %11, bw;\n\t"
+        "add.cc.u32 %0, d0, t0;\n\t"
+        "addc.cc.u32 %1, d1, t1;\n\t"
+        "addc.u32 %2, d2, t2;\n\t"
+        "}"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(q[0]), "r"(q[1]), "r"(q[2]));
+}
+
+template <>
+__device__ __forceinline__ void sub_mod_ptx<4>(uint32_t (&r)[4], const uint32_t (&a)[4], const uint32_t (&b)[4],
+                                          const uint32_t (&q)[4]) {
+    asm("{\n\t.reg .u32 d0,d1,d2,d3,t0,t1,t2,t3,bw;\n\t.reg .pred p;\n\t"
+        "sub.cc.u32 d0, %4, %8;\n\t"
+        "subc.cc.u32 d1, %5, %9;\n\t"
+        "subc.cc.u32 d2, %6, %10;\n\t"
+        "subc.cc.u32 d3, %7, %11;\n\t"
+        "subc.u32 bw, 0, 0;\n\t"
+        "and.b32 t0, %12, bw;\n\t"
+        "and.b32 t1, %13, bw;\n\t"
+        "and.b32 t2, %14, bw;\n\t"
+        "and.b32 t3, %15, bw;\n\t"
+        "add.cc.u32 %0, d0, t0;\n\t"
+        "addc.cc.u32 %1, d1, t1;\n\t"
+        "addc.cc.u32 %2, d2, t2;\n\t"
+        "addc.u32 %3, d3, t3;\n\t"
+        "}"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(q[0]), "r"(q[1]), "r"(q[2]), "r"(q[3]));
+}
+
+// r = (a + b) mod q for a, b in [0, q)  (q < 2^(32L-1), so a + b fits)
 template <int L>
 __device__ __forceinline__ void add_mod(uint32_t (&r)[L], const uint32_t (&a)[L], const uint32_t (&b)[L],
                                         const Mod<L>& md) {
-    add_n<L>(r, a, b);
-    cond_sub<L>(r, md);
+    add_mod_ptx<L>(r, a, b, md.q);
 }
 
 // r = (a - b) mod q for a, b in [0, q)
 template <int L>
 __device__ __forceinline__ void sub_mod(uint32_t (&r)[L], const uint32_t (&a)[L], const uint32_t (&b)[L],
                                         const Mod<L>& md) {
-    uint32_t borrow = sub_n<L>(r, a, b);
-    uint32_t t[L];
-    add_n<L>(t, r, md.q);
-#pragma unroll
-    for (int i = 0; i < L; ++i) r[i] = borrow ? t[i] : r[i];
+    sub_mod_ptx<L>(r, a, b, md.q);
 }
 
 // r = (q - a) mod q

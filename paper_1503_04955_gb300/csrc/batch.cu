@@ -247,7 +247,7 @@ dkss_status dkss_batch_plan(dkss_batch_t* out, const uint64_t* n_bits, size_t co
         auto t = std::make_unique<ClassTables>();
         s = dkss_planning::plan_host(&t->host, b->class_N[c], b->class_params[c].M, kBm, b->class_params[c].u, kBp,
                                      kBz);
-        if (s == DKSS_OK && (t->host.L != kBL || t->host.LR != kBLR)) s = DKSS_EUNSUPPORTED;
+        if (s == DKSS_OK && (t->host.L != kBL || t->host.LR != kBLR || !t->host.ntt_ok)) s = DKSS_EUNSUPPORTED;
         if (s == DKSS_OK) {
             std::vector<uint32_t> ev, nt;
             dkss_planning::build_eval_table(&t->host, ev);
@@ -303,6 +303,7 @@ dkss_status dkss_batch_plan(dkss_batch_t* out, const uint64_t* n_bits, size_t co
         lp.table = t.d_eval;
         lp.table_eval = t.d_eval;
         lp.ntt_cst = t.d_ntt;
+        lp.ntt_prescale = h.ntt_bias.prescale ? 1u : 0u;
         lp.poly_words = h.P2 * kBm * kBL;
         lp.P2 = h.P2;
         lp.mu_top = h.mu_top;
@@ -379,7 +380,8 @@ dkss_status dkss_batch_plan(dkss_batch_t* out, const uint64_t* n_bits, size_t co
     }
 
     // persistent grid: as many CTAs as can be resident
-    b->smem = std::max(sizeof(uint32_t) * (size_t)G::TWO_M * G::EW, sizeof(uint32_t) * 2 * max_rlast * G::EW);
+    b->smem = std::max({sizeof(uint32_t) * (size_t)G::TWO_M * G::EW, sizeof(uint32_t) * 2 * max_rlast * G::EW,
+                        sizeof(uint32_t) * (size_t)dkss::kDecSmemWords});
     int per_sm = 0, sms = 0, optin = 0;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device) != cudaSuccess ||
         (int)b->smem > optin ||

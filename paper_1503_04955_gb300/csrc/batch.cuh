@@ -117,8 +117,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(const BatchJob* __restric
                     dft_inv_column<m, L>(lp, md, smem, local);
                     break;
                 case kStDecTiles:
-                    if (jb.dp.u == 32) decode_tile_aligned<L, 1>(jb.dp, local);
-                    else if (jb.dp.u == 16) decode_tile_aligned<L, 2>(jb.dp, local);
+                    if (jb.dp.u == 32) decode_tile_aligned<L, 1>(jb.dp, local, smem);
+                    else if (jb.dp.u == 16) decode_tile_aligned<L, 2>(jb.dp, local, smem);
                     else decode_tile<L>(jb.dp, local);
                     break;
                 case kStDecScan:

@@ -186,6 +186,8 @@ dkss_status plan_host(dkss_plan_s* pl, uint64_t n_bits, uint64_t M, uint32_t m, 
     u128 rdev_m = c.to(rdev);
     u128 ks = c.from(c.mul(c.mul(p2inv, rdev_m), rdev_m));
     for (uint32_t i = 0; i < 5; ++i) pl->kscale[i] = i < LR ? (uint32_t)(ks >> (26 * i)) & ((1u << 26) - 1) : 0;
+    // limits of the lazy transform in R (NTT form of the R-multiplications)
+    pl->ntt_ok = ntt_lazy_bounds(m, LR, q, &pl->ntt_bias);
     return DKSS_OK;
 }
 
@@ -235,7 +237,8 @@ void build_ntt_consts(const dkss_plan_s* pl, std::vector<uint32_t>& out) {
     const uint32_t m = pl->m, LR = pl->LR;
     uint32_t lg = 0;
     while ((1u << lg) < m) ++lg;
-    const uint32_t Q = 2 * m + lg, COUNT = Q + 5;
+    // layout of NttLayout<m> (ntt_rmul.cuh)
+    const uint32_t Q = 2 * m + lg + 2, COUNT = Q + 7;
     out.assign((size_t)COUNT * LR, 0);
     MontCtx c(pl->q);
     const u128 rdev = pow2_mod(26 * (int)LR, pl->q);
@@ -246,7 +249,13 @@ void build_ntt_consts(const dkss_plan_s* pl, std::vector<uint32_t>& out) {
         put_rr(&out[(size_t)k * LR], to_dev(c, c.pow(psi, brv(k, lg)), rdev), LR);
         put_rr(&out[(size_t)(m + k) * LR], to_dev(c, c.pow(psi_inv, brv(k, lg)), rdev), LR);
     }
-    for (uint32_t b = 0; b < lg; ++b) put_rr(&out[(size_t)(2 * m + b) * LR], pl->q << b, LR);
+    // lazy-arithmetic biases (ntt_bounds.cpp): backwards stages, forward, negation
+    for (uint32_t b = 0; b < lg; ++b)
+        for (uint32_t i = 0; i < LR; ++i) out[(size_t)(2 * m + b) * LR + i] = pl->ntt_bias.bwd[b][i];
+    for (uint32_t i = 0; i < LR; ++i) {
+        out[(size_t)(2 * m + lg) * LR + i] = pl->ntt_bias.fwd[i];
+        out[(size_t)(2 * m + lg + 1) * LR + i] = pl->ntt_bias.neg[i];
+    }
     put_rr(&out[(size_t)Q * LR], pl->q, LR);
     const u128 minv = c.pow(c.to(m), phi - 1);
     const u128 p2inv = c.pow(c.to(pl->P2 % pl->q), phi - 1);
@@ -258,6 +267,9 @@ void build_ntt_consts(const dkss_plan_s* pl, std::vector<uint32_t>& out) {
     const u128 rdev_m = c.to(rdev);
     put_rr(&out[(size_t)(Q + 3) * LR], to_dev(c, c.mul(c.mul(minv, p2inv), rdev_m), rdev), LR);
     put_rr(&out[(size_t)(Q + 4) * LR], to_dev(c, c.mul(c.mul(c.mul(zlast, minv), p2inv), rdev_m), rdev), LR);
+    // last backwards stage after a prescaled componentwise product: 1 and psi^-1
+    put_rr(&out[(size_t)(Q + 5) * LR], rdev, LR);
+    put_rr(&out[(size_t)(Q + 6) * LR], to_dev(c, zlast, rdev), LR);
 }
 
 // Evaluations of the bad twiddles: rho^s(gamma^(2j+1)) = omega^(s(2j+1)), stored
@@ -316,11 +328,13 @@ bool overlap(const void* a, size_t an, const void* b, size_t bn) {
 }
 
 void fill_consts(const dkss_plan_s* pl, uint64_t* consts, size_t n) {
-    uint64_t v[12] = {pl->P2, pl->mu_top, pl->L, (uint64_t)pl->col_levels + 1, (uint64_t)pl->q,
+    const uint64_t form = (pl->flags & DKSS_FORM_INT8TC) ? 2 : ((pl->flags & DKSS_RMUL_DIRECT) || !pl->ntt_ok) ? 1 : 0;
+    uint64_t v[14] = {pl->P2, pl->mu_top, pl->L, (uint64_t)pl->col_levels + 1, (uint64_t)pl->q,
                       (uint64_t)(pl->q >> 64), pl->roots.zeta, (uint64_t)pl->roots.omega,
                       (uint64_t)(pl->roots.omega >> 64), (uint64_t)pl->roots.gamma,
-                      (uint64_t)(pl->roots.gamma >> 64), pl->LR};
-    for (size_t i = 0; i < n && i < 12; ++i) consts[i] = v[i];
+                      (uint64_t)(pl->roots.gamma >> 64), pl->LR, form,
+                      (uint64_t)(form == 0 && pl->ntt_bias.prescale)};
+    for (size_t i = 0; i < n && i < 14; ++i) consts[i] = v[i];
 }
 
 }  // namespace
@@ -343,6 +357,8 @@ dkss_status dkss_plan(dkss_plan_t* plan, uint64_t n_bits, uint64_t M, uint32_t m
         delete pl;
         return s;
     }
+    // a ring outside the lazy transform's limits takes the direct convolution
+    if (!pl->ntt_ok && !(flags & (DKSS_RMUL_DIRECT | DKSS_FORM_INT8TC))) pl->flags |= DKSS_RMUL_DIRECT;
     if (cudaGetDevice(&pl->device) != cudaSuccess) {
         delete pl;
         return DKSS_ECUDA;

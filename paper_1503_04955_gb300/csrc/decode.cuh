@@ -13,6 +13,7 @@
 #pragma once
 #include <cstdint>
 
+#include "arith.cuh"
 #include "status_bits.hpp"
 
 namespace dkss {
@@ -177,83 +178,119 @@ __global__ void __launch_bounds__(kDecThreads) k_decode_tiles(DecodeParams p) {
     decode_tile<L>(p, blockIdx.x);
 }
 
-// Same tile kernel for u = 32/R (R = 1, 2): digit k sits at bit u*k, so window
-// j takes limb t of the digits k = R(j - t) + s, shifted by u*s bits.  A thread
-// loads each digit its 9 windows (j0-1 .. j0+7) touch once into registers.
+// Same tile for u = 32/R (R = 1, 2): digit k sits at bit u*k, so the digits
+// R j .. R j + R - 1 start in window j and reach windows j .. j + T - 1.
+// Lane x of a warp owns window j = chunk + x: it loads its R digits (lanes
+// read consecutive residues, so a warp's loads are contiguous), cuts them into
+// the pieces P_t landing in windows j + t, and takes the pieces of window j
+// from lanes x - t with shuffles (from the previous chunk across the warp's
+// edge).  Window values go through shared memory (sbuf: kDecSmemWords words)
+// to the layout of decode_tile_finish, 8 consecutive windows per thread.
+constexpr int kDecSmemWords = kDecTile + kDecTile / 4;
+
 template <int L, int R>
-__device__ __forceinline__ void decode_tile_aligned(const DecodeParams& p, uint64_t tile) {
+__device__ __forceinline__ void decode_tile_aligned(const DecodeParams& p, uint64_t tile, uint32_t* sbuf) {
     constexpr int U = 32 / R;
-    constexpr int T = L + 2;                 // limbs a shifted digit can reach
-    constexpr int NW = kDecWPT + 1;          // windows j0-1 .. j0+7
-    constexpr int NK = R * (NW + T - 1);     // digits touching them
-    const int64_t j0 = (int64_t)tile * kDecTile + (int64_t)threadIdx.x * kDecWPT;
-    const int64_t jb = j0 - 1;
-    const int64_t base_k = (int64_t)R * (jb - T + 1);
+    constexpr int T = L + 2;                               // windows a digit reaches
+    constexpr int PER_WARP = kDecTile / (kDecThreads / 32);
+    uint32_t* s_wv = sbuf;
+    uint8_t* s_gp = reinterpret_cast<uint8_t*>(sbuf + kDecTile);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t jt = (int64_t)tile * kDecTile;
+    const int64_t jw = jt + (int64_t)warp * PER_WARP;
     const uint32_t hshift = 31 - __clz(p.h);
-    uint32_t D[NK][L + 1];
+    uint64_t Pprev[T], Sprev = 0;
 #pragma unroll
-    for (int n = 0; n < NK; ++n) {
-        const int64_t k = base_k + n;
+    for (int t = 0; t < T; ++t) Pprev[t] = 0;
+    for (int it = -1; it < PER_WARP / 32; ++it) {
+        const int64_t j = jw + 32 * it + lane;
+        uint64_t P[T];
 #pragma unroll
-        for (int w = 0; w <= L; ++w) D[n][w] = 0;
-        if (k < 0 || (uint64_t)k >= p.k_max) continue;
-        const uint64_t i = (uint64_t)k >> hshift;
-        const uint32_t t = (uint32_t)k & (p.h - 1);
-        if (i < p.P2) {
-            const uint32_t* s = p.c + (i * p.m + t) * L;
+        for (int t = 0; t < T; ++t) P[t] = 0;
 #pragma unroll
-            for (int w = 0; w < L; ++w) D[n][w] = s[w];
-        }
-        if (i >= 1 && i - 1 < p.P2) {
-            const uint32_t* s = p.c + ((i - 1) * p.m + t + p.h) * L;
-            uint32_t carry = 0;
+        for (int s = 0; s < R; ++s) {
+            const int64_t k = (int64_t)R * j + s;
+            uint32_t D[L + 1];
 #pragma unroll
-            for (int w = 0; w < L; ++w) {
-                uint64_t x = (uint64_t)D[n][w] + s[w] + carry;
-                D[n][w] = (uint32_t)x;
-                carry = (uint32_t)(x >> 32);
+            for (int w = 0; w <= L; ++w) D[w] = 0;
+            if (k >= 0 && (uint64_t)k < p.k_max) {
+                const uint64_t i = (uint64_t)k >> hshift;
+                const uint32_t t = (uint32_t)k & (p.h - 1);
+                uint32_t y[L];
+                if (i < p.P2) {
+                    ld_res<L>(y, p.c + (i * p.m + t) * L);
+#pragma unroll
+                    for (int w = 0; w < L; ++w) D[w] = y[w];
+                }
+                if (i >= 1 && i - 1 < p.P2) {
+                    ld_res<L>(y, p.c + ((i - 1) * p.m + t + p.h) * L);
+                    uint32_t carry = 0;
+#pragma unroll
+                    for (int w = 0; w < L; ++w) {
+                        const uint64_t x = (uint64_t)D[w] + y[w] + carry;
+                        D[w] = (uint32_t)x;
+                        carry = (uint32_t)(x >> 32);
+                    }
+                    D[L] = carry;
+                }
             }
-            D[n][L] += carry;
-        }
-    }
-    uint64_t S[NW];
 #pragma unroll
-    for (int w = 0; w < NW; ++w) {
-        uint64_t acc = 0;
-#pragma unroll
-        for (int t = 0; t < T; ++t) {
-#pragma unroll
-            for (int s = 0; s < R; ++s) {
-                const int n = R * (w - t + T - 1) + s;
-                const int sh = 32 * t - U * s;   // bit of the digit at the window start
+            for (int t = 0; t < T; ++t) {
+                const int sh = 32 * t - U * s;   // bit of the digit at the start of window j + t
                 uint32_t piece;
                 if (sh < 0) {
-                    piece = D[n][0] << (-sh);
+                    piece = D[0] << (-sh);
                 } else {
                     const int lw = sh >> 5, bs = sh & 31;
-                    const uint32_t a = lw <= L ? D[n][lw] : 0u;
-                    const uint32_t b = lw + 1 <= L ? D[n][lw + 1] : 0u;
+                    const uint32_t a = lw <= L ? D[lw] : 0u;
+                    const uint32_t b = lw + 1 <= L ? D[lw + 1] : 0u;
                     piece = bs ? ((a >> bs) | (b << (32 - bs))) : a;
                 }
-                acc += piece;
+                P[t] += piece;
             }
         }
-        S[w] = (jb + w >= 0 && (uint64_t)(jb + w) < p.n_windows) ? acc : 0;
+        // window j's pieces: P_t of lane x - t (lane y sends to lane y + t, or
+        // across the edge its previous chunk's piece)
+        uint64_t S = P[0];
+#pragma unroll
+        for (int t = 1; t < T; ++t) {
+            const uint64_t send = lane + t < 32 ? P[t] : Pprev[t];
+            const int src = (lane - t) & 31;
+            const uint32_t lo = __shfl_sync(0xffffffffu, (uint32_t)send, src);
+            const uint32_t hi = __shfl_sync(0xffffffffu, (uint32_t)(send >> 32), src);
+            S += ((uint64_t)hi << 32) | lo;
+        }
+        if (j < 0 || (uint64_t)j >= p.n_windows) S = 0;
+        // T_j = (S_j mod 2^32) + (S_(j-1) div 2^32)
+        const uint64_t sendS = lane == 31 ? Sprev : S;
+        const uint32_t phi = __shfl_sync(0xffffffffu, (uint32_t)(sendS >> 32), (lane - 1) & 31);
+        if (it >= 0) {
+            const uint64_t T2 = (S & 0xffffffffull) + phi;
+            const uint32_t v = (uint32_t)T2;
+            s_wv[j - jt] = v;
+            s_gp[j - jt] = (uint8_t)((uint32_t)(T2 >> 32) | ((v == 0xffffffffu) ? 2u : 0u));
+        }
+#pragma unroll
+        for (int t = 0; t < T; ++t) Pprev[t] = P[t];
+        Sprev = S;
     }
+    __syncthreads();
     uint32_t wv[kDecWPT], gbit = 0, pbit = 0;
 #pragma unroll
     for (int w = 0; w < kDecWPT; ++w) {
-        uint64_t T2 = (S[w + 1] & 0xffffffffull) + (S[w] >> 32);
-        wv[w] = (uint32_t)T2;
-        gbit |= (uint32_t)(T2 >> 32) << w;
-        pbit |= (uint32_t)(wv[w] == 0xffffffffu) << w;
+        const int idx = threadIdx.x * kDecWPT + w;
+        wv[w] = s_wv[idx];
+        const uint32_t gp = s_gp[idx];
+        gbit |= (gp & 1u) << w;
+        pbit |= ((gp >> 1) & 1u) << w;
     }
-    decode_tile_finish(p, (uint64_t)j0, wv, gbit, pbit, tile);
+    decode_tile_finish(p, (uint64_t)(jt + threadIdx.x * kDecWPT), wv, gbit, pbit, tile);
 }
 
 template <int L, int R>
 __global__ void __launch_bounds__(kDecThreads) k_decode_tiles_aligned(DecodeParams p) {
-    decode_tile_aligned<L, R>(p, blockIdx.x);
+    __shared__ uint32_t sbuf[kDecSmemWords];
+    decode_tile_aligned<L, R>(p, blockIdx.x, sbuf);
 }
 
 // One CTA of THREADS threads: exclusive scan of the tile aggregates into

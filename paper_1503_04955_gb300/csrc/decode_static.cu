@@ -30,8 +30,10 @@ uint32_t* g_scratch_ptr[kMaxDevices] = {nullptr};
 
 template <int L>
 void launch(const dkss::DecodeParams& dp, uint32_t u, cudaStream_t st) {
-    if (u == 32) dkss::k_decode_tiles_aligned<L, 1><<<(unsigned)dp.n_tiles, dkss::kDecThreads, 0, st>>>(dp);
-    else if (u == 16) dkss::k_decode_tiles_aligned<L, 2><<<(unsigned)dp.n_tiles, dkss::kDecThreads, 0, st>>>(dp);
+    // the u = 32 and u = 16 kernels read residues with L-word vector loads
+    const bool vec_ok = (uintptr_t)dp.c % (L == 3 ? 4u : 4u * L) == 0;
+    if (u == 32 && vec_ok) dkss::k_decode_tiles_aligned<L, 1><<<(unsigned)dp.n_tiles, dkss::kDecThreads, 0, st>>>(dp);
+    else if (u == 16 && vec_ok) dkss::k_decode_tiles_aligned<L, 2><<<(unsigned)dp.n_tiles, dkss::kDecThreads, 0, st>>>(dp);
     else dkss::k_decode_tiles<L><<<(unsigned)dp.n_tiles, dkss::kDecThreads, 0, st>>>(dp);
 }
 

@@ -64,6 +64,7 @@ struct LevelParams {
     const uint32_t* table_eval;  // rho^s(gamma^(2 brv(i)+1)) R', s < mu_top, i < m: LR words each
     const uint32_t* ntt_cst;     // NttLayout<m> constants, LR words each
     uint32_t i8_S;               // bytes per residue (INT8 tensor-core form)
+    uint32_t ntt_prescale;       // NTT form: scale b before the componentwise product
 };
 
 // How R-multiplications are computed.
@@ -167,13 +168,14 @@ __device__ void dft_dit(uint32_t* s0, uint32_t* s1, int arrays, int n, int root,
 #pragma unroll
             for (int c = 0; c < G::CPL; ++c) {
                 int t = tm.lane + c * G::TEAM;
-                uint32_t sa[L], sb[L];
-                if (ng[c]) {
-                    sub_mod<L>(sa, a[c], y[c], md);
-                    add_mod<L>(sb, a[c], y[c], md);
-                } else {
-                    add_mod<L>(sa, a[c], y[c], md);
-                    sub_mod<L>(sb, a[c], y[c], md);
+                // a + y and a - y, swapped where the shifted coefficient carries a minus sign
+                uint32_t pl[L], mi[L], sa[L], sb[L];
+                add_mod<L>(pl, a[c], y[c], md);
+                sub_mod<L>(mi, a[c], y[c], md);
+#pragma unroll
+                for (int w = 0; w < L; ++w) {
+                    sa[w] = ng[c] ? mi[w] : pl[w];
+                    sb[w] = ng[c] ? pl[w] : mi[w];
                 }
                 st_res<L>(s + ia * G::EW + t * L, sa);
                 st_res<L>(s + ib * G::EW + t * L, sb);
@@ -218,8 +220,13 @@ __device__ void dft_dif(uint32_t* s, int n, int root, const Mod<L>& md) {
                 }
                 ld_res<L>(a, s + ia * G::EW + src * L);
                 ld_res<L>(b, s + ib * G::EW + src * L);
-                if (neg) sub_mod<L>(db[c], b, a, md);
-                else sub_mod<L>(db[c], a, b, md);
+                uint32_t x[L], y[L];
+#pragma unroll
+                for (int w = 0; w < L; ++w) {
+                    x[w] = neg ? b[w] : a[w];
+                    y[w] = neg ? a[w] : b[w];
+                }
+                sub_mod<L>(db[c], x, y, md);
             }
             __syncwarp(tm.mask);
 #pragma unroll
@@ -439,10 +446,11 @@ __global__ void __launch_bounds__(kThreads) k_twiddle(LevelParams prm, ModRR<LR>
 }
 
 // Coefficients l and l + m/2 of alpha^r x (x: m residues of L words) in
-// 26-bit limbs: coefficient t of alpha^r x is +-x[(t - r) mod m].
+// 26-bit limbs: coefficient t of alpha^r x is +-x[(t - r) mod m]; a negated
+// one is the lazy bias(K p^z) - x (ntt_rmul.cuh).
 template <int m, int L, int LR>
 __device__ __forceinline__ void load_shifted_rr(uint32_t (&out)[LR], const uint32_t* x, int t, int r,
-                                                const ModRR<LR>& md) {
+                                                const uint32_t (&bn)[LR]) {
     int src = t - r;
     bool neg = false;
     if (src < 0) {
@@ -453,10 +461,11 @@ __device__ __forceinline__ void load_shifted_rr(uint32_t (&out)[LR], const uint3
             neg = false;
         }
     }
-    uint32_t v[L];
+    uint32_t v[L], y[LR];
     ld_res<L>(v, x + src * L);
-    to_rr<L, LR>(out, v);
-    if (neg) neg_rr<LR>(out, out, md);
+    to_rr<L, LR>(y, v);
+#pragma unroll
+    for (int i = 0; i < LR; ++i) out[i] = neg ? bn[i] - y[i] : y[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -482,8 +491,10 @@ __device__ __forceinline__ void twiddle_ntt_group(const LevelParams& prm, const 
     uint32_t* x = poly + (blk * prm.len + v * mu_d + l) * G::EW;
     const int lane = tm.lane;
     uint32_t lo[LR], hi[LR];
-    load_shifted_rr<m, L, LR>(lo, x, lane, r, mr);
-    load_shifted_rr<m, L, LR>(hi, x, lane + m / 2, r, mr);
+    uint32_t bn[LR];
+    ldg_rr<LR>(bn, prm.ntt_cst + NttLayout<m>::BN * LR);
+    load_shifted_rr<m, L, LR>(lo, x, lane, r, bn);
+    load_shifted_rr<m, L, LR>(hi, x, lane + m / 2, r, bn);
     ntt_forward<m, LR>(lo, hi, lane, tm.mask, prm.ntt_cst, mr);
     uint32_t t0[LR], t1[LR];
     const uint32_t* tw = prm.table_eval + (sidx * m + 2 * lane) * LR;
@@ -492,6 +503,8 @@ __device__ __forceinline__ void twiddle_ntt_group(const LevelParams& prm, const 
     mmul<LR>(lo, lo, t0, mr);
     mmul<LR>(hi, hi, t1, mr);
     ntt_backward<m, LR>(lo, hi, lane, tm.mask, prm.ntt_cst, NttLayout<m>::TW_LO, NttLayout<m>::TW_HI, mr);
+    canon<LR>(lo, lo, mr);
+    canon<LR>(hi, hi, mr);
     __syncwarp(tm.mask);   // every lane has read its shifted inputs before any write
     uint32_t o[L];
     from_rr<L, LR>(o, lo);
@@ -578,9 +591,23 @@ __device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>
             to_rr<L, LR>(bhi, w);
             ntt_forward<m, LR>(alo, ahi, lane, tm.mask, prm.ntt_cst, mr);
             ntt_forward<m, LR>(blo, bhi, lane, tm.mask, prm.ntt_cst, mr);
-            mmul<LR>(alo, alo, blo, mr);
-            mmul<LR>(ahi, ahi, bhi, mr);
-            ntt_backward<m, LR>(alo, ahi, lane, tm.mask, prm.ntt_cst, NttLayout<m>::PW_LO, NttLayout<m>::PW_HI, mr);
+            if (prm.ntt_prescale) {
+                // scale b first so that the product of two lazy evaluations stays in range
+                uint32_t c[LR];
+                ldg_rr<LR>(c, prm.ntt_cst + NttLayout<m>::PW_LO * LR);
+                mmul<LR>(blo, blo, c, mr);
+                mmul<LR>(bhi, bhi, c, mr);
+                mmul<LR>(alo, alo, blo, mr);
+                mmul<LR>(ahi, ahi, bhi, mr);
+                ntt_backward<m, LR>(alo, ahi, lane, tm.mask, prm.ntt_cst, NttLayout<m>::ONE, NttLayout<m>::ZLAST, mr);
+            } else {
+                mmul<LR>(alo, alo, blo, mr);
+                mmul<LR>(ahi, ahi, bhi, mr);
+                ntt_backward<m, LR>(alo, ahi, lane, tm.mask, prm.ntt_cst, NttLayout<m>::PW_LO, NttLayout<m>::PW_HI,
+                                    mr);
+            }
+            canon<LR>(alo, alo, mr);
+            canon<LR>(ahi, ahi, mr);
             from_rr<L, LR>(w, alo);
             st_res<L>(sa + v * G::EW + lane * L, w);
             from_rr<L, LR>(w, ahi);

@@ -40,6 +40,7 @@ static LevelParams make_level(const dkss_plan_s* pl) {
     lp.table_eval = pl->d_table;
     lp.ntt_cst = pl->d_ntt;
     lp.i8_S = pl->i8_S;
+    lp.ntt_prescale = pl->ntt_bias.prescale ? 1u : 0u;
     return lp;
 }
 

@@ -1,0 +1,292 @@
+// Worst-case limb and value bounds of the lazy NTT-form R-multiplication
+// (see ntt_bounds.hpp for what is checked and why).
+#include "ntt_bounds.hpp"
+
+#include <algorithm>
+#include <vector>
+
+namespace dkss_planning {
+namespace {
+
+using dkss_host::u128;
+constexpr uint64_t kM26 = (1u << 26) - 1;
+
+// Unsigned integer of any size, little-endian base 2^32 (bounds only).
+struct Big {
+    std::vector<uint32_t> w;
+    static Big of(u128 x) {
+        Big b;
+        while (x) {
+            b.w.push_back((uint32_t)x);
+            x >>= 32;
+        }
+        return b;
+    }
+    void trim() {
+        while (!w.empty() && w.back() == 0) w.pop_back();
+    }
+    Big operator+(const Big& o) const {
+        Big r;
+        uint64_t c = 0;
+        for (size_t i = 0; i < std::max(w.size(), o.w.size()); ++i) {
+            c += (i < w.size() ? w[i] : 0u) + (uint64_t)(i < o.w.size() ? o.w[i] : 0u);
+            r.w.push_back((uint32_t)c);
+            c >>= 32;
+        }
+        if (c) r.w.push_back((uint32_t)c);
+        r.trim();
+        return r;
+    }
+    Big operator*(const Big& o) const {
+        Big r;
+        r.w.assign(w.size() + o.w.size() + 1, 0);
+        for (size_t i = 0; i < w.size(); ++i) {
+            uint64_t c = 0;
+            for (size_t j = 0; j < o.w.size(); ++j) {
+                c += (uint64_t)w[i] * o.w[j] + r.w[i + j];
+                r.w[i + j] = (uint32_t)c;
+                c >>= 32;
+            }
+            for (size_t k = i + o.w.size(); c; ++k) {
+                c += r.w[k];
+                r.w[k] = (uint32_t)c;
+                c >>= 32;
+            }
+        }
+        r.trim();
+        return r;
+    }
+    // floor(this / 2^bits)
+    Big shr(unsigned bits) const {
+        Big r;
+        const size_t ws = bits / 32, bs = bits % 32;
+        for (size_t i = ws; i < w.size(); ++i) {
+            uint64_t v = w[i] >> bs;
+            if (bs && i + 1 < w.size()) v |= (uint64_t)w[i + 1] << (32 - bs);
+            r.w.push_back((uint32_t)v);
+        }
+        r.trim();
+        return r;
+    }
+    int cmp(const Big& o) const {
+        if (w.size() != o.w.size()) return w.size() < o.w.size() ? -1 : 1;
+        for (size_t i = w.size(); i-- > 0;)
+            if (w[i] != o.w[i]) return w[i] < o.w[i] ? -1 : 1;
+        return 0;
+    }
+    // value if below 2^64, else UINT64_MAX
+    uint64_t u64() const {
+        if (w.size() > 2) return UINT64_MAX;
+        return (w.size() > 0 ? w[0] : 0) | (w.size() > 1 ? (uint64_t)w[1] << 32 : 0);
+    }
+    static Big pow2(unsigned bits) {
+        Big b;
+        b.w.assign(bits / 32 + 1, 0);
+        b.w[bits / 32] = 1u << (bits % 32);
+        return b;
+    }
+    Big minus_one() const {   // this - 1 for this > 0
+        Big r = *this;
+        for (size_t i = 0; i < r.w.size(); ++i)
+            if (r.w[i]-- != 0) break;
+        r.trim();
+        return r;
+    }
+};
+
+// Worst case of a residue held as LR limbs: each limb's maximum and the value's.
+struct Bnd {
+    uint64_t l[5] = {0, 0, 0, 0, 0};
+    Big v;
+};
+
+struct Ctx {
+    uint32_t LR;
+    u128 q;
+    uint64_t qr[5];   // q in 26-bit limbs
+    Big qb, rp;       // q, R' = 2^(26 LR)
+
+    Bnd canonical() const {   // a residue below q, normalised limbs
+        Bnd b;
+        b.v = qb.minus_one();
+        for (uint32_t i = 0; i + 1 < LR; ++i) b.l[i] = kM26;
+        b.l[LR - 1] = b.v.shr(26 * (LR - 1)).u64();
+        return b;
+    }
+    bool limbs_ok(const Bnd& b) const {
+        for (uint32_t i = 0; i < LR; ++i)
+            if (b.l[i] >= ((uint64_t)1 << 32)) return false;
+        return true;
+    }
+    Bnd add(const Bnd& a, const Bnd& b) const {
+        Bnd r;
+        for (uint32_t i = 0; i < LR; ++i) r.l[i] = a.l[i] + b.l[i];
+        r.v = a.v + b.v;
+        return r;
+    }
+    Bnd max(const Bnd& a, const Bnd& b) const {
+        Bnd r;
+        for (uint32_t i = 0; i < LR; ++i) r.l[i] = std::max(a.l[i], b.l[i]);
+        r.v = a.v.cmp(b.v) >= 0 ? a.v : b.v;
+        return r;
+    }
+    // Montgomery product with 64-bit columns (rr_arith.cuh, lazy reduction);
+    // false on any overflow.
+    bool mmul(const Bnd& x, const Bnd& y, Bnd* out) const {
+        if (!limbs_ok(x) || !limbs_ok(y)) return false;
+        const u128 lim = (u128)1 << 64;
+        u128 col[10] = {0};
+        for (uint32_t a = 0; a < LR; ++a)
+            for (uint32_t b = 0; b < LR; ++b) {
+                col[a + b] += (u128)x.l[a] * y.l[b];
+                if (col[a + b] >= lim) return false;
+            }
+        u128 carry = 0;
+        for (uint32_t i = 0; i < LR; ++i) {
+            const u128 acc = col[i] + carry + (u128)kM26 * qr[0];
+            if (acc >= lim) return false;
+            carry = acc >> 26;
+            for (uint32_t k = 1; k < LR; ++k) {
+                col[i + k] += (u128)kM26 * qr[k];
+                if (col[i + k] >= lim) return false;
+            }
+        }
+        for (uint32_t i = 0; i < LR; ++i) {
+            const u128 v = col[LR + i] + carry;
+            if (v >= lim) return false;
+            carry = v >> 26;
+        }
+        // value: (T + Q q) / R' with T <= x.v y.v and Q < R'
+        Bnd r;
+        r.v = (x.v * y.v + rp.minus_one() * qb).shr(26 * LR);
+        const Big top = r.v.shr(26 * (LR - 1));
+        if (top.cmp(Big::pow2(32)) >= 0) return false;
+        for (uint32_t i = 0; i + 1 < LR; ++i) r.l[i] = kM26;
+        r.l[LR - 1] = top.u64();
+        *out = r;
+        return true;
+    }
+    // Smallest K with limbs of K q, after moving units down from higher limbs,
+    // each at least need[i].
+    bool bias(const Bnd& need, uint32_t* limbs, Bnd* as_bnd) const {
+        for (uint64_t K = 1; K <= (1u << 16); ++K) {
+            const Big v = qb * Big::of(K);
+            int64_t n[5];
+            for (uint32_t i = 0; i < LR; ++i) {
+                const Big part = v.shr(26 * i);
+                const uint64_t lo = part.w.empty() ? 0 : part.w[0];
+                if (i + 1 < LR) {
+                    n[i] = (int64_t)(lo & kM26);
+                } else {
+                    if (part.cmp(Big::pow2(40)) >= 0) return false;
+                    n[i] = (int64_t)part.u64();
+                }
+            }
+            for (uint32_t i = 0; i + 1 < LR; ++i) {
+                if (n[i] < (int64_t)need.l[i]) {
+                    const int64_t c = ((int64_t)need.l[i] - n[i] + (int64_t)kM26) >> 26;
+                    n[i] += c << 26;
+                    n[i + 1] -= c;
+                }
+            }
+            bool ok = n[LR - 1] >= (int64_t)need.l[LR - 1];
+            for (uint32_t i = 0; i < LR; ++i) ok = ok && n[i] >= 0 && n[i] < ((int64_t)1 << 32);
+            if (!ok) continue;
+            Bnd b;
+            for (uint32_t i = 0; i < LR; ++i) {
+                limbs[i] = (uint32_t)n[i];
+                b.l[i] = (uint64_t)n[i];
+            }
+            b.v = v;
+            *as_bnd = b;
+            return true;
+        }
+        return false;
+    }
+    bool below_2q(const Bnd& b) const { return b.v.cmp((qb + qb).minus_one()) <= 0; }
+};
+
+}  // namespace
+
+bool ntt_lazy_bounds(uint32_t m, uint32_t LR, u128 q, NttBiases* out) {
+    if (LR < 2 || LR > 5 || m < 4 || m > 128 || (m & (m - 1)) != 0) return false;
+    uint32_t lg = 0;
+    while ((1u << lg) < m) ++lg;
+    if (lg > 7) return false;
+    Ctx c;
+    c.LR = LR;
+    c.q = q;
+    for (uint32_t i = 0; i < 5; ++i) c.qr[i] = i < LR ? (uint64_t)((q >> (26 * i)) & kM26) : 0;
+    c.qr[LR - 1] = (uint64_t)(q >> (26 * (LR - 1)));
+    c.qb = Big::of(q);
+    c.rp = Big::pow2(26 * LR);
+    *out = NttBiases{};
+    const Bnd C = c.canonical();
+
+    // input: canonical coefficients, or K q - y for the negated ones
+    Bnd BN;
+    if (!c.bias(C, out->neg, &BN)) return false;
+    Bnd X = c.max(C, BN);
+    // forward butterflies: t = hi z, lo + t, lo + BF - t.  BF must cover every
+    // t; take it first for t < 2q, then again for the largest t that bias gives.
+    auto forward = [&](const Bnd& BF, Bnd* Xout, Bnd* tmax) {
+        Bnd x = X, tm;
+        tm.v = Big();
+        for (uint32_t s = 0; s < lg; ++s) {
+            Bnd t;
+            if (!c.mmul(x, C, &t) || !c.below_2q(t)) return false;
+            for (uint32_t i = 0; i < LR; ++i)
+                if (BF.l[i] < t.l[i]) return false;
+            tm = s ? c.max(tm, t) : t;
+            x = c.add(x, BF);
+            if (!c.limbs_ok(x)) return false;
+        }
+        *Xout = x;
+        *tmax = tm;
+        return true;
+    };
+    Bnd t_need = C;
+    t_need.v = (c.qb + c.qb).minus_one();
+    t_need.l[LR - 1] = t_need.v.shr(26 * (LR - 1)).u64();
+    Bnd BF, Xf, tmax;
+    if (!c.bias(t_need, out->fwd, &BF) || !forward(BF, &Xf, &tmax)) return false;
+    {
+        uint32_t tight[5];
+        Bnd BF2, Xf2, tmax2;
+        if (c.bias(tmax, tight, &BF2) && forward(BF2, &Xf2, &tmax2)) {
+            for (uint32_t i = 0; i < 5; ++i) out->fwd[i] = tight[i];
+            Xf = Xf2;
+        }
+    }
+    X = Xf;
+    // componentwise: by a canonical twiddle, or a by b (b scaled first when a b would not fit)
+    Bnd P_tw, P_fin;
+    if (!c.mmul(X, C, &P_tw)) return false;
+    out->prescale = !(c.mmul(X, X, &P_fin) && c.below_2q(P_fin));
+    if (out->prescale && !c.mmul(X, P_tw, &P_fin)) return false;
+    Bnd U = c.max(P_tw, P_fin);
+    // backwards butterflies: lo + hi, (lo + BB_b - hi) z; the last stage multiplies both
+    for (uint32_t b = 0; b < lg; ++b) {
+        if (b + 1 == lg) {   // the last stage first carry-propagates its inputs to 26-bit limbs
+            if (!c.limbs_ok(U)) return false;
+            const Big top = U.v.shr(26 * (LR - 1));
+            if (top.cmp(Big::pow2(32)) >= 0) return false;
+            for (uint32_t i = 0; i + 1 < LR; ++i) U.l[i] = kM26;
+            U.l[LR - 1] = top.u64();
+        }
+        Bnd BB;
+        if (!c.bias(U, out->bwd[b], &BB)) return false;
+        const Bnd s = c.add(U, U), d = c.add(U, BB);
+        if (!c.limbs_ok(s) || !c.limbs_ok(d)) return false;
+        Bnd r1, r2;
+        if (!c.mmul(d, C, &r2)) return false;
+        if (b + 1 == lg) {
+            if (!c.mmul(s, C, &r1) || !c.below_2q(r1) || !c.below_2q(r2)) return false;
+        } else {
+            U = c.max(s, r2);
+        }
+    }
+    return true;
+}
+
+}  // namespace dkss_planning

@@ -1,0 +1,35 @@
+// Limits of the lazy arithmetic in the NTT form of the R-multiplication
+// (ntt_rmul.cuh), checked on the host for one ring before a plan uses it.
+//
+// The transform keeps residues mod p^z unreduced between Montgomery products:
+// sums are limbwise additions of 26-bit limb vectors (limbs may grow past 26
+// bits) and a difference x - y is x + B - y for a bias B = K p^z whose limbs
+// are each at least y's (so no limb goes negative).  ntt_lazy_bounds follows
+// the worst case of every limb and of the value through the forward
+// transform, the componentwise products and the backwards transform, and
+// accepts the ring only if
+//   * no 64-bit column of a product or of its Montgomery reduction overflows,
+//   * every limb stays below 2^32,
+//   * every reduction result fits its limbs, and
+//   * the backwards transform ends below 2 p^z (one subtraction makes it
+//     canonical).
+// It also picks the smallest K for every bias.
+#pragma once
+#include <cstdint>
+
+#include "host_math.hpp"
+
+namespace dkss_planning {
+
+struct NttBiases {
+    uint32_t fwd[5];      // forward butterflies: K p^z, limbs >= those of a reduced product
+    uint32_t neg[5];      // negated input coefficients: K p^z, limbs >= those of a canonical residue
+    uint32_t bwd[7][5];   // backwards stage b: K_b p^z, limbs >= those of any stage input
+    bool prescale;        // componentwise products scale one factor first (keeps the product in range)
+};
+
+// true when the lazy transform of R = (Z/qZ)[alpha]/(alpha^m + 1) with LR
+// limbs of 26 bits stays within every limit above; fills *out.
+bool ntt_lazy_bounds(uint32_t m, uint32_t LR, dkss_host::u128 q, NttBiases* out);
+
+}  // namespace dkss_planning

@@ -16,9 +16,15 @@
 // which leave evaluations in bit-reversed order; backwards stages use
 // Gentleman-Sande butterflies with psi^-brv(k) and return natural order.
 // Between stages lanes l and l ^ 2^b swap one value with a shuffle.
-// Residues are 26-bit limbs (rr_arith.cuh); sums stay below 2^lg(m) p^z and
-// the plan picks LR with 4 m p^z < 2^(26 LR), so every Montgomery product
-// input is in range.
+//
+// Arithmetic is lazy: residues are vectors of LR limbs of nominally 26 bits,
+// a sum is a limbwise addition (limbs may grow past 26 bits), a difference
+// x - y is x + B - y with a bias B = K p^z whose limbs are each at least
+// y's, and a Montgomery product (R' = 2^(26 LR)) leaves normalised limbs of a
+// value below 2 p^z without a final subtraction.  The plan's host check
+// (ntt_bounds.cpp) follows the worst case of every limb through both
+// transforms and picks the biases; only the results written back are made
+// canonical.
 #pragma once
 #include <cstdint>
 
@@ -32,13 +38,17 @@ struct NttLayout {
     static constexpr int LG = (m >= 64) ? 6 : (m >= 32) ? 5 : (m >= 16) ? 4 : (m >= 8) ? 3 : 2;
     static constexpr int ZF = 0;            // psi^brv(k) R', k in [1, m)
     static constexpr int ZI = m;            // psi^-brv(k) R'
-    static constexpr int BIAS = 2 * m;      // 2^b p^z, b < LG (normalised)
-    static constexpr int Q = BIAS + LG;     // p^z
+    static constexpr int BB = 2 * m;        // backwards stage biases, LG of them
+    static constexpr int BF = BB + LG;      // forward butterfly bias
+    static constexpr int BN = BF + 1;       // bias of negated input coefficients
+    static constexpr int Q = BN + 1;        // p^z (normalised)
     static constexpr int TW_LO = Q + 1;     // m^-1 R'            (last backwards stage, twiddles)
     static constexpr int TW_HI = Q + 2;     // psi^-1 m^-1 R'
     static constexpr int PW_LO = Q + 3;     // m^-1 (2M)^-1 R'^2  (componentwise products of
     static constexpr int PW_HI = Q + 4;     // psi^-1 m^-1 (2M)^-1 R'^2   two normal-form factors)
-    static constexpr int COUNT = Q + 5;
+    static constexpr int ONE = Q + 5;       // R'                 (last backwards stage after a
+    static constexpr int ZLAST = Q + 6;     // psi^-1 R'           prescaled componentwise product)
+    static constexpr int COUNT = Q + 7;
 };
 
 template <int LR>
@@ -47,35 +57,72 @@ __device__ __forceinline__ void ldg_rr(uint32_t (&x)[LR], const uint32_t* p) {
     for (int i = 0; i < LR; ++i) x[i] = __ldg(p + i);
 }
 
-// r = a + b, limbs normalised to 26 bits (the value must fit in LR limbs)
+// r = a + b, limbwise
 template <int LR>
-__device__ __forceinline__ void add_norm(uint32_t (&r)[LR], const uint32_t (&a)[LR], const uint32_t (&b)[LR]) {
-    uint32_t carry = 0;
+__device__ __forceinline__ void lz_add(uint32_t (&r)[LR], const uint32_t (&a)[LR], const uint32_t (&b)[LR]) {
 #pragma unroll
-    for (int i = 0; i < LR; ++i) {
-        const uint32_t s = a[i] + b[i] + carry;
-        r[i] = i + 1 < LR ? (s & kM26) : s;
-        carry = s >> 26;
-    }
+    for (int i = 0; i < LR; ++i) r[i] = a[i] + b[i];
 }
 
-// r = c - v for normalised c >= v
+// r = a + B - b, limbwise (B[i] >= b[i] for every i)
 template <int LR>
-__device__ __forceinline__ void sub_norm(uint32_t (&r)[LR], const uint32_t (&c)[LR], const uint32_t (&v)[LR]) {
-    uint32_t borrow = 0;
+__device__ __forceinline__ void lz_sub(uint32_t (&r)[LR], const uint32_t (&a)[LR], const uint32_t (&B)[LR],
+                                       const uint32_t (&b)[LR]) {
 #pragma unroll
-    for (int i = 0; i < LR; ++i) {
-        const uint32_t d = c[i] - v[i] - borrow;
-        borrow = d >> 31;
-        r[i] = d & kM26;
-    }
+    for (int i = 0; i < LR; ++i) r[i] = a[i] + B[i] - b[i];
 }
 
-// canonical product a * b * 2^(-26 LR) mod q (a b < q 2^(26 LR))
+// Montgomery product a b 2^(-26 LR) mod q as normalised limbs of a value
+// below a b / R' + q (the top limb holds every bit above 26 (LR - 1)).
 template <int LR>
 __device__ __forceinline__ void mmul(uint32_t (&r)[LR], const uint32_t (&a)[LR], const uint32_t (&b)[LR],
                                      const ModRR<LR>& md) {
-    mont_mul_rr<LR>(r, a, b, md);
+    uint64_t col[2 * LR];
+#pragma unroll
+    for (int i = 0; i < 2 * LR; ++i) col[i] = 0;
+    mac_cols<LR>(col, a, b);
+#pragma unroll
+    for (int i = 0; i < LR; ++i) {
+        const uint32_t qi = ((uint32_t)col[i] * md.nprime) & kM26;
+        const uint64_t c = col[i] + (uint64_t)qi * md.q[0];   // low 26 bits become 0
+        col[i + 1] += c >> 26;
+#pragma unroll
+        for (int k = 1; k < LR; ++k) col[i + k] += (uint64_t)qi * md.q[k];
+    }
+    uint64_t carry = 0;
+#pragma unroll
+    for (int i = 0; i < LR; ++i) {
+        const uint64_t v = col[LR + i] + carry;
+        r[i] = i + 1 < LR ? ((uint32_t)v & kM26) : (uint32_t)v;
+        carry = v >> 26;
+    }
+}
+
+// canonical residue of normalised limbs of a value below 2q
+template <int LR>
+__device__ __forceinline__ void canon(uint32_t (&r)[LR], const uint32_t (&x)[LR], const ModRR<LR>& md) {
+    uint32_t d[LR], borrow = 0;
+#pragma unroll
+    for (int i = 0; i < LR; ++i) {
+        const uint32_t v = x[i] - md.q[i] - borrow;
+        borrow = v >> 31;
+        d[i] = i + 1 < LR ? (v & kM26) : v;
+    }
+#pragma unroll
+    for (int i = 0; i < LR; ++i) r[i] = borrow ? x[i] : d[i];
+}
+
+// carry-propagate limbs (each below 2^32) to 26 bits; the top limb keeps the rest
+template <int LR>
+__device__ __forceinline__ void lz_norm(uint32_t (&x)[LR]) {
+    uint32_t carry = 0;
+#pragma unroll
+    for (int i = 0; i + 1 < LR; ++i) {
+        const uint32_t v = x[i] + carry;
+        carry = (v >> 26) + (v < carry ? 64u : 0u);
+        x[i] = v & kM26;
+    }
+    x[LR - 1] += carry;
 }
 
 template <int m, int LR>
@@ -91,30 +138,29 @@ __device__ __forceinline__ void team_swap(uint32_t (&lo)[LR], uint32_t (&hi)[LR]
 }
 
 // Forward negacyclic transform: on entry lane l holds coefficients l, l+m/2;
-// on exit the evaluations with bit-reversed indices 2l, 2l+1.
+// on exit the evaluations with bit-reversed indices 2l, 2l+1 (lazy).
 template <int m, int LR>
 __device__ __forceinline__ void ntt_forward(uint32_t (&lo)[LR], uint32_t (&hi)[LR], int lane, unsigned mask,
                                             const uint32_t* cst, const ModRR<LR>& md) {
     using NL = NttLayout<m>;
-    uint32_t q[LR];
-    ldg_rr<LR>(q, cst + NL::Q * LR);
+    uint32_t bf[LR];
+    ldg_rr<LR>(bf, cst + NL::BF * LR);
 #pragma unroll
     for (int b = NL::LG - 1; b >= 0; --b) {
         if (b < NL::LG - 1) team_swap<m, LR>(lo, hi, lane, b, mask);
         const int k = (1 << (NL::LG - 1 - b)) + (lane >> b);
-        uint32_t z[LR], t[LR], d[LR];
+        uint32_t z[LR], t[LR];
         ldg_rr<LR>(z, cst + (NL::ZF + k) * LR);
-        mmul<LR>(t, hi, z, md);           // canonical, < q
-        sub_norm<LR>(d, q, t);            // q - t
-        add_norm<LR>(hi, lo, d);          // lo - t + q
-        add_norm<LR>(lo, lo, t);          // lo + t
+        mmul<LR>(t, hi, z, md);
+        lz_sub<LR>(hi, lo, bf, t);        // lo - t
+        lz_add<LR>(lo, lo, t);            // lo + t
     }
 }
 
 // Backwards transform scaled by a constant: on entry lane l holds the
-// evaluations 2l, 2l+1 (bit-reversed order); on exit the canonical
-// coefficients l, l+m/2 of the interpolated element times c, where the last
-// stage multiplies by cst[lo_c] and cst[hi_c] (= c and psi^-1 c, times R').
+// evaluations 2l, 2l+1 (bit-reversed order); on exit the coefficients l,
+// l+m/2 of the interpolated element times c (normalised, below 2q), where the
+// last stage multiplies by cst[lo_c] and cst[hi_c] (= c and psi^-1 c, times R').
 template <int m, int LR>
 __device__ __forceinline__ void ntt_backward(uint32_t (&lo)[LR], uint32_t (&hi)[LR], int lane, unsigned mask,
                                              const uint32_t* cst, int lo_c, int hi_c, const ModRR<LR>& md) {
@@ -122,11 +168,14 @@ __device__ __forceinline__ void ntt_backward(uint32_t (&lo)[LR], uint32_t (&hi)[
 #pragma unroll
     for (int b = 0; b < NL::LG; ++b) {
         if (b > 0) team_swap<m, LR>(lo, hi, lane, b - 1, mask);
-        uint32_t bias[LR], s[LR], dd[LR], d[LR], z[LR];
-        ldg_rr<LR>(bias, cst + (NL::BIAS + b) * LR);   // 2^b q >= hi
-        add_norm<LR>(s, lo, hi);                        // u + v
-        sub_norm<LR>(dd, bias, hi);
-        add_norm<LR>(d, lo, dd);                        // u - v + 2^b q
+        uint32_t bias[LR], s[LR], d[LR], z[LR];
+        if (b == NL::LG - 1) {          // sums of m/2 values: bring the limbs back to 26 bits
+            lz_norm<LR>(lo);
+            lz_norm<LR>(hi);
+        }
+        ldg_rr<LR>(bias, cst + (NL::BB + b) * LR);
+        lz_add<LR>(s, lo, hi);                  // u + v
+        lz_sub<LR>(d, lo, bias, hi);            // u - v
         if (b == NL::LG - 1) {
             uint32_t c[LR];
             ldg_rr<LR>(c, cst + lo_c * LR);

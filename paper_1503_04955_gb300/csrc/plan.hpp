@@ -7,6 +7,7 @@
 
 #include "../../include/dkss.h"
 #include "host_math.hpp"
+#include "ntt_bounds.hpp"
 #include "status_bits.hpp"
 
 struct dkss_plan_s {
@@ -26,6 +27,8 @@ struct dkss_plan_s {
     uint32_t nprime26 = 0;        // -(p^z)^-1 mod 2^26
     uint32_t kscale[5] = {0, 0, 0, 0, 0};  // (2M)^-1 R'^2 mod p^z, 26-bit limbs
     dkss_host::Roots roots;
+    bool ntt_ok = false;                  // the lazy NTT form's limits hold for this ring
+    dkss_planning::NttBiases ntt_bias{};  // its bias constants
     // device memory owned by the plan
     int device = 0;
     uint32_t* d_table = nullptr;  // rho^s (s < mu_top): coefficients, or evaluations (default)

@@ -25,6 +25,7 @@ SMALL = [
     (786432, 2048, 32, 24, 65537, 5),       # m=32, L=3, last level 2m
     (1 << 22, 1 << 12, 64, 32, 7340033, 4),  # m=64, L=3 (three REDC subtractions), last level 2m
     (1 << 21, 1 << 14, 64, 16, 998244353, 4),  # m=64, L=4, two radix-2m levels, last level 2
+    (4096, 32, 16, 16, 40961, 3),           # m=16, L=2, LR=2: NTT form prescales the componentwise products
 ]
 
 
@@ -48,6 +49,8 @@ def check_product(dk, oc, cfg, A, B, with_oracle=True, with_forward=True, flags=
     par = o.Params(*cfg).check()
     roots = o.compute_roots(par)
     with dk.Plan(*cfg, flags=flags) as plan:
+        # the default runs the evaluation-map form on every ring tested here
+        assert plan.info()["rmul"] == (2 if flags & 2 else 1 if flags & 16 else 0)
         c = plan.mul(to_dev(A), to_dev(B))
         fwd = plan.forward(to_dev(A)) if with_forward else None
         plan.sync_status()
@@ -75,7 +78,7 @@ def test_small_configs_random(dk, oc, cfg, flags):
 
 @pytest.mark.parametrize("flags", FORMS)
 @pytest.mark.parametrize("kind", ["zero", "one", "ones", "top"])
-@pytest.mark.parametrize("cfg", [SMALL[0], SMALL[4], SMALL[6]])
+@pytest.mark.parametrize("cfg", [SMALL[0], SMALL[4], SMALL[6], SMALL[7]])
 def test_small_configs_special_operands(dk, oc, cfg, kind, flags):
     A = syn.special_operand(cfg[0], kind)
     B = syn.special_operand(cfg[0], "ones")

@@ -100,3 +100,17 @@ def test_int8_form_needs_m_32(dk):
     h = ctypes.c_void_p()
     rc = dk.load().dkss_plan(ctypes.byref(h), 1 << 16, 512, 16, 16, 12289, 4, 2)
     assert rc == 4 and not h.value
+
+
+def test_rings_take_the_evaluation_map_form(dk):
+    """Every workload ring and every tested small ring stays within the lazy
+    transform's limits (else the plan falls back to the direct convolution);
+    the m = 16, p^z = 40961^3 ring is one that prescales its componentwise
+    products."""
+    for cfg in [syn.workload_params(k) for k in syn.WORKLOADS] + GPU_SMALL:
+        _, consts = dk.plan_rho(*cfg)
+        assert consts["rmul"] == 0, cfg
+    _, consts = dk.plan_rho(4096, 32, 16, 16, 40961, 3)
+    assert consts["rmul"] == 0 and consts["prescale"] == 1
+    _, consts = dk.plan_rho(*syn.workload_params("dkss_2p24b"))
+    assert consts["prescale"] == 0

@@ -32,7 +32,12 @@ def product_polynomial_words(A, B, par, L):
     return np.ascontiguousarray(words[:, :L]).reshape(-1)
 
 
-@pytest.mark.parametrize("cfg", [syn.workload_params("dkss_65536b"), (26600, 128, 32, 13, 257, 5)])
+# u = 16 (L = 2), u = 13 (generic windows), u = 32 (L = 3 and L = 4)
+NO_ALLOC_CFGS = [syn.workload_params("dkss_65536b"), (26600, 128, 32, 13, 257, 5), (65536, 256, 16, 32, 12289, 6),
+                 (1 << 20, 2048, 32, 32, 65537, 6)]
+
+
+@pytest.mark.parametrize("cfg", NO_ALLOC_CFGS)
 def test_decode_static_matches_dkss_mul_twice(cfg):
     import torch
     import oracle_c
@@ -61,3 +66,25 @@ def test_decode_static_rejects_oversize():
     n_bits = 1 << 34                                     # beyond DKSS_DECODE_STATIC_MAX_TILES
     rc = lib.dkss_decode_static(c.data_ptr(), n_bits, 1 << 29, 64, 32, 4, out.data_ptr(), None)
     assert rc == 4                                       # DKSS_EUNSUPPORTED, nothing launched
+
+
+@pytest.mark.parametrize("cfg", [NO_ALLOC_CFGS[0], NO_ALLOC_CFGS[3]])
+def test_decode_static_unaligned_input(cfg):
+    """A product polynomial that starts one word past an aligned address is
+    read with word loads instead of vector loads; the result is the same."""
+    import torch
+    import oracle_c
+    import paper_1503_04955_gb300 as dk
+    dk.buildlib.build()
+    oracle_c.build()
+    par = o.Params(*cfg).check()
+    with dk.Plan(*cfg) as plan:
+        L = plan.info()["L"]
+        A, B = syn.operand_pair(par.n_bits, 4343)
+        want = to_host(plan.mul(to_dev(A), to_dev(B)))
+        words = product_polynomial_words(A, B, par, L).view(np.int32)
+        buf = torch.zeros(words.size + 1, dtype=torch.int32, device="cuda")
+        buf[1:] = torch.from_numpy(words).cuda()
+        got = dk.binding.decode_static(buf[1:], par.n_bits, par.M, par.m, par.u, L)
+        torch.cuda.synchronize()
+        assert np.array_equal(to_host(got), want)
