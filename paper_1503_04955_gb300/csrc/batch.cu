@@ -292,7 +292,6 @@ dkss_status dkss_batch_plan(dkss_batch_t* out, const uint64_t* n_bits, size_t co
     }
     b->h_jobs.resize(count);
     uint32_t max_levels = 0;
-    uint64_t max_rlast = 0;
     for (size_t j = 0; j < count; ++j) {
         const ClassTables& t = *b->tables[b->job_class[j]];
         const dkss_plan_s& h = t.host;
@@ -330,7 +329,6 @@ dkss_status dkss_batch_plan(dkss_batch_t* out, const uint64_t* n_bits, size_t co
         jb.col_levels = h.col_levels;
         jb.r_last = (uint32_t)h.r_last;
         max_levels = std::max(max_levels, h.col_levels);
-        max_rlast = std::max<uint64_t>(max_rlast, h.r_last);
     }
 
     // stage list and per-stage job offsets
@@ -362,7 +360,8 @@ dkss_status dkss_batch_plan(dkss_batch_t* out, const uint64_t* n_bits, size_t co
         for (size_t j = 0; j < count; ++j) {
             offs[k * (count + 1) + j] = acc;
             const dkss_plan_s& h = b->tables[b->job_class[j]]->host;
-            acc += dkss::batch_items<kBm>(st[k].first, st[k].second, h.P2, h.col_levels, h.r_last, tiles[j], G::NTEAMS);
+            acc += dkss::batch_items<kBm>(st[k].first, st[k].second, h.P2, h.col_levels, h.r_last, tiles[j],
+                                          dkss::NttTeam<kBm>::NTEAMS);
         }
         offs[k * (count + 1) + count] = acc;
         stages[k].type = st[k].first;
@@ -380,7 +379,13 @@ dkss_status dkss_batch_plan(dkss_batch_t* out, const uint64_t* n_bits, size_t co
     }
 
     // persistent grid: as many CTAs as can be resident
-    b->smem = std::max({sizeof(uint32_t) * (size_t)G::TWO_M * G::EW, sizeof(uint32_t) * 2 * max_rlast * G::EW,
+    // column DFTs; the fused last level with the NTT exchange buffers after its
+    // two blocks; twiddle exchange buffers; decode tiles
+    const size_t xbuf = sizeof(uint32_t) * (size_t)dkss::NttTeam<kBm>::NTEAMS * kBm * kBLR;
+    size_t fin = 0;
+    for (const auto& t : b->tables)
+        fin = std::max(fin, dkss::final_smem_bytes<kBm, kBL, kBLR>((int)t->host.r_last, dkss::kFormNtt));
+    b->smem = std::max({sizeof(uint32_t) * (size_t)G::TWO_M * G::EW, fin, xbuf,
                         sizeof(uint32_t) * (size_t)dkss::kDecSmemWords});
     int per_sm = 0, sms = 0, optin = 0;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device) != cudaSuccess ||

@@ -54,12 +54,12 @@ __host__ __device__ inline uint64_t batch_items(uint32_t type, uint32_t level, u
     uint64_t len = P2;
     for (uint32_t i = 0; i < level; ++i) len /= 2 * m;
     const uint64_t mu_d = len / (2 * m);
-    const uint64_t tw = (uint64_t)(2 * m - 1) * (mu_d > 0 ? mu_d - 1 : 0) * (len ? P2 / len : 0);
-    const uint64_t groups = (tw + nteams - 1) / nteams;
+    // NTT-form twiddle stages: one team per element of the level
+    const uint64_t groups = mu_d > 1 ? (P2 + nteams - 1) / nteams : 0;
     switch (type) {
         case kStFwdDft: return level < col_levels ? 2 * cols : 0;
         case kStFwdTwiddle: return level < col_levels ? 2 * groups : 0;
-        case kStFinal: return P2 / r_last;
+        case kStFinal: return P2 / (r_last * final_blocks_per_cta<m>((int)r_last));
         case kStInvTwiddle: return level < col_levels ? groups : 0;
         case kStInvDft: return level < col_levels ? cols : 0;
         case kStDecTiles: return n_tiles;
@@ -100,13 +100,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(const BatchJob* __restric
                     break;
                 case kStFwdTwiddle:
                 case kStInvTwiddle: {
-                    const uint64_t mu_d = lp.len / G::TWO_M;
-                    const uint64_t tw = (uint64_t)(G::TWO_M - 1) * (mu_d - 1) * (lp.P2 / lp.len);
-                    const uint64_t groups = (tw + G::NTEAMS - 1) / G::NTEAMS;
+                    const uint64_t groups = (lp.P2 + NttTeam<m>::NTEAMS - 1) / NttTeam<m>::NTEAMS;
                     if (st.type == kStFwdTwiddle)
-                        twiddle_ntt_group<m, L, LR, false>(lp, mr, local % groups, (int)(local / groups));
+                        twiddle_ntt_group<m, L, LR, false>(lp, mr, local % groups, (int)(local / groups), smem);
                     else
-                        twiddle_ntt_group<m, L, LR, true>(lp, mr, local, 0);
+                        twiddle_ntt_group<m, L, LR, true>(lp, mr, local, 0, smem);
                     break;
                 }
                 case kStFinal:

@@ -122,6 +122,30 @@ struct Team {
     }
 };
 
+// Team of the NTT-form R-multiplication (ntt_rmul.cuh): m/4 lanes per element.
+template <int m>
+struct NttTeam {
+    static constexpr int TEAM = m / 4;
+    static constexpr int TEAMS_PER_WARP = 32 / TEAM;
+    static constexpr int NTEAMS = kWarps * TEAMS_PER_WARP;
+    static constexpr int BUF_WORDS_PER_LR = m;   // exchange buffer: m residues
+    int id, lane;
+    unsigned mask;
+    __device__ __forceinline__ NttTeam() {
+        const int warp = threadIdx.x >> 5, l = threadIdx.x & 31;
+        id = warp * TEAMS_PER_WARP + l / TEAM;
+        lane = l % TEAM;
+        mask = TEAM == 32 ? 0xffffffffu : (((1u << TEAM) - 1u) << (l / TEAM * TEAM));
+    }
+};
+
+// Blocks of the last level (n elements each) per CTA of the NTT-form fused
+// kernel: enough that every team of the CTA owns an element.
+template <int m>
+__host__ __device__ constexpr int final_blocks_per_cta(int n) {
+    return n >= NttTeam<m>::NTEAMS ? 1 : NttTeam<m>::NTEAMS / n;
+}
+
 // Coefficient t of alpha^sh * y (sh in [0, 2m)): +-y[src] (negacyclic shift).
 template <int m, int L>
 __device__ __forceinline__ void shifted(uint32_t (&out)[L], bool& neg, const uint32_t* y, int t, int sh) {
@@ -139,46 +163,48 @@ __device__ __forceinline__ void shifted(uint32_t (&out)[L], bool& neg, const uin
 }
 
 // In-place radix-2 DIT over n elements held in shared memory in bit-reversed
-// slots (one array, or two arrays transformed together); leaves
-// X_v = sum_j x_j (alpha^root)^(j v) in slot v.  root is a shift amount in
-// [0, 2m).  Butterflies are spread over teams; a team owns whole butterflies,
-// so one __syncwarp separates its reads from its writes.
+// slots, for `arrays` consecutive arrays of n elements transformed together;
+// leaves X_v = sum_j x_j (alpha^root)^(j v) in slot v.  root is a shift
+// amount in [0, 2m).  Butterflies are spread over teams; a team owns whole
+// butterflies, so one __syncwarp separates its reads from its writes.
 template <int m, int L>
-__device__ void dft_dit(uint32_t* s0, uint32_t* s1, int arrays, int n, int root, const Mod<L>& md) {
+__device__ void dft_dit(uint32_t* base, int arrays, int n, int root, const Mod<L>& md) {
     using G = Geo<m, L>;
     Team<m, L> tm;
-    for (int half = 1; half < n; half <<= 1) {
-        const int scale = n / (2 * half);
+    const int log2n = 31 - __clz(n);
+    for (int lh = 0; lh < log2n; ++lh) {          // half = 2^lh (powers of two: shifts, no division)
+        const int half = 1 << lh;
+        const int scale = n >> (lh + 1);
         for (int bfa = tm.id; bfa < arrays * (n / 2); bfa += G::NTEAMS) {
-            uint32_t* s = bfa < n / 2 ? s0 : s1;
-            int bf = bfa < n / 2 ? bfa : bfa - n / 2;
-            int k_in = bf % half;
-            int ia = (bf / half) * 2 * half + k_in;
+            uint32_t* s = base + (bfa >> (log2n - 1)) * n * G::EW;
+            int bf = bfa & (n / 2 - 1);
+            int k_in = bf & (half - 1);
+            int ia = ((bf >> lh) << (lh + 1)) + k_in;
             int ib = ia + half;
-            int sh = (root * scale * k_in) % G::TWO_M;
+            int sh = (root * scale * k_in) & (G::TWO_M - 1);
+            uint32_t* pa = s + ia * G::EW;
+            uint32_t* pb = s + ib * G::EW;
             uint32_t a[G::CPL][L], y[G::CPL][L];
             bool ng[G::CPL];
 #pragma unroll
             for (int c = 0; c < G::CPL; ++c) {
                 int t = tm.lane + c * G::TEAM;
-                ld_res<L>(a[c], s + ia * G::EW + t * L);
-                shifted<m, L>(y[c], ng[c], s + ib * G::EW, t, sh);
+                ld_res<L>(a[c], pa + t * L);
+                shifted<m, L>(y[c], ng[c], pb, t, sh);
             }
             __syncwarp(tm.mask);
 #pragma unroll
             for (int c = 0; c < G::CPL; ++c) {
                 int t = tm.lane + c * G::TEAM;
-                // a + y and a - y, swapped where the shifted coefficient carries a minus sign
-                uint32_t pl[L], mi[L], sa[L], sb[L];
+                // a + y and a - y; where the shifted coefficient carries a minus
+                // sign the two results trade places (the store addresses swap)
+                uint32_t pl[L], mi[L];
                 add_mod<L>(pl, a[c], y[c], md);
                 sub_mod<L>(mi, a[c], y[c], md);
-#pragma unroll
-                for (int w = 0; w < L; ++w) {
-                    sa[w] = ng[c] ? mi[w] : pl[w];
-                    sb[w] = ng[c] ? pl[w] : mi[w];
-                }
-                st_res<L>(s + ia * G::EW + t * L, sa);
-                st_res<L>(s + ib * G::EW + t * L, sb);
+                uint32_t* d0 = (ng[c] ? pb : pa) + t * L;
+                uint32_t* d1 = (ng[c] ? pa : pb) + t * L;
+                st_res<L>(d0, pl);
+                st_res<L>(d1, mi);
             }
             __syncwarp(tm.mask);
         }
@@ -186,19 +212,24 @@ __device__ void dft_dit(uint32_t* s0, uint32_t* s1, int arrays, int n, int root,
     }
 }
 
-// In-place radix-2 DIF over n elements in natural slots; leaves
-// X_v = sum_j x_j (alpha^root)^(j v) in slot bitrev(v).
+// In-place radix-2 DIF over n elements in natural slots, for `arrays`
+// consecutive arrays of n elements; leaves X_v = sum_j x_j (alpha^root)^(j v)
+// in slot bitrev(v).
 template <int m, int L>
-__device__ void dft_dif(uint32_t* s, int n, int root, const Mod<L>& md) {
+__device__ void dft_dif(uint32_t* base, int arrays, int n, int root, const Mod<L>& md) {
     using G = Geo<m, L>;
     Team<m, L> tm;
-    for (int half = n / 2; half >= 1; half >>= 1) {
-        const int scale = n / (2 * half);
-        for (int bf = tm.id; bf < n / 2; bf += G::NTEAMS) {
-            int k_in = bf % half;
-            int ia = (bf / half) * 2 * half + k_in;
+    const int log2n = 31 - __clz(n);
+    for (int lh = log2n - 1; lh >= 0; --lh) {     // half = 2^lh
+        const int half = 1 << lh;
+        const int scale = n >> (lh + 1);
+        for (int bfa = tm.id; bfa < arrays * (n / 2); bfa += G::NTEAMS) {
+            uint32_t* s = base + (bfa >> (log2n - 1)) * n * G::EW;
+            const int bf = bfa & (n / 2 - 1);
+            int k_in = bf & (half - 1);
+            int ia = ((bf >> lh) << (lh + 1)) + k_in;
             int ib = ia + half;
-            int sh = (root * scale * k_in) % G::TWO_M;
+            int sh = (root * scale * k_in) & (G::TWO_M - 1);
             uint32_t sa[G::CPL][L], db[G::CPL][L];
 #pragma unroll
             for (int c = 0; c < G::CPL; ++c) {
@@ -218,15 +249,12 @@ __device__ void dft_dif(uint32_t* s, int n, int root, const Mod<L>& md) {
                         neg = false;
                     }
                 }
-                ld_res<L>(a, s + ia * G::EW + src * L);
-                ld_res<L>(b, s + ib * G::EW + src * L);
-                uint32_t x[L], y[L];
-#pragma unroll
-                for (int w = 0; w < L; ++w) {
-                    x[w] = neg ? b[w] : a[w];
-                    y[w] = neg ? a[w] : b[w];
-                }
-                sub_mod<L>(db[c], x, y, md);
+                // b - a instead of a - b where the coefficient carries a minus sign
+                const uint32_t* pa = s + (neg ? ib : ia) * G::EW + src * L;
+                const uint32_t* pb = s + (neg ? ia : ib) * G::EW + src * L;
+                ld_res<L>(a, pa);
+                ld_res<L>(b, pb);
+                sub_mod<L>(db[c], a, b, md);
             }
             __syncwarp(tm.mask);
 #pragma unroll
@@ -392,7 +420,7 @@ __device__ __forceinline__ void dft_fwd_column(const LevelParams& prm, const Mod
         }
     }
     __syncthreads();
-    dft_dit<m, L>(col, col, 1, G::TWO_M, 1, md);
+    dft_dit<m, L>(col, 1, G::TWO_M, 1, md);
     for (int idx = threadIdx.x; idx < G::TWO_M * m; idx += kThreads) {
         int v = idx / m, t = idx % m;
         uint32_t x[L];
@@ -470,52 +498,62 @@ __device__ __forceinline__ void load_shifted_rr(uint32_t (&out)[LR], const uint3
 
 // ---------------------------------------------------------------------------
 // Bad multiplications of level d through the evaluation map of R
-// (ntt_rmul.cuh): same element set and grid as k_twiddle, no shared memory.
+// (ntt_rmul.cuh): same element set as k_twiddle, one team of m/4 lanes per
+// element, xbuf = the CTA's exchange buffers (NttTeam<m>::NTEAMS of m
+// residues of LR words).
 // ---------------------------------------------------------------------------
 template <int m, int L, int LR, bool INV>
-__device__ __forceinline__ void twiddle_ntt_group(const LevelParams& prm, const ModRR<LR>& mr, uint64_t group, int op) {
+__device__ __forceinline__ void twiddle_ntt_group(const LevelParams& prm, const ModRR<LR>& mr, uint64_t group, int op,
+                                                  uint32_t* xbuf) {
     using G = Geo<m, L>;
-    Team<m, L> tm;
+    using NT = NttTeam<m>;
+    NT tm;
     uint32_t* poly = prm.data + (op ? prm.poly_words : 0);
-    const uint64_t mu_d = prm.len / G::TWO_M;
-    const uint64_t per_blk = (uint64_t)(G::TWO_M - 1) * (mu_d - 1);
-    const uint64_t total = per_blk * (prm.P2 / prm.len);
-    const uint64_t idx = group * G::NTEAMS + tm.id;
-    if (idx >= total) return;
-    const uint64_t blk = idx / per_blk, rem = idx % per_blk;
-    const uint64_t v = 1 + rem / (mu_d - 1), l = 1 + rem % (mu_d - 1);
+    // element (blk, v, l) of the level, all P2 of them (len, mu_d powers of two:
+    // shifts, no division); the twiddle of v = 0 or l = 0 is 1
+    const int lg_len = __ffsll((long long)prm.len) - 1;
+    const int lg_mu = lg_len - ilog2<G::TWO_M>();
+    const uint64_t idx = group * NT::NTEAMS + tm.id;
+    if (idx >= prm.P2) return;
+    const uint64_t blk = idx >> lg_len, rem = idx & (prm.len - 1);
+    const uint64_t v = rem >> lg_mu, l = rem & ((1ull << lg_mu) - 1);
+    if (v == 0 || l == 0) return;
+    const uint64_t mu_d = 1ull << lg_mu;
     uint64_t e = v * l * prm.bp;                          // in (0, 2M)
     if (INV) e = prm.P2 - e;
     const int r = (int)(e >> prm.log2_mu_top);
     const uint64_t sidx = e & (prm.mu_top - 1);
     uint32_t* x = poly + (blk * prm.len + v * mu_d + l) * G::EW;
+    uint32_t* buf = xbuf + tm.id * m * LR;
     const int lane = tm.lane;
-    uint32_t lo[LR], hi[LR];
     uint32_t bn[LR];
     ldg_rr<LR>(bn, prm.ntt_cst + NttLayout<m>::BN * LR);
-    load_shifted_rr<m, L, LR>(lo, x, lane, r, bn);
-    load_shifted_rr<m, L, LR>(hi, x, lane + m / 2, r, bn);
-    ntt_forward<m, LR>(lo, hi, lane, tm.mask, prm.ntt_cst, mr);
-    uint32_t t0[LR], t1[LR];
-    const uint32_t* tw = prm.table_eval + (sidx * m + 2 * lane) * LR;
-    ldg_rr<LR>(t0, tw);
-    ldg_rr<LR>(t1, tw + LR);
-    mmul<LR>(lo, lo, t0, mr);
-    mmul<LR>(hi, hi, t1, mr);
-    ntt_backward<m, LR>(lo, hi, lane, tm.mask, prm.ntt_cst, NttLayout<m>::TW_LO, NttLayout<m>::TW_HI, mr);
-    canon<LR>(lo, lo, mr);
-    canon<LR>(hi, hi, mr);
+    uint32_t vv[4][LR];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) load_shifted_rr<m, L, LR>(vv[j], x, lane + j * NT::TEAM, r, bn);
+    ntt_forward<m, LR>(vv, buf, lane, tm.mask, prm.ntt_cst, mr);
+    const uint32_t* tw = prm.table_eval + (sidx * m + 4 * lane) * LR;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        uint32_t t[LR];
+        ldg_rr<LR>(t, tw + j * LR);
+        mmul<LR>(vv[j], vv[j], t, mr);
+    }
+    ntt_backward<m, LR>(vv, buf, lane, tm.mask, prm.ntt_cst, NttLayout<m>::TW_LO, NttLayout<m>::TW_HI, mr);
     __syncwarp(tm.mask);   // every lane has read its shifted inputs before any write
-    uint32_t o[L];
-    from_rr<L, LR>(o, lo);
-    st_res<L>(x + lane * L, o);
-    from_rr<L, LR>(o, hi);
-    st_res<L>(x + (lane + m / 2) * L, o);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        uint32_t c[LR], o[L];
+        canon<LR>(c, vv[j], mr);
+        from_rr<L, LR>(o, c);
+        st_res<L>(x + (lane + j * NT::TEAM) * L, o);
+    }
 }
 
 template <int m, int L, int LR, bool INV>
-__global__ void __launch_bounds__(kThreads) k_twiddle_ntt(LevelParams prm, ModRR<LR> mr) {
-    twiddle_ntt_group<m, L, LR, INV>(prm, mr, blockIdx.x, blockIdx.y);
+__global__ void __launch_bounds__(kThreads, (LR >= 5 || m >= 64) ? 3 : 4) k_twiddle_ntt(LevelParams prm, ModRR<LR> mr) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    twiddle_ntt_group<m, L, LR, INV>(prm, mr, blockIdx.x, blockIdx.y, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -530,16 +568,19 @@ __device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>
     using G = Geo<m, L>;
     const int n = (int)prm.len;
     const int log2n = 31 - __clz(n);
+    // the NTT form takes nb consecutive blocks per CTA so that every team has an element
+    const int nb = FORM == kFormNtt ? final_blocks_per_cta<m>(n) : 1;
+    const int nn = nb * n;
     uint32_t* sa = smem;
-    uint32_t* sb = smem + n * G::EW;
-    uint32_t* tbuf = sb + n * G::EW;
-    const uint64_t base = block * n;
+    uint32_t* sb = smem + nn * G::EW;
+    uint32_t* tbuf = sb + nn * G::EW;
+    const uint64_t base = block * nn;
     uint32_t* pa = prm.data;
     uint32_t* pb = prm.data + prm.poly_words;
-    for (int idx = threadIdx.x; idx < n * m; idx += kThreads) {
+    for (int idx = threadIdx.x; idx < nn * m; idx += kThreads) {
         int j = idx / m, t = idx % m;
         uint32_t x[L];
-        int slot = bitrev(j, log2n);
+        int slot = ((j >> log2n) << log2n) + bitrev(j & (n - 1), log2n);
         ld_res<L>(x, pa + ((base + j) * m + t) * L);
         st_res<L>(sa + slot * G::EW + t * L, x);
         ld_res<L>(x, pb + ((base + j) * m + t) * L);
@@ -547,7 +588,7 @@ __device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>
     }
     __syncthreads();
     const int root = G::TWO_M / n;
-    dft_dit<m, L>(sa, sb, 2, n, root, md);
+    dft_dit<m, L>(sa, 2 * nb, n, root, md);
     // componentwise products c_v = a_v * b_v * (2M)^-1
     Team<m, L> tm;
     if constexpr (FORM == kFormI8) {
@@ -578,40 +619,54 @@ __device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>
             __syncwarp();
         }
     } else if constexpr (FORM == kFormNtt) {
-        for (int v = tm.id; v < n; v += G::NTEAMS) {
-            const int lane = tm.lane;
-            uint32_t alo[LR], ahi[LR], blo[LR], bhi[LR], w[L];
-            ld_res<L>(w, sa + v * G::EW + lane * L);
-            to_rr<L, LR>(alo, w);
-            ld_res<L>(w, sa + v * G::EW + (lane + m / 2) * L);
-            to_rr<L, LR>(ahi, w);
-            ld_res<L>(w, sb + v * G::EW + lane * L);
-            to_rr<L, LR>(blo, w);
-            ld_res<L>(w, sb + v * G::EW + (lane + m / 2) * L);
-            to_rr<L, LR>(bhi, w);
-            ntt_forward<m, LR>(alo, ahi, lane, tm.mask, prm.ntt_cst, mr);
-            ntt_forward<m, LR>(blo, bhi, lane, tm.mask, prm.ntt_cst, mr);
+        // per team: an exchange buffer, then a buffer holding b's evaluations
+        // while a is transformed (one element in registers at a time)
+        using NT = NttTeam<m>;
+        NT nt;
+        uint32_t* buf = tbuf + nt.id * 2 * m * LR;
+        uint32_t* park = buf + m * LR + 4 * nt.lane * LR;
+        const int lane = nt.lane;
+#pragma unroll 1
+        for (int v = nt.id; v < nn; v += NT::NTEAMS) {
+            uint32_t x[4][LR], w[L];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                ld_res<L>(w, sb + v * G::EW + (lane + j * NT::TEAM) * L);
+                to_rr<L, LR>(x[j], w);
+            }
+            ntt_forward<m, LR>(x, buf, lane, nt.mask, prm.ntt_cst, mr);
             if (prm.ntt_prescale) {
                 // scale b first so that the product of two lazy evaluations stays in range
                 uint32_t c[LR];
                 ldg_rr<LR>(c, prm.ntt_cst + NttLayout<m>::PW_LO * LR);
-                mmul<LR>(blo, blo, c, mr);
-                mmul<LR>(bhi, bhi, c, mr);
-                mmul<LR>(alo, alo, blo, mr);
-                mmul<LR>(ahi, ahi, bhi, mr);
-                ntt_backward<m, LR>(alo, ahi, lane, tm.mask, prm.ntt_cst, NttLayout<m>::ONE, NttLayout<m>::ZLAST, mr);
-            } else {
-                mmul<LR>(alo, alo, blo, mr);
-                mmul<LR>(ahi, ahi, bhi, mr);
-                ntt_backward<m, LR>(alo, ahi, lane, tm.mask, prm.ntt_cst, NttLayout<m>::PW_LO, NttLayout<m>::PW_HI,
-                                    mr);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) mmul<LR>(x[j], x[j], c, mr);
             }
-            canon<LR>(alo, alo, mr);
-            canon<LR>(ahi, ahi, mr);
-            from_rr<L, LR>(w, alo);
-            st_res<L>(sa + v * G::EW + lane * L, w);
-            from_rr<L, LR>(w, ahi);
-            st_res<L>(sa + v * G::EW + (lane + m / 2) * L, w);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) st_rr<LR>(park + j * LR, x[j]);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                ld_res<L>(w, sa + v * G::EW + (lane + j * NT::TEAM) * L);
+                to_rr<L, LR>(x[j], w);
+            }
+            ntt_forward<m, LR>(x, buf, lane, nt.mask, prm.ntt_cst, mr);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                uint32_t y[LR];
+                ld_rr<LR>(y, park + j * LR);
+                mmul<LR>(x[j], x[j], y, mr);
+            }
+            if (prm.ntt_prescale)
+                ntt_backward<m, LR>(x, buf, lane, nt.mask, prm.ntt_cst, NttLayout<m>::ONE, NttLayout<m>::ZLAST, mr);
+            else
+                ntt_backward<m, LR>(x, buf, lane, nt.mask, prm.ntt_cst, NttLayout<m>::PW_LO, NttLayout<m>::PW_HI, mr);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                uint32_t c[LR];
+                canon<LR>(c, x[j], mr);
+                from_rr<L, LR>(w, c);
+                st_res<L>(sa + v * G::EW + (lane + j * NT::TEAM) * L, w);
+            }
         }
     } else {
         uint32_t* X = tbuf + tm.id * TeamBuf<m, LR>::WORDS;
@@ -637,17 +692,18 @@ __device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>
     }
     __syncthreads();
     // first backwards level: DFT with root alpha^(-2m/n), natural in, bit-reversed out
-    dft_dif<m, L>(sa, n, (G::TWO_M - root) % G::TWO_M, md);
-    for (int idx = threadIdx.x; idx < n * m; idx += kThreads) {
+    dft_dif<m, L>(sa, nb, n, (G::TWO_M - root) % G::TWO_M, md);
+    for (int idx = threadIdx.x; idx < nn * m; idx += kThreads) {
         int j = idx / m, t = idx % m;
         uint32_t x[L];
-        ld_res<L>(x, sa + bitrev(j, log2n) * G::EW + t * L);
+        const int slot = ((j >> log2n) << log2n) + bitrev(j & (n - 1), log2n);
+        ld_res<L>(x, sa + slot * G::EW + t * L);
         st_res<L>(pa + ((base + j) * m + t) * L, x);
     }
 }
 
 template <int m, int L, int LR, int FORM>
-__global__ void __launch_bounds__(kThreads) k_final_pointwise(LevelParams prm, Mod<L> md, ModRR<LR> mr) {
+__global__ void __launch_bounds__(kThreads, FORM == kFormNtt ? (LR >= 5 ? 2 : 3) : 1) k_final_pointwise(LevelParams prm, Mod<L> md, ModRR<LR> mr) {
     extern __shared__ __align__(16) uint32_t smem[];
     final_block<m, L, LR, FORM>(prm, md, mr, smem, blockIdx.x);
 }
@@ -715,7 +771,7 @@ __device__ __forceinline__ void dft_inv_column(const LevelParams& prm, const Mod
         st_res<L>(col + j * G::EW + t * L, x);
     }
     __syncthreads();
-    dft_dif<m, L>(col, G::TWO_M, G::TWO_M - 1, md);
+    dft_dif<m, L>(col, 1, G::TWO_M, G::TWO_M - 1, md);
     for (int idx = threadIdx.x; idx < G::TWO_M * m; idx += kThreads) {
         int j = idx / m, t = idx % m;
         uint32_t x[L];
@@ -743,9 +799,16 @@ constexpr size_t twiddle_smem_bytes() {
 template <int m, int L, int LR>
 size_t final_smem_bytes(int n, int form = kFormDirect, int S = 0) {
     using G = Geo<m, L>;
-    const size_t tb = form == kFormI8 ? (size_t)kWarps * i8_warp_words<m, LR>(S)
-                                      : (size_t)G::NTEAMS * TeamBuf<m, LR>::WORDS;
-    return sizeof(uint32_t) * (2 * (size_t)n * G::EW + tb);
+    const size_t tb = form == kFormI8    ? (size_t)kWarps * i8_warp_words<m, LR>(S)
+                      : form == kFormNtt ? (size_t)NttTeam<m>::NTEAMS * 2 * m * LR
+                                         : (size_t)G::NTEAMS * TeamBuf<m, LR>::WORDS;
+    const size_t nn = (size_t)n * (form == kFormNtt ? final_blocks_per_cta<m>(n) : 1);
+    return sizeof(uint32_t) * (2 * nn * G::EW + tb);
+}
+
+template <int m, int L, int LR>
+constexpr size_t twiddle_ntt_smem_bytes() {
+    return sizeof(uint32_t) * (size_t)NttTeam<m>::NTEAMS * m * LR;
 }
 
 template <int m, int L, int LR>

@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(kThreads) k_final_dft(LevelParams prm, Mod<L> 
         st_res<L>(smem + bitrev(j, log2n) * G::EW + t * L, x);
     }
     __syncthreads();
-    dft_dit<m, L>(smem, smem, 1, n, G::TWO_M / n, md);
+    dft_dit<m, L>(smem, 1, n, G::TWO_M / n, md);
     for (int idx = threadIdx.x; idx < n * m; idx += kThreads) {
         int j = idx / m, t = idx % m;
         uint32_t x[L];
@@ -101,11 +101,13 @@ dkss_status prepare(dkss_plan_s* pl) {
     using G = Geo<m, L>;
     const int colb = (int)column_smem_bytes<m, L>();
     const int twb = (int)twiddle_smem_bytes<m, L, LR>();
-    const int fin = (int)final_smem_bytes<m, L, LR>((int)pl->r_last);
+    const bool direct = (pl->flags & (DKSS_RMUL_DIRECT | DKSS_FORM_INT8TC)) != 0;
+    const int fin = (int)final_smem_bytes<m, L, LR>((int)pl->r_last, direct ? kFormDirect : kFormNtt);
+    const int twn = (int)twiddle_ntt_smem_bytes<m, L, LR>();
     int optin = 0;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device) != cudaSuccess)
         return DKSS_ECUDA;
-    if (colb > optin || twb > optin || fin > optin) return DKSS_EUNSUPPORTED;
+    if (colb > optin || twb > optin || twn > optin || fin > optin) return DKSS_EUNSUPPORTED;
     if (pl->flags & DKSS_FORM_INT8TC) {
         if constexpr (m >= 32) {
             // INT8 form: sized for the largest byte count (16), shared by all plans of this kind
@@ -126,6 +128,7 @@ dkss_status prepare(dkss_plan_s* pl) {
     // (m, L, LR): set it to the most any plan can ask for (last level of
     // length 2m), capped by the device, so that no plan lowers another's.
     const int fin_max = (int)std::min<size_t>(final_smem_bytes<m, L, LR>(G::TWO_M), (size_t)optin);
+    const int fin_ntt_max = (int)std::min<size_t>(final_smem_bytes<m, L, LR>(G::TWO_M, kFormNtt), (size_t)optin);
     const int fdft_max = (int)std::min<size_t>(sizeof(uint32_t) * G::TWO_M * G::EW, (size_t)optin);
     if (cudaFuncSetAttribute(k_dft_fwd<m, L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, colb) ||
         cudaFuncSetAttribute(k_dft_fwd<m, L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, colb) ||
@@ -135,7 +138,9 @@ dkss_status prepare(dkss_plan_s* pl) {
         cudaFuncSetAttribute(k_final_pointwise<m, L, LR, kFormDirect>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              fin_max) ||
         cudaFuncSetAttribute(k_final_pointwise<m, L, LR, kFormNtt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             fin_max) ||
+                             fin_ntt_max) ||
+        cudaFuncSetAttribute(k_twiddle_ntt<m, L, LR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, twn) ||
+        cudaFuncSetAttribute(k_twiddle_ntt<m, L, LR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, twn) ||
         cudaFuncSetAttribute(k_final_dft<m, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, fdft_max))
         return DKSS_ECUDA;
     // launches per dkss_mul: per radix-2m level a DFT and a twiddle launch forward
@@ -167,8 +172,11 @@ static dkss_status launch_twiddle(dkss_plan_s* pl, LevelParams lp, int operands,
         }
     } else if (pl->flags & DKSS_RMUL_DIRECT)
         k_twiddle<m, L, LR, INV><<<grid, kThreads, twiddle_smem_bytes<m, L, LR>(), st>>>(lp, mr);
-    else
-        k_twiddle_ntt<m, L, LR, INV><<<grid, kThreads, 0, st>>>(lp, mr);
+    else {
+        // one team per element of the level (those with twiddle 1 return at once)
+        dim3 gn((unsigned)((pl->P2 + NttTeam<m>::NTEAMS - 1) / NttTeam<m>::NTEAMS), operands);
+        k_twiddle_ntt<m, L, LR, INV><<<gn, kThreads, twiddle_ntt_smem_bytes<m, L, LR>(), st>>>(lp, mr);
+    }
     DKSS_CHECK_LAUNCH();
     return DKSS_OK;
 }
@@ -216,8 +224,9 @@ dkss_status run_mul(dkss_plan_s* pl, const uint64_t* a, const uint64_t* b, uint6
             k_final_pointwise<m, L, LR, kFormDirect><<<blocks, kThreads, final_smem_bytes<m, L, LR>((int)pl->r_last), st>>>(
                 lp, md, mr);
         } else {
-            k_final_pointwise<m, L, LR, kFormNtt><<<blocks, kThreads, final_smem_bytes<m, L, LR>((int)pl->r_last), st>>>(
-                lp, md, mr);
+            const unsigned nblocks = blocks / (unsigned)final_blocks_per_cta<m>((int)pl->r_last);
+            k_final_pointwise<m, L, LR, kFormNtt>
+                <<<nblocks, kThreads, final_smem_bytes<m, L, LR>((int)pl->r_last, kFormNtt), st>>>(lp, md, mr);
         }
         DKSS_CHECK_LAUNCH();
     }

@@ -11,11 +11,14 @@
 // plan tabulates them directly; alpha^r is applied before the transform as a
 // negacyclic coefficient shift, as in the direct form.
 //
-// One team of m/2 lanes owns an element; lane l holds two coefficients.
-// Forward stages use Cooley-Tukey butterflies with psi^brv(k) (psi = gamma),
-// which leave evaluations in bit-reversed order; backwards stages use
-// Gentleman-Sande butterflies with psi^-brv(k) and return natural order.
-// Between stages lanes l and l ^ 2^b swap one value with a shuffle.
+// One team of m/4 lanes owns an element; each lane holds four residues whose
+// indices differ in two "local" index bits, so two butterfly stages run in
+// registers (two independent butterflies per lane and stage), after which the
+// team exchanges values through its shared-memory buffer to make the next two
+// index bits local.  Forward stages use Cooley-Tukey butterflies with
+// psi^brv(k) (psi = gamma), which leave evaluations in bit-reversed order;
+// backwards stages use Gentleman-Sande butterflies with psi^-brv(k) and
+// return natural order.
 //
 // Arithmetic is lazy: residues are vectors of LR limbs of nominally 26 bits,
 // a sum is a limbwise addition (limbs may grow past 26 bits), a difference
@@ -125,69 +128,111 @@ __device__ __forceinline__ void lz_norm(uint32_t (&x)[LR]) {
     x[LR - 1] += carry;
 }
 
-template <int m, int LR>
-__device__ __forceinline__ void team_swap(uint32_t (&lo)[LR], uint32_t (&hi)[LR], int lane, int b, unsigned mask) {
-    const bool bit = (lane >> b) & 1;
-#pragma unroll
-    for (int w = 0; w < LR; ++w) {
-        const uint32_t send = bit ? lo[w] : hi[w];
-        const uint32_t recv = __shfl_xor_sync(mask, send, 1 << b, m / 2);
-        if (bit) lo[w] = recv;
-        else hi[w] = recv;
-    }
+// Position of index i in a team's exchange buffer: an XOR swizzle of its
+// low bits by its high bits, so that in every layout below the eight lanes of
+// a quarter warp touch eight different 16-byte bank groups (m = 32, 64).
+template <int m>
+__device__ __forceinline__ int xpos(int i) {
+    if constexpr (m == 32) return i ^ (((i >> 3) & 1) * 2) ^ (((i >> 4) & 1) * 5);
+    else if constexpr (m == 64) return i ^ ((i >> 3) & 1) ^ (((i >> 4) & 1) * 6);
+    else return i;
 }
 
-// Forward negacyclic transform: on entry lane l holds coefficients l, l+m/2;
-// on exit the evaluations with bit-reversed indices 2l, 2l+1 (lazy).
+// Index held in slot j (0..3) by lane l when the local index bits are (h, h-1).
+__device__ __forceinline__ int lidx(int l, int j, int h) {
+    const int low = (1 << (h - 1)) - 1;
+    return ((l & ~low) << 2) | (j << (h - 1)) | (l & low);
+}
+
+// Re-deal the team's 4 m/4 residues from local bits (h_from, h_from - 1) to
+// (h_to, h_to - 1) through the team's buffer (m residues of LR words).
 template <int m, int LR>
-__device__ __forceinline__ void ntt_forward(uint32_t (&lo)[LR], uint32_t (&hi)[LR], int lane, unsigned mask,
+__device__ __forceinline__ void ntt_exchange(uint32_t (&v)[4][LR], uint32_t* buf, int lane, int h_from, int h_to,
+                                             unsigned mask) {
+    __syncwarp(mask);   // the team's last reads of buf are done
+#pragma unroll
+    for (int j = 0; j < 4; ++j) st_rr<LR>(buf + xpos<m>(lidx(lane, j, h_from)) * LR, v[j]);
+    __syncwarp(mask);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) ld_rr<LR>(v[j], buf + xpos<m>(lidx(lane, j, h_to)) * LR);
+}
+
+// Forward negacyclic transform (lazy).  On entry slot j of lane l holds
+// coefficient l + j m/4; on exit the evaluations at bit-reversed positions
+// 4l + j.
+template <int m, int LR>
+__device__ __forceinline__ void ntt_forward(uint32_t (&v)[4][LR], uint32_t* buf, int lane, unsigned mask,
                                             const uint32_t* cst, const ModRR<LR>& md) {
     using NL = NttLayout<m>;
+    constexpr int LG = NL::LG;
     uint32_t bf[LR];
     ldg_rr<LR>(bf, cst + NL::BF * LR);
+    int h = LG - 1;
 #pragma unroll
-    for (int b = NL::LG - 1; b >= 0; --b) {
-        if (b < NL::LG - 1) team_swap<m, LR>(lo, hi, lane, b, mask);
-        const int k = (1 << (NL::LG - 1 - b)) + (lane >> b);
-        uint32_t z[LR], t[LR];
-        ldg_rr<LR>(z, cst + (NL::ZF + k) * LR);
-        mmul<LR>(t, hi, z, md);
-        lz_sub<LR>(hi, lo, bf, t);        // lo - t
-        lz_add<LR>(lo, lo, t);            // lo + t
+    for (int b = LG - 1; b >= 0; --b) {
+        if ((LG - 1 - b) % 2 == 0 && b != LG - 1) {   // a new pair of stages: make bits (b, b-1) local
+            const int hn = b >= 1 ? b : 1;
+            ntt_exchange<m, LR>(v, buf, lane, h, hn, mask);
+            h = hn;
+        }
+        const int sbit = b == h ? 2 : 1;               // slot bit of index bit b
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const int jl = sbit == 2 ? p : 2 * p, jh = jl + sbit;
+            const int k = (1 << (LG - 1 - b)) + (lidx(lane, jl, h) >> (b + 1));
+            uint32_t z[LR], t[LR];
+            ldg_rr<LR>(z, cst + (NL::ZF + k) * LR);
+            mmul<LR>(t, v[jh], z, md);
+            lz_sub<LR>(v[jh], v[jl], bf, t);       // lo - t
+            lz_add<LR>(v[jl], v[jl], t);           // lo + t
+        }
     }
 }
 
-// Backwards transform scaled by a constant: on entry lane l holds the
-// evaluations 2l, 2l+1 (bit-reversed order); on exit the coefficients l,
-// l+m/2 of the interpolated element times c (normalised, below 2q), where the
-// last stage multiplies by cst[lo_c] and cst[hi_c] (= c and psi^-1 c, times R').
+// Backwards transform scaled by a constant.  On entry slot j of lane l holds
+// the evaluation at bit-reversed position 4l + j; on exit coefficient
+// l + j m/4 of the interpolated element times c (normalised, below 2q), where
+// the last stage multiplies by cst[lo_c] and cst[hi_c] (= c and psi^-1 c,
+// times R').
 template <int m, int LR>
-__device__ __forceinline__ void ntt_backward(uint32_t (&lo)[LR], uint32_t (&hi)[LR], int lane, unsigned mask,
+__device__ __forceinline__ void ntt_backward(uint32_t (&v)[4][LR], uint32_t* buf, int lane, unsigned mask,
                                              const uint32_t* cst, int lo_c, int hi_c, const ModRR<LR>& md) {
     using NL = NttLayout<m>;
+    constexpr int LG = NL::LG;
+    int h = 1;
 #pragma unroll
-    for (int b = 0; b < NL::LG; ++b) {
-        if (b > 0) team_swap<m, LR>(lo, hi, lane, b - 1, mask);
-        uint32_t bias[LR], s[LR], d[LR], z[LR];
-        if (b == NL::LG - 1) {          // sums of m/2 values: bring the limbs back to 26 bits
-            lz_norm<LR>(lo);
-            lz_norm<LR>(hi);
+    for (int b = 0; b < LG; ++b) {
+        if (b % 2 == 0 && b != 0) {                      // make bits (b+1, b) local
+            const int hn = b + 1 <= LG - 1 ? b + 1 : LG - 1;
+            ntt_exchange<m, LR>(v, buf, lane, h, hn, mask);
+            h = hn;
         }
-        ldg_rr<LR>(bias, cst + (NL::BB + b) * LR);
-        lz_add<LR>(s, lo, hi);                  // u + v
-        lz_sub<LR>(d, lo, bias, hi);            // u - v
-        if (b == NL::LG - 1) {
-            uint32_t c[LR];
-            ldg_rr<LR>(c, cst + lo_c * LR);
-            ldg_rr<LR>(z, cst + hi_c * LR);
-            mmul<LR>(lo, s, c, md);
-            mmul<LR>(hi, d, z, md);
-        } else {
-            const int k = (1 << (NL::LG - 1 - b)) + (lane >> b);
-            ldg_rr<LR>(z, cst + (NL::ZI + k) * LR);
+        if (b == LG - 1) {                               // sums of m/2 values: limbs back to 26 bits
 #pragma unroll
-            for (int w = 0; w < LR; ++w) lo[w] = s[w];
-            mmul<LR>(hi, d, z, md);
+            for (int j = 0; j < 4; ++j) lz_norm<LR>(v[j]);
+        }
+        uint32_t bias[LR];
+        ldg_rr<LR>(bias, cst + (NL::BB + b) * LR);
+        const int sbit = b == h ? 2 : 1;
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const int jl = sbit == 2 ? p : 2 * p, jh = jl + sbit;
+            uint32_t s[LR], d[LR], z[LR];
+            lz_add<LR>(s, v[jl], v[jh]);                 // u + v
+            lz_sub<LR>(d, v[jl], bias, v[jh]);           // u - v
+            if (b == LG - 1) {
+                uint32_t c[LR];
+                ldg_rr<LR>(c, cst + lo_c * LR);
+                ldg_rr<LR>(z, cst + hi_c * LR);
+                mmul<LR>(v[jl], s, c, md);
+                mmul<LR>(v[jh], d, z, md);
+            } else {
+                const int k = (1 << (LG - 1 - b)) + (lidx(lane, jl, h) >> (b + 1));
+                ldg_rr<LR>(z, cst + (NL::ZI + k) * LR);
+#pragma unroll
+                for (int w = 0; w < LR; ++w) v[jl][w] = s[w];
+                mmul<LR>(v[jh], d, z, md);
+            }
         }
     }
 }
