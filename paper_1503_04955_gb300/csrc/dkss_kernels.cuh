@@ -389,13 +389,13 @@ __device__ __forceinline__ void i8_stage_ext_from32(uint32_t* E, const uint32_t*
 // operand words and encodes them (Section 3.2.4) on the fly.
 // ---------------------------------------------------------------------------
 template <int m, int L, bool FIRST>
-__device__ __forceinline__ void dft_fwd_column(const LevelParams& prm, const Mod<L>& md, uint32_t* col, uint64_t column,
-                                               int op) {
+__device__ __forceinline__ void column_load_fwd(const LevelParams& prm, uint32_t* col, uint64_t column, int op) {
     using G = Geo<m, L>;
     constexpr int LOG2_TWO_M = ilog2<G::TWO_M>();
     uint32_t* poly = prm.data + (op ? prm.poly_words : 0);
-    const uint64_t mu_d = prm.len / G::TWO_M;
-    const uint64_t blk = column / mu_d, l = column % mu_d;
+    const int lg_mu = (__ffsll((long long)prm.len) - 1) - LOG2_TWO_M;
+    const uint64_t mu_d = 1ull << lg_mu;
+    const uint64_t blk = column >> lg_mu, l = column & (mu_d - 1);
     const uint64_t base = blk * prm.len;
     // element j of the column sits at base + j*mu_d + l; load it into slot bitrev(j)
     if constexpr (FIRST) {
@@ -419,6 +419,18 @@ __device__ __forceinline__ void dft_fwd_column(const LevelParams& prm, const Mod
             st_res<L>(col + bitrev(j, LOG2_TWO_M) * G::EW + t * L, x);
         }
     }
+}
+
+template <int m, int L, bool FIRST>
+__device__ __forceinline__ void dft_fwd_column(const LevelParams& prm, const Mod<L>& md, uint32_t* col, uint64_t column,
+                                               int op) {
+    using G = Geo<m, L>;
+    uint32_t* poly = prm.data + (op ? prm.poly_words : 0);
+    const int lg_mu = (__ffsll((long long)prm.len) - 1) - ilog2<G::TWO_M>();
+    const uint64_t mu_d = 1ull << lg_mu;
+    const uint64_t blk = column >> lg_mu, l = column & (mu_d - 1);
+    const uint64_t base = blk * prm.len;
+    column_load_fwd<m, L, FIRST>(prm, col, column, op);
     __syncthreads();
     dft_dit<m, L>(col, 1, G::TWO_M, 1, md);
     for (int idx = threadIdx.x; idx < G::TWO_M * m; idx += kThreads) {
@@ -554,6 +566,140 @@ template <int m, int L, int LR, bool INV>
 __global__ void __launch_bounds__(kThreads, (LR >= 5 || m >= 64) ? 3 : 4) k_twiddle_ntt(LevelParams prm, ModRR<LR> mr) {
     extern __shared__ __align__(16) uint32_t smem[];
     twiddle_ntt_group<m, L, LR, INV>(prm, mr, blockIdx.x, blockIdx.y, smem);
+}
+
+// ---------------------------------------------------------------------------
+// A radix-2m level fused with its bad multiplications (NTT form), one CTA per
+// column: forward, the column's inner DFT (integer ALU) and then the
+// R-multiplications of its 2m outputs (multiply pipe); backwards, the
+// R-multiplications of the column's inputs and then its inner DFT.  Several
+// CTAs per SM sit in different phases, so the two pipes overlap, and each
+// level reads and writes the polynomial once.  smem: the column (2m elements)
+// and the teams' exchange buffers.
+// ---------------------------------------------------------------------------
+template <int m, int L, int LR>
+__device__ __forceinline__ void level_rmul_element(const LevelParams& prm, const ModRR<LR>& mr, const uint32_t* src,
+                                                   uint32_t* dst, uint64_t e, uint32_t* buf, int lane, unsigned mask,
+                                                   const uint32_t (&bn)[LR]) {
+    using NT = NttTeam<m>;
+    const int r = (int)(e >> prm.log2_mu_top);
+    const uint64_t sidx = e & (prm.mu_top - 1);
+    uint32_t vv[4][LR];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) load_shifted_rr<m, L, LR>(vv[j], src, lane + j * NT::TEAM, r, bn);
+    ntt_forward<m, LR>(vv, buf, lane, mask, prm.ntt_cst, mr);
+    const uint32_t* tw = prm.table_eval + (sidx * m + 4 * lane) * LR;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        uint32_t t[LR];
+        ldg_rr<LR>(t, tw + j * LR);
+        mmul<LR>(vv[j], vv[j], t, mr);
+    }
+    ntt_backward<m, LR>(vv, buf, lane, mask, prm.ntt_cst, NttLayout<m>::TW_LO, NttLayout<m>::TW_HI, mr);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        uint32_t c[LR], o[L];
+        canon<LR>(c, vv[j], mr);
+        from_rr<L, LR>(o, c);
+        st_res<L>(dst + (lane + j * NT::TEAM) * L, o);
+    }
+}
+
+template <int m, int L, int LR, bool FIRST>
+__device__ __forceinline__ void level_fwd_ntt(const LevelParams& prm, const Mod<L>& md, const ModRR<LR>& mr,
+                                              uint32_t* smem, uint64_t column, int op) {
+    using G = Geo<m, L>;
+    using NT = NttTeam<m>;
+    uint32_t* col = smem;
+    uint32_t* xbuf = smem + G::TWO_M * G::EW;
+    uint32_t* poly = prm.data + (op ? prm.poly_words : 0);
+    const int lg_mu = (__ffsll((long long)prm.len) - 1) - ilog2<G::TWO_M>();
+    const uint64_t mu_d = 1ull << lg_mu;
+    const uint64_t blk = column >> lg_mu, l = column & (mu_d - 1);
+    const uint64_t base = blk * prm.len;
+    column_load_fwd<m, L, FIRST>(prm, col, column, op);
+    __syncthreads();
+    dft_dit<m, L>(col, 1, G::TWO_M, 1, md);     // ends with __syncthreads: output v in slot v
+    NT nt;
+    uint32_t* buf = xbuf + nt.id * m * LR;
+    uint32_t bn[LR];
+    ldg_rr<LR>(bn, prm.ntt_cst + NttLayout<m>::BN * LR);
+    for (int v = nt.id; v < G::TWO_M; v += NT::NTEAMS) {
+        const uint32_t* src = col + v * G::EW;
+        uint32_t* dst = poly + (base + (uint64_t)v * mu_d + l) * G::EW;
+        if (v == 0 || l == 0) {                  // twiddle 1
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                uint32_t x[L];
+                ld_res<L>(x, src + (nt.lane + j * NT::TEAM) * L);
+                st_res<L>(dst + (nt.lane + j * NT::TEAM) * L, x);
+            }
+            continue;
+        }
+        level_rmul_element<m, L, LR>(prm, mr, src, dst, (uint64_t)v * l * prm.bp, buf, nt.lane, nt.mask, bn);
+    }
+}
+
+template <int m, int L, int LR, bool FIRST>
+__global__ void __launch_bounds__(kThreads, m >= 64 ? 1 : 4)
+    k_level_fwd_ntt(LevelParams prm, Mod<L> md, ModRR<LR> mr) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    level_fwd_ntt<m, L, LR, FIRST>(prm, md, mr, smem, blockIdx.x, blockIdx.y);
+}
+
+template <int m, int L, int LR>
+__device__ __forceinline__ void level_inv_ntt(const LevelParams& prm, const Mod<L>& md, const ModRR<LR>& mr,
+                                              uint32_t* smem, uint64_t column) {
+    using G = Geo<m, L>;
+    using NT = NttTeam<m>;
+    constexpr int LOG2_TWO_M = ilog2<G::TWO_M>();
+    uint32_t* col = smem;
+    uint32_t* xbuf = smem + G::TWO_M * G::EW;
+    uint32_t* poly = prm.data;
+    const int lg_mu = (__ffsll((long long)prm.len) - 1) - LOG2_TWO_M;
+    const uint64_t mu_d = 1ull << lg_mu;
+    const uint64_t blk = column >> lg_mu, l = column & (mu_d - 1);
+    const uint64_t base = blk * prm.len;
+    NT nt;
+    uint32_t* buf = xbuf + nt.id * m * LR;
+    uint32_t bn[LR];
+    ldg_rr<LR>(bn, prm.ntt_cst + NttLayout<m>::BN * LR);
+    // element v of the column times rho^(-v l bp), into slot v
+    for (int v = nt.id; v < G::TWO_M; v += NT::NTEAMS) {
+        const uint32_t* src = poly + (base + (uint64_t)v * mu_d + l) * G::EW;
+        uint32_t* dst = col + v * G::EW;
+        if (v == 0 || l == 0) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                uint32_t x[L];
+                ld_res<L>(x, src + (nt.lane + j * NT::TEAM) * L);
+                st_res<L>(dst + (nt.lane + j * NT::TEAM) * L, x);
+            }
+            continue;
+        }
+        level_rmul_element<m, L, LR>(prm, mr, src, dst, prm.P2 - (uint64_t)v * l * prm.bp, buf, nt.lane, nt.mask,
+                                     bn);
+    }
+    __syncthreads();
+    dft_dif<m, L>(col, 1, G::TWO_M, G::TWO_M - 1, md);
+    for (int idx = threadIdx.x; idx < G::TWO_M * m; idx += kThreads) {
+        int j = idx / m, t = idx % m;
+        uint32_t x[L];
+        ld_res<L>(x, col + bitrev(j, LOG2_TWO_M) * G::EW + t * L);
+        st_res<L>(poly + ((base + (uint64_t)j * mu_d + l) * m + t) * L, x);
+    }
+}
+
+template <int m, int L, int LR>
+__global__ void __launch_bounds__(kThreads, m >= 64 ? 1 : 4)
+    k_level_inv_ntt(LevelParams prm, Mod<L> md, ModRR<LR> mr) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    level_inv_ntt<m, L, LR>(prm, md, mr, smem, blockIdx.x);
+}
+
+template <int m, int L, int LR>
+constexpr size_t level_ntt_smem_bytes() {
+    return sizeof(uint32_t) * ((size_t)Geo<m, L>::TWO_M * Geo<m, L>::EW + (size_t)NttTeam<m>::NTEAMS * m * LR);
 }
 
 // ---------------------------------------------------------------------------

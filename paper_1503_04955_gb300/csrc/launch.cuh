@@ -96,6 +96,15 @@ __global__ void k_unpermute(const uint32_t* src, uint64_t* dst, uint64_t P2, uin
         if (cudaGetLastError() != cudaSuccess) return DKSS_ECUDA; \
     } while (0)
 
+// The NTT form runs each radix-2m level as one fused kernel (column DFT and
+// its R-multiplications) when a column and the exchange buffers fit three or
+// more CTAs per SM; bigger columns (m = 64 with 4-word residues) keep the
+// separate DFT and element-parallel twiddle kernels.
+template <int m, int L, int LR>
+static bool fused_levels(const dkss_plan_s* pl) {
+    return !(pl->flags & (DKSS_RMUL_DIRECT | DKSS_FORM_INT8TC)) && level_ntt_smem_bytes<m, L, LR>() <= 64 * 1024;
+}
+
 template <int m, int L, int LR>
 dkss_status prepare(dkss_plan_s* pl) {
     using G = Geo<m, L>;
@@ -104,10 +113,11 @@ dkss_status prepare(dkss_plan_s* pl) {
     const bool direct = (pl->flags & (DKSS_RMUL_DIRECT | DKSS_FORM_INT8TC)) != 0;
     const int fin = (int)final_smem_bytes<m, L, LR>((int)pl->r_last, direct ? kFormDirect : kFormNtt);
     const int twn = (int)twiddle_ntt_smem_bytes<m, L, LR>();
+    const int lvl = (int)level_ntt_smem_bytes<m, L, LR>();
     int optin = 0;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device) != cudaSuccess)
         return DKSS_ECUDA;
-    if (colb > optin || twb > optin || twn > optin || fin > optin) return DKSS_EUNSUPPORTED;
+    if (colb > optin || twb > optin || twn > optin || fin > optin || lvl > optin) return DKSS_EUNSUPPORTED;
     if (pl->flags & DKSS_FORM_INT8TC) {
         if constexpr (m >= 32) {
             // INT8 form: sized for the largest byte count (16), shared by all plans of this kind
@@ -139,13 +149,17 @@ dkss_status prepare(dkss_plan_s* pl) {
                              fin_max) ||
         cudaFuncSetAttribute(k_final_pointwise<m, L, LR, kFormNtt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              fin_ntt_max) ||
+        cudaFuncSetAttribute(k_level_fwd_ntt<m, L, LR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lvl) ||
+        cudaFuncSetAttribute(k_level_fwd_ntt<m, L, LR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lvl) ||
+        cudaFuncSetAttribute(k_level_inv_ntt<m, L, LR>, cudaFuncAttributeMaxDynamicSharedMemorySize, lvl) ||
         cudaFuncSetAttribute(k_twiddle_ntt<m, L, LR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, twn) ||
         cudaFuncSetAttribute(k_twiddle_ntt<m, L, LR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, twn) ||
         cudaFuncSetAttribute(k_final_dft<m, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, fdft_max))
         return DKSS_ECUDA;
     // launches per dkss_mul: per radix-2m level a DFT and a twiddle launch forward
     // and backwards, the fused last level, three decode kernels
-    pl->launches = 4 * pl->col_levels + 1 + 3;
+    // (the NTT form fuses each level's DFT and R-multiplications into one launch)
+    pl->launches = (fused_levels<m, L, LR>(pl) ? 2 : 4) * pl->col_levels + 1 + 3;
     return DKSS_OK;
 }
 
@@ -186,8 +200,19 @@ static dkss_status launch_forward_levels(dkss_plan_s* pl, LevelParams lp, int op
     using G = Geo<m, L>;
     const Mod<L> md = make_mod<L>(pl);
     dim3 grid((unsigned)(pl->P2 / G::TWO_M), operands);
+    const bool fused = fused_levels<m, L, LR>(pl);
     for (uint32_t d = 0; d < pl->col_levels; ++d) {
         level_geometry(pl, d, &lp.len, &lp.bp);
+        if (fused) {   // inner DFT and R-multiplications of a column in one kernel (NTT form)
+            ProfScope ps(pl, st, kProfFwdTwiddle);
+            const ModRR<LR> mr = make_modrr<LR>(pl);
+            if (d == 0)
+                k_level_fwd_ntt<m, L, LR, true><<<grid, kThreads, level_ntt_smem_bytes<m, L, LR>(), st>>>(lp, md, mr);
+            else
+                k_level_fwd_ntt<m, L, LR, false><<<grid, kThreads, level_ntt_smem_bytes<m, L, LR>(), st>>>(lp, md, mr);
+            DKSS_CHECK_LAUNCH();
+            continue;
+        }
         {
             ProfScope ps(pl, st, kProfFwdDft);
             if (d == 0) k_dft_fwd<m, L, true><<<grid, kThreads, column_smem_bytes<m, L>(), st>>>(lp, md);
@@ -230,8 +255,16 @@ dkss_status run_mul(dkss_plan_s* pl, const uint64_t* a, const uint64_t* b, uint6
         }
         DKSS_CHECK_LAUNCH();
     }
+    const bool fused = fused_levels<m, L, LR>(pl);
     for (int d = (int)pl->col_levels - 1; d >= 0; --d) {
         level_geometry(pl, (uint32_t)d, &lp.len, &lp.bp);
+        if (fused) {   // R-multiplications and inner DFT of a column in one kernel (NTT form)
+            ProfScope ps(pl, st, kProfInvTwiddle);
+            k_level_inv_ntt<m, L, LR><<<(unsigned)(pl->P2 / G::TWO_M), kThreads, level_ntt_smem_bytes<m, L, LR>(), st>>>(
+                lp, md, mr);
+            DKSS_CHECK_LAUNCH();
+            continue;
+        }
         {
             ProfScope ps(pl, st, kProfInvTwiddle);
             s = launch_twiddle<m, L, LR, true>(pl, lp, 1, st);
