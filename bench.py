@@ -48,7 +48,7 @@ SM_MAX_MHZ = 2070.0
 HBM_GBS = 6782.1                  # measured copy bandwidth of the GB300s (MEASURED_PEAKS.json)
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture
 # (profiles/stage_kernels_dkss_2p24b.md); valid only for the kernel version captured.
-NCU_TRAFFIC_BYTES = {("dkss_2p24b", "ntt", "fwd_twiddle"): 65.9e6}
+NCU_TRAFFIC_BYTES = {("dkss_2p24b", "ntt", "fwd_twiddle"): 45.1e6}
 
 
 def parse_args():

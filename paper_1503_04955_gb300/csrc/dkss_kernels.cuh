@@ -770,7 +770,7 @@ __device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>
         using NT = NttTeam<m>;
         NT nt;
         uint32_t* buf = tbuf + nt.id * 2 * m * LR;
-        uint32_t* park = buf + m * LR + 4 * nt.lane * LR;
+        uint32_t* park = buf + m * LR + nt.lane * LR;     // residue j at park + j * TEAM * LR
         const int lane = nt.lane;
 #pragma unroll 1
         for (int v = nt.id; v < nn; v += NT::NTEAMS) {
@@ -789,7 +789,7 @@ __device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>
                 for (int j = 0; j < 4; ++j) mmul<LR>(x[j], x[j], c, mr);
             }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) st_rr<LR>(park + j * LR, x[j]);
+            for (int j = 0; j < 4; ++j) st_rr<LR>(park + j * NT::TEAM * LR, x[j]);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 ld_res<L>(w, sa + v * G::EW + (lane + j * NT::TEAM) * L);
@@ -799,7 +799,7 @@ __device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 uint32_t y[LR];
-                ld_rr<LR>(y, park + j * LR);
+                ld_rr<LR>(y, park + j * NT::TEAM * LR);
                 mmul<LR>(x[j], x[j], y, mr);
             }
             if (prm.ntt_prescale)
