@@ -48,6 +48,7 @@ SM_MAX_MHZ = 2070.0
 HBM_GBS = 6782.1                  # measured copy bandwidth of the GB300s (MEASURED_PEAKS.json)
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture
 # (profiles/stage_kernels_dkss_2p24b.md); valid only for the kernel version captured.
+FORM_FLAGS = {"eval": 0, "ntt": 128, "direct": 16}   # binding.LEVELS_COEF, binding.RMUL_DIRECT
 NCU_TRAFFIC_BYTES = {("dkss_2p24b", "ntt", "fwd_twiddle"): 45.1e6}
 
 
@@ -64,8 +65,9 @@ def parse_args():
     ap.add_argument("--batched-steps", type=int, default=10)
     ap.add_argument("--no-forms", action="store_true", help="skip the R-multiplication form comparison")
     ap.add_argument("--form-steps", type=int, default=20)
-    ap.add_argument("--form", default="ntt", choices=["ntt", "direct"],
-                    help="R-multiplications through the evaluation map of R (ntt) or the direct convolution")
+    ap.add_argument("--form", default="eval", choices=["eval", "ntt", "direct"],
+                    help="inner levels in evaluation coordinates (eval, the default), every level on coefficients "
+                         "with R-multiplications through the evaluation map of R (ntt), or the direct convolution")
     return ap.parse_args()
 
 
@@ -149,6 +151,37 @@ def rmul_imads(m, L, form, pointwise=False):
     return (forwards * (m // 2) * lg + m + (m // 2) * (lg + 1)) * modmul_imads(L)
 
 
+def nontrivial_dft_products(n):
+    """Twiddle products of a radix-2 DIT of n points other than those by 1."""
+    return sum(n // 2 - n // (2 << s) for s in range(1, n.bit_length() - 1))
+
+
+def stage_work_eval(info, m, L):
+    """Algorithmic multiply-adds of the levels-in-evaluation-coordinates form,
+    by kernel group: level 0 maps every element to evaluation coordinates (m/2
+    log m products) and multiplies its twiddle (m); levels d >= 1 run 2m-point
+    DFTs over P per coordinate and pointwise twiddles; the last level r-point
+    DFTs, the scaled componentwise products (2 per coordinate) and inverse DFTs;
+    backwards, pointwise twiddles, DFTs, and level 0's return to coefficients
+    (m/2 (log m + 1)).  Products by 1 are not counted."""
+    P2, col_levels = info["P2"], info["levels"] - 1
+    lg = m.bit_length() - 1
+    r_last = P2 // (2 * m) ** col_levels
+    nontrivial, length = [], P2
+    for _ in range(col_levels):
+        mu_d = length // (2 * m)
+        nontrivial.append((P2 // length) * (mu_d - 1) * (2 * m - 1))
+        length //= 2 * m
+    cols = P2 // (2 * m)
+    dft = cols * m * nontrivial_dft_products(2 * m)
+    fwd = P2 * (m // 2) * lg + nontrivial[0] * m + sum(dft + nt * m for nt in nontrivial[1:])
+    fin = 2 * (P2 // r_last) * m * nontrivial_dft_products(r_last) + 2 * P2 * m + (P2 // r_last) * m * nontrivial_dft_products(r_last)
+    inv = P2 * (m // 2) * (lg + 1) + nontrivial[0] * m + sum(dft + nt * m for nt in nontrivial[1:])
+    k = modmul_imads(L)
+    return {"fwd_twiddle": (2 * fwd * k, col_levels), "final_pointwise": (fin * k, 1),
+            "inv_twiddle": (inv * k, col_levels)}
+
+
 def stage_work(info, m, form):
     """Per kernel group: (algorithmic 32-bit multiply-adds per step, launches
     per step).  Twiddles rho^0 = 1 are not work; every other twiddle and every
@@ -156,6 +189,8 @@ def stage_work(info, m, form):
     each product coefficient by (2M)^-1 with one Montgomery product).  The
     inner DFTs have no products."""
     P2, L, col_levels = info["P2"], info["L"], info["levels"] - 1
+    if form == "eval":
+        return stage_work_eval(info, m, L)
     nontrivial = []
     length = P2
     for _ in range(col_levels):
@@ -199,7 +234,7 @@ def run_ours(args):
     cfg = syn.workload_params(args.workload)
     n_bits = cfg[0]
     A, B = syn.operand_pair(n_bits, syn.config_seed(syn.WORKLOADS[args.workload]["index"]), product=rank)
-    flags = binding.FORM_PROFILE | (binding.RMUL_DIRECT if args.form == "direct" else 0)
+    flags = binding.FORM_PROFILE | FORM_FLAGS[args.form]
     plan = dk.Plan(*cfg, flags=flags)
     info = plan.info()
     a = torch.from_numpy(A.view(np.int64)).to(dev)
@@ -341,7 +376,8 @@ def compare_forms(args, dev, flush, a, b, out, ms_main):
     cfg = syn.workload_params(args.workload)
     res = {}
     stream = torch.cuda.current_stream(dev)
-    for name, flags in (("ntt", 0), ("direct", binding.RMUL_DIRECT), ("int8tc", binding.FORM_INT8TC)):
+    for name, flags in (("eval", 0), ("ntt", binding.LEVELS_COEF), ("direct", binding.RMUL_DIRECT),
+                        ("int8tc", binding.FORM_INT8TC)):
         if name == args.form:
             res[name] = {"ms_per_step": round(ms_main, 5)}
             continue

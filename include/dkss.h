@@ -53,8 +53,14 @@ enum {
                               (mma.sync u8, byte slices of the residues); m >= 32 */
     DKSS_PROFILE = 4,      /* per-stage CUDA-event timing, read with dkss_profile_read */
     DKSS_DEBUG_CHECKS = 8, /* reserved: extra device-side range checks */
-    DKSS_RMUL_DIRECT = 16  /* R-multiplications by the direct negacyclic convolution
+    DKSS_RMUL_DIRECT = 16, /* R-multiplications by the direct negacyclic convolution
                               (Section 2.9.2) instead of through the evaluation map of R */
+    DKSS_LEVELS_COEF = 128 /* every level's inner DFT by alpha-shifts on coefficients.  By
+                              default (m <= 32, NTT form) every radix-2m level but the
+                              first, and the last level, run in the evaluation coordinates
+                              of R (the CRT map of Section 3.2.3): their inner DFTs become m
+                              independent DFTs over Z/p^zZ and their bad twiddles pointwise
+                              products */
 };
 
 /*
@@ -68,7 +74,9 @@ enum {
  *           M*(m/2)*(2^u-1)^2 (Section 3.2.2); m*p^z < 2^127 (so that
  *           products in 26-bit limbs stay within 5 limbs).
  *   flags   0 (R-multiplications through the evaluation map of R on the
- *           integer pipe), DKSS_RMUL_DIRECT (direct convolution, integer pipe)
+ *           integer pipe, inner levels in evaluation coordinates where m <= 32),
+ *           DKSS_LEVELS_COEF (the same R-multiplications, every inner DFT by
+ *           alpha-shifts), DKSS_RMUL_DIRECT (direct convolution, integer pipe)
  *           or DKSS_FORM_INT8TC (INT8 tensor cores; DKSS_EUNSUPPORTED if
  *           m < 32), optionally | DKSS_PROFILE.
  * On the host it tests p (deterministic Miller-Rabin), finds the smallest
@@ -176,9 +184,13 @@ dkss_status dkss_mul_batch(const dkss_job* jobs, size_t count, uint32_t flags, d
  * word, p^z high word, generator zeta, omega low, omega high, gamma low,
  * gamma high, LR (26-bit limbs of the product arithmetic), the form of the
  * R-multiplications (0 through the evaluation map, 1 direct convolution,
- * 2 INT8 tensor cores; a ring outside the evaluation-map form's limits on its
- * unreduced sums gets 1 unless the flags ask for 2), and 1 when that form
- * scales one factor of each componentwise product first (else 0).
+ * 2 INT8 tensor cores, 3 inner levels in evaluation coordinates (the default
+ * where it applies);
+ * a ring outside the evaluation-map form's limits on its unreduced sums gets
+ * 1 unless the flags ask for 2), 1 when form 0 (every level on
+ * coefficients) scales one factor of each componentwise product first (else
+ * 0), and 1 when the ring allows the inner levels in evaluation coordinates
+ * (else 0).
  */
 dkss_status dkss_plan_info(dkss_plan_t plan, uint64_t* consts, size_t n_consts, uint64_t* rho_out);
 

@@ -188,6 +188,8 @@ dkss_status plan_host(dkss_plan_s* pl, uint64_t n_bits, uint64_t M, uint32_t m, 
     for (uint32_t i = 0; i < 5; ++i) pl->kscale[i] = i < LR ? (uint32_t)(ks >> (26 * i)) & ((1u << 26) - 1) : 0;
     // limits of the lazy transform in R (NTT form of the R-multiplications)
     pl->ntt_ok = ntt_lazy_bounds(m, LR, q, &pl->ntt_bias);
+    pl->eval_levels = !(pl->flags & (DKSS_RMUL_DIRECT | DKSS_FORM_INT8TC | DKSS_LEVELS_COEF)) && m <= 32 &&
+                      pl->ntt_ok && pl->ntt_bias.eval_ok;
     return DKSS_OK;
 }
 
@@ -238,7 +240,7 @@ void build_ntt_consts(const dkss_plan_s* pl, std::vector<uint32_t>& out) {
     uint32_t lg = 0;
     while ((1u << lg) < m) ++lg;
     // layout of NttLayout<m> (ntt_rmul.cuh)
-    const uint32_t Q = 2 * m + lg + 2, COUNT = Q + 7;
+    const uint32_t Q = 2 * m + lg + 2, COUNT = Q + 8 + 2 * m;
     out.assign((size_t)COUNT * LR, 0);
     MontCtx c(pl->q);
     const u128 rdev = pow2_mod(26 * (int)LR, pl->q);
@@ -270,6 +272,61 @@ void build_ntt_consts(const dkss_plan_s* pl, std::vector<uint32_t>& out) {
     // last backwards stage after a prescaled componentwise product: 1 and psi^-1
     put_rr(&out[(size_t)(Q + 5) * LR], rdev, LR);
     put_rr(&out[(size_t)(Q + 6) * LR], to_dev(c, zlast, rdev), LR);
+    // DFTs in evaluation coordinates: their bias and the powers psi^t, t < 2m
+    for (uint32_t i = 0; i < LR; ++i) out[(size_t)(Q + 7) * LR + i] = pl->ntt_bias.evl[i];
+    u128 pt = c.to(1);
+    for (uint32_t t = 0; t < 2 * m; ++t) {
+        put_rr(&out[(size_t)(Q + 8 + t) * LR], to_dev(c, pt, rdev), LR);
+        pt = c.mul(pt, psi);
+    }
+}
+
+// Bad twiddles of levels d >= 1 in evaluation coordinates (eval_levels.cuh):
+// rho^e(gamma^(2j+1)) = omega^(e(2j+1)) for every e = e' b_d (b_d = (2m)^d),
+// e' < 2M / b_d, at index i with j = brv(i), in device Montgomery form.  Level
+// d's table starts at word offs[d].
+void build_eval_level_tables(const dkss_plan_s* pl, std::vector<uint32_t>& out, std::vector<uint64_t>& offs) {
+    const uint32_t m = pl->m, LR = pl->LR;
+    uint32_t lg = 0;
+    while ((1u << lg) < m) ++lg;
+    MontCtx c(pl->q);
+    const u128 rdev = pow2_mod(26 * (int)LR, pl->q);
+    const u128 om = c.to(pl->roots.omega);
+    offs.assign(pl->col_levels + 1, 0);
+    uint64_t total = 0, bp = 1;
+    for (uint32_t d = 0; d < pl->col_levels; ++d) {
+        offs[d] = total;
+        if (d > 0) total += (pl->P2 / bp) * m * LR;
+        bp *= 2 * m;
+    }
+    offs[pl->col_levels] = total;
+    out.assign(total, 0);
+    bp = 2 * m;
+    for (uint32_t d = 1; d < pl->col_levels; ++d, bp *= 2 * m) {
+        const uint64_t n = pl->P2 / bp;
+        const u128 wb = c.pow(om, bp);   // omega^(b_d)
+        unsigned hw = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+        uint64_t chunks = std::min<uint64_t>(hw, n);
+        std::vector<std::thread> th;
+        for (uint64_t ci = 0; ci < chunks; ++ci) {
+            th.emplace_back([&, ci]() {
+                uint64_t e0 = n * ci / chunks, e1 = n * (ci + 1) / chunks;
+                u128 w = c.pow(wb, e0);
+                std::vector<u128> val(m);
+                for (uint64_t e = e0; e < e1; ++e) {
+                    u128 w2 = c.mul(w, w), cur = w;
+                    for (uint32_t j = 0; j < m; ++j) {
+                        val[j] = cur;
+                        cur = c.mul(cur, w2);
+                    }
+                    for (uint32_t i = 0; i < m; ++i)
+                        put_rr(&out[offs[d] + (e * m + i) * LR], to_dev(c, val[brv(i, lg)], rdev), LR);
+                    w = c.mul(w, wb);
+                }
+            });
+        }
+        for (auto& t : th) t.join();
+    }
 }
 
 // Evaluations of the bad twiddles: rho^s(gamma^(2j+1)) = omega^(s(2j+1)), stored
@@ -318,7 +375,9 @@ void free_device(dkss_plan_s* pl) {
     cudaFree(pl->d_status);
     cudaFree(pl->d_stage);
     cudaFree(pl->d_ntt);
+    cudaFree(pl->d_evtw);
     pl->d_ntt = nullptr;
+    pl->d_evtw = nullptr;
     pl->d_table = nullptr; pl->d_work = nullptr; pl->d_agg = nullptr; pl->d_status = nullptr; pl->d_stage = nullptr;
 }
 
@@ -328,13 +387,17 @@ bool overlap(const void* a, size_t an, const void* b, size_t bn) {
 }
 
 void fill_consts(const dkss_plan_s* pl, uint64_t* consts, size_t n) {
-    const uint64_t form = (pl->flags & DKSS_FORM_INT8TC) ? 2 : ((pl->flags & DKSS_RMUL_DIRECT) || !pl->ntt_ok) ? 1 : 0;
-    uint64_t v[14] = {pl->P2, pl->mu_top, pl->L, (uint64_t)pl->col_levels + 1, (uint64_t)pl->q,
+    const uint64_t form = (pl->flags & DKSS_FORM_INT8TC)                          ? 2
+                          : ((pl->flags & DKSS_RMUL_DIRECT) || !pl->ntt_ok)         ? 1
+                          : pl->eval_levels                                          ? 3
+                                                                                     : 0;
+    uint64_t v[15] = {pl->P2, pl->mu_top, pl->L, (uint64_t)pl->col_levels + 1, (uint64_t)pl->q,
                       (uint64_t)(pl->q >> 64), pl->roots.zeta, (uint64_t)pl->roots.omega,
                       (uint64_t)(pl->roots.omega >> 64), (uint64_t)pl->roots.gamma,
                       (uint64_t)(pl->roots.gamma >> 64), pl->LR, form,
-                      (uint64_t)(form == 0 && pl->ntt_bias.prescale)};
-    for (size_t i = 0; i < n && i < 14; ++i) consts[i] = v[i];
+                      (uint64_t)(pl->ntt_ok && pl->ntt_bias.prescale),
+                      (uint64_t)(pl->ntt_ok && pl->ntt_bias.eval_ok && pl->m <= 32)};
+    for (size_t i = 0; i < n && i < 15; ++i) consts[i] = v[i];
 }
 
 }  // namespace
@@ -359,6 +422,8 @@ dkss_status dkss_plan(dkss_plan_t* plan, uint64_t n_bits, uint64_t M, uint32_t m
     }
     // a ring outside the lazy transform's limits takes the direct convolution
     if (!pl->ntt_ok && !(flags & (DKSS_RMUL_DIRECT | DKSS_FORM_INT8TC))) pl->flags |= DKSS_RMUL_DIRECT;
+    // inner levels in evaluation coordinates: the NTT form, m <= 32, within their limits
+    pl->eval_levels = pl->eval_levels && !(pl->flags & DKSS_RMUL_DIRECT);
     if (cudaGetDevice(&pl->device) != cudaSuccess) {
         delete pl;
         return DKSS_ECUDA;
@@ -367,6 +432,8 @@ dkss_status dkss_plan(dkss_plan_t* plan, uint64_t n_bits, uint64_t M, uint32_t m
     if (pl->flags & (DKSS_RMUL_DIRECT | DKSS_FORM_INT8TC)) build_table(pl, table);
     else build_eval_table(pl, table);
     build_ntt_consts(pl, ntt);
+    std::vector<uint32_t> evtw;
+    if (pl->eval_levels) build_eval_level_tables(pl, evtw, pl->evtw_offs);
     pl->poly_words = pl->P2 * pl->m * pl->L;
     const uint64_t nw = (n_bits + 63) / 64;
     pl->n_tiles = (4 * nw + 2047) / 2048;
@@ -374,7 +441,8 @@ dkss_status dkss_plan(dkss_plan_t* plan, uint64_t n_bits, uint64_t M, uint32_t m
               cudaMalloc(&pl->d_work, 2 * pl->poly_words * sizeof(uint32_t)) == cudaSuccess &&
               cudaMalloc(&pl->d_agg, pl->n_tiles * sizeof(uint32_t)) == cudaSuccess &&
               cudaMalloc(&pl->d_status, sizeof(uint32_t)) == cudaSuccess &&
-              cudaMalloc(&pl->d_ntt, ntt.size() * sizeof(uint32_t)) == cudaSuccess;
+              cudaMalloc(&pl->d_ntt, ntt.size() * sizeof(uint32_t)) == cudaSuccess &&
+              (evtw.empty() || cudaMalloc(&pl->d_evtw, evtw.size() * sizeof(uint32_t)) == cudaSuccess);
     if (!ok) {
         cudaGetLastError();
         free_device(pl);
@@ -383,6 +451,8 @@ dkss_status dkss_plan(dkss_plan_t* plan, uint64_t n_bits, uint64_t M, uint32_t m
     }
     if (cudaMemcpy(pl->d_table, table.data(), table.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(pl->d_ntt, ntt.data(), ntt.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+        (!evtw.empty() &&
+         cudaMemcpy(pl->d_evtw, evtw.data(), evtw.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess) ||
         cudaMemset(pl->d_status, 0, sizeof(uint32_t)) != cudaSuccess) {
         free_device(pl);
         delete pl;

@@ -65,6 +65,7 @@ struct LevelParams {
     const uint32_t* ntt_cst;     // NttLayout<m> constants, LR words each
     uint32_t i8_S;               // bytes per residue (INT8 tensor-core form)
     uint32_t ntt_prescale;       // NTT form: scale b before the componentwise product
+    const uint32_t* tw_lvl;      // inner levels in evaluation coordinates: this level's twiddles
 };
 
 // How R-multiplications are computed.

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include "decode.cuh"
 #include "dkss_kernels.cuh"
+#include "eval_levels.cuh"
 #include "plan.hpp"
 
 namespace dkss {
@@ -156,6 +157,16 @@ dkss_status prepare(dkss_plan_s* pl) {
         cudaFuncSetAttribute(k_twiddle_ntt<m, L, LR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, twn) ||
         cudaFuncSetAttribute(k_final_dft<m, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, fdft_max))
         return DKSS_ECUDA;
+    if constexpr (m <= 32) {
+        if (pl->eval_levels) {
+            const int fe = (int)std::min<size_t>(final_eval_smem_bytes<m, L, LR>(G::TWO_M), (size_t)optin);
+            if ((int)final_eval_smem_bytes<m, L, LR>((int)pl->r_last) > optin) return DKSS_EUNSUPPORTED;
+            if (cudaFuncSetAttribute(k_level0_fwd_eval<m, L, LR>, cudaFuncAttributeMaxDynamicSharedMemorySize, lvl) ||
+                cudaFuncSetAttribute(k_level0_inv_eval<m, L, LR>, cudaFuncAttributeMaxDynamicSharedMemorySize, lvl) ||
+                cudaFuncSetAttribute(k_final_eval<m, L, LR>, cudaFuncAttributeMaxDynamicSharedMemorySize, fe))
+                return DKSS_ECUDA;
+        }
+    }
     // launches per dkss_mul: per radix-2m level a DFT and a twiddle launch forward
     // and backwards, the fused last level, three decode kernels
     // (the NTT form fuses each level's DFT and R-multiplications into one launch)
@@ -226,6 +237,82 @@ static dkss_status launch_forward_levels(dkss_plan_s* pl, LevelParams lp, int op
     return DKSS_OK;
 }
 
+// Decoding and carry propagation of the product polynomial in the plan's workspace.
+template <int m, int L, int LR>
+static dkss_status launch_decode(dkss_plan_s* pl, uint64_t* out, cudaStream_t st) {
+    DecodeParams dp{};
+    dp.c = pl->d_work;
+    dp.out = reinterpret_cast<uint32_t*>(out);
+    dp.agg = pl->d_agg;
+    dp.status = pl->d_status;
+    dp.P2 = pl->P2;
+    dp.n_windows = 4 * ((pl->n_bits + 63) / 64);
+    dp.n_tiles = pl->n_tiles;
+    dp.k_max = pl->P2 * (m / 2) + m / 2;
+    dp.m = m;
+    dp.h = m / 2;
+    dp.u = pl->u;
+    dp.db = 0;
+    for (dkss_host::u128 t = pl->q; t; t >>= 1) dp.db++;
+    dp.db += 1;
+    dp.out_aligned16 = ((uintptr_t)out & 15) == 0;
+    ProfScope ps(pl, st, kProfDecode);
+    if (pl->u == 32) k_decode_tiles_aligned<L, 1><<<(unsigned)pl->n_tiles, kDecThreads, 0, st>>>(dp);
+    else if (pl->u == 16) k_decode_tiles_aligned<L, 2><<<(unsigned)pl->n_tiles, kDecThreads, 0, st>>>(dp);
+    else k_decode_tiles<L><<<(unsigned)pl->n_tiles, kDecThreads, 0, st>>>(dp);
+    DKSS_CHECK_LAUNCH();
+    k_decode_scan<<<1, kScanThreads, 0, st>>>(dp);
+    DKSS_CHECK_LAUNCH();
+    k_decode_fix<<<(unsigned)((pl->n_tiles + 255) / 256), 256, 0, st>>>(dp);
+    DKSS_CHECK_LAUNCH();
+    return DKSS_OK;
+}
+
+// Inner levels in evaluation coordinates: level 0 forward, levels >= 1 and the last level in
+// evaluation coordinates, level 0 backwards (eval_levels.cuh).
+template <int m, int L, int LR>
+static dkss_status run_eval_levels(dkss_plan_s* pl, LevelParams lp, cudaStream_t st) {
+    using G = Geo<m, L>;
+    const Mod<L> md = make_mod<L>(pl);
+    const ModRR<LR> mr = make_modrr<LR>(pl);
+    const unsigned cols = (unsigned)(pl->P2 / G::TWO_M);
+    const unsigned slices = (unsigned)(m / kEvalKC);
+    {
+        ProfScope ps(pl, st, kProfFwdTwiddle);
+        for (uint32_t d = 0; d < pl->col_levels; ++d) {
+            level_geometry(pl, d, &lp.len, &lp.bp);
+            if (d == 0) {
+                k_level0_fwd_eval<m, L, LR><<<dim3(cols, 2), kThreads, level_ntt_smem_bytes<m, L, LR>(), st>>>(lp, md, mr);
+            } else {
+                lp.tw_lvl = pl->d_evtw + pl->evtw_offs[d];
+                k_level_eval_fwd<m, L, LR><<<dim3(cols, slices, 2), kThreads, level_eval_smem_bytes<m, L, LR>(), st>>>(
+                    lp, mr);
+            }
+            DKSS_CHECK_LAUNCH();
+        }
+    }
+    lp.len = pl->r_last;
+    {
+        ProfScope ps(pl, st, kProfFinal);
+        const unsigned blocks = (unsigned)(pl->P2 / final_eval_elems<m>((int)pl->r_last));
+        k_final_eval<m, L, LR><<<dim3(blocks, slices), kThreads, final_eval_smem_bytes<m, L, LR>((int)pl->r_last), st>>>(
+            lp, mr);
+        DKSS_CHECK_LAUNCH();
+    }
+    ProfScope ps(pl, st, kProfInvTwiddle);
+    for (int d = (int)pl->col_levels - 1; d >= 0; --d) {
+        level_geometry(pl, (uint32_t)d, &lp.len, &lp.bp);
+        if (d == 0) {
+            k_level0_inv_eval<m, L, LR><<<cols, kThreads, level_ntt_smem_bytes<m, L, LR>(), st>>>(lp, md, mr);
+        } else {
+            lp.tw_lvl = pl->d_evtw + pl->evtw_offs[d];
+            k_level_eval_inv<m, L, LR><<<dim3(cols, slices), kThreads, level_eval_smem_bytes<m, L, LR>(), st>>>(lp, mr);
+        }
+        DKSS_CHECK_LAUNCH();
+    }
+    return DKSS_OK;
+}
+
 template <int m, int L, int LR>
 dkss_status run_mul(dkss_plan_s* pl, const uint64_t* a, const uint64_t* b, uint64_t* out, cudaStream_t st) {
     using G = Geo<m, L>;
@@ -234,7 +321,15 @@ dkss_status run_mul(dkss_plan_s* pl, const uint64_t* a, const uint64_t* b, uint6
     LevelParams lp = make_level(pl);
     lp.raw_a = a;
     lp.raw_b = b;
-    dkss_status s = launch_forward_levels<m, L, LR>(pl, lp, 2, st);
+    dkss_status s = DKSS_OK;
+    if constexpr (m <= 32) {
+        if (pl->eval_levels) {
+            s = run_eval_levels<m, L, LR>(pl, lp, st);
+            if (s != DKSS_OK) return s;
+            return launch_decode<m, L, LR>(pl, out, st);
+        }
+    }
+    s = launch_forward_levels<m, L, LR>(pl, lp, 2, st);
     if (s != DKSS_OK) return s;
     lp.len = pl->r_last;
     {
@@ -274,32 +369,7 @@ dkss_status run_mul(dkss_plan_s* pl, const uint64_t* a, const uint64_t* b, uint6
         k_dft_inv<m, L><<<(unsigned)(pl->P2 / G::TWO_M), kThreads, column_smem_bytes<m, L>(), st>>>(lp, md);
         DKSS_CHECK_LAUNCH();
     }
-    DecodeParams dp{};
-    dp.c = pl->d_work;
-    dp.out = reinterpret_cast<uint32_t*>(out);
-    dp.agg = pl->d_agg;
-    dp.status = pl->d_status;
-    dp.P2 = pl->P2;
-    dp.n_windows = 4 * ((pl->n_bits + 63) / 64);
-    dp.n_tiles = pl->n_tiles;
-    dp.k_max = pl->P2 * (m / 2) + m / 2;
-    dp.m = m;
-    dp.h = m / 2;
-    dp.u = pl->u;
-    dp.db = 0;
-    for (dkss_host::u128 t = pl->q; t; t >>= 1) dp.db++;
-    dp.db += 1;
-    dp.out_aligned16 = ((uintptr_t)out & 15) == 0;
-    ProfScope ps(pl, st, kProfDecode);
-    if (pl->u == 32) k_decode_tiles_aligned<L, 1><<<(unsigned)pl->n_tiles, kDecThreads, 0, st>>>(dp);
-    else if (pl->u == 16) k_decode_tiles_aligned<L, 2><<<(unsigned)pl->n_tiles, kDecThreads, 0, st>>>(dp);
-    else k_decode_tiles<L><<<(unsigned)pl->n_tiles, kDecThreads, 0, st>>>(dp);
-    DKSS_CHECK_LAUNCH();
-    k_decode_scan<<<1, kScanThreads, 0, st>>>(dp);
-    DKSS_CHECK_LAUNCH();
-    k_decode_fix<<<(unsigned)((pl->n_tiles + 255) / 256), 256, 0, st>>>(dp);
-    DKSS_CHECK_LAUNCH();
-    return DKSS_OK;
+    return launch_decode<m, L, LR>(pl, out, st);
 }
 
 template <int m, int L, int LR>

@@ -259,6 +259,25 @@ bool ntt_lazy_bounds(uint32_t m, uint32_t LR, u128 q, NttBiases* out) {
         }
     }
     X = Xf;
+    // DFTs of length <= 2m in evaluation coordinates (eval_levels.cuh): inputs below
+    // 2q normalised, Cooley-Tukey butterflies t = b w (the first stage t = b), lo + t,
+    // lo + BE - t for log2(2m) stages; then a product by a canonical constant, or a
+    // by b after b is scaled (the last level's componentwise products)
+    {
+        const Bnd E0 = t_need;   // below 2q, normalised
+        Bnd BE;
+        out->eval_ok = c.bias(E0, out->evl, &BE);
+        Bnd x = E0;
+        for (uint32_t s = 0; s <= lg && out->eval_ok; ++s) {
+            Bnd t = E0;
+            if (s > 0) out->eval_ok = c.mmul(x, C, &t) && c.below_2q(t);
+            x = c.add(x, BE);
+            out->eval_ok = out->eval_ok && c.limbs_ok(x);
+        }
+        Bnd r1, r2, r3;
+        out->eval_ok = out->eval_ok && c.mmul(x, C, &r1) && c.below_2q(r1) && c.mmul(x, r1, &r2) && c.below_2q(r2) &&
+                       c.mmul(r2, C, &r3);
+    }
     // componentwise: by a canonical twiddle, or a by b (b scaled first when a b would not fit)
     Bnd P_tw, P_fin;
     if (!c.mmul(X, C, &P_tw)) return false;

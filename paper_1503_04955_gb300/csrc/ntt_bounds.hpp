@@ -26,6 +26,8 @@ struct NttBiases {
     uint32_t neg[5];      // negated input coefficients: K p^z, limbs >= those of a canonical residue
     uint32_t bwd[7][5];   // backwards stage b: K_b p^z, limbs >= those of any stage input
     bool prescale;        // componentwise products scale one factor first (keeps the product in range)
+    uint32_t evl[5];      // DFTs in evaluation coordinates: K p^z, limbs >= those of any value below 2 p^z
+    bool eval_ok;         // the limits of those DFTs (log2(2m) lazy stages) hold
 };
 
 // true when the lazy transform of R = (Z/qZ)[alpha]/(alpha^m + 1) with LR

@@ -33,6 +33,9 @@ struct dkss_plan_s {
     int device = 0;
     uint32_t* d_table = nullptr;  // rho^s (s < mu_top): coefficients, or evaluations (default)
     uint32_t* d_ntt = nullptr;    // constants of the transform in R
+    bool eval_levels = false;     // inner levels in evaluation coordinates (eval_levels.cuh)
+    uint32_t* d_evtw = nullptr;   // their bad twiddles of levels d >= 1
+    std::vector<uint64_t> evtw_offs;  // word offset of level d's table in d_evtw
     uint32_t* d_work = nullptr;   // two transformed polynomials
     uint64_t poly_words = 0;
     uint32_t* d_agg = nullptr;    // carry-scan tile aggregates
@@ -56,6 +59,7 @@ dkss_status plan_host(dkss_plan_s* pl, uint64_t n_bits, uint64_t M, uint32_t m, 
 void build_table(const dkss_plan_s* pl, std::vector<uint32_t>& out);
 void build_eval_table(const dkss_plan_s* pl, std::vector<uint32_t>& out);
 void build_ntt_consts(const dkss_plan_s* pl, std::vector<uint32_t>& out);
+void build_eval_level_tables(const dkss_plan_s* pl, std::vector<uint32_t>& out, std::vector<uint64_t>& offs);
 }  // namespace dkss_planning
 
 namespace dkss {
