@@ -277,9 +277,9 @@ static dkss_status run_eval_levels(dkss_plan_s* pl, LevelParams lp, cudaStream_t
     const ModRR<LR> mr = make_modrr<LR>(pl);
     const unsigned cols = (unsigned)(pl->P2 / G::TWO_M);
     const unsigned slices = (unsigned)(m / kEvalKC);
-    {
-        ProfScope ps(pl, st, kProfFwdTwiddle);
-        for (uint32_t d = 0; d < pl->col_levels; ++d) {
+    for (uint32_t d = 0; d < pl->col_levels; ++d) {
+        {
+            ProfScope ps(pl, st, kProfFwdTwiddle);
             level_geometry(pl, d, &lp.len, &lp.bp);
             if (d == 0) {
                 k_level0_fwd_eval<m, L, LR><<<dim3(cols, 2), kThreads, level_ntt_smem_bytes<m, L, LR>(), st>>>(lp, md, mr);
@@ -299,8 +299,8 @@ static dkss_status run_eval_levels(dkss_plan_s* pl, LevelParams lp, cudaStream_t
             lp, mr);
         DKSS_CHECK_LAUNCH();
     }
-    ProfScope ps(pl, st, kProfInvTwiddle);
     for (int d = (int)pl->col_levels - 1; d >= 0; --d) {
+        ProfScope ps(pl, st, kProfInvTwiddle);
         level_geometry(pl, (uint32_t)d, &lp.len, &lp.bp);
         if (d == 0) {
             k_level0_inv_eval<m, L, LR><<<cols, kThreads, level_ntt_smem_bytes<m, L, LR>(), st>>>(lp, md, mr);
