@@ -48,7 +48,7 @@ SM_MAX_MHZ = 2070.0
 HBM_GBS = 6782.1                  # measured copy bandwidth of the GB300s (MEASURED_PEAKS.json)
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture
 # (profiles/stage_kernels_dkss_2p24b.md); valid only for the kernel version captured.
-FORM_FLAGS = {"eval": 0, "ntt": 128, "direct": 16}   # binding.LEVELS_COEF, binding.RMUL_DIRECT
+FORM_FLAGS = {"ntt": 0, "eval": 128, "direct": 16}   # binding.LEVELS_EVAL, binding.RMUL_DIRECT
 NCU_TRAFFIC_BYTES = {("dkss_2p24b", "ntt", "fwd_twiddle"): 45.1e6, ("dkss_2p24b", "eval", "fwd_twiddle"): 44.4e6}
 
 
@@ -65,9 +65,9 @@ def parse_args():
     ap.add_argument("--batched-steps", type=int, default=10)
     ap.add_argument("--no-forms", action="store_true", help="skip the R-multiplication form comparison")
     ap.add_argument("--form-steps", type=int, default=20)
-    ap.add_argument("--form", default="eval", choices=["eval", "ntt", "direct"],
-                    help="inner levels in evaluation coordinates (eval, the default), every level on coefficients "
-                         "with R-multiplications through the evaluation map of R (ntt), or the direct convolution")
+    ap.add_argument("--form", default="ntt", choices=["ntt", "eval", "direct"],
+                    help="alpha-shift inner DFTs with R-multiplications through the evaluation map of R (ntt, the "
+                         "default), inner levels in evaluation coordinates (eval), or the direct convolution")
     return ap.parse_args()
 
 
@@ -376,7 +376,7 @@ def compare_forms(args, dev, flush, a, b, out, ms_main):
     cfg = syn.workload_params(args.workload)
     res = {}
     stream = torch.cuda.current_stream(dev)
-    for name, flags in (("eval", 0), ("ntt", binding.LEVELS_COEF), ("direct", binding.RMUL_DIRECT),
+    for name, flags in (("ntt", 0), ("eval", binding.LEVELS_EVAL), ("direct", binding.RMUL_DIRECT),
                         ("int8tc", binding.FORM_INT8TC)):
         if name == args.form:
             res[name] = {"ms_per_step": round(ms_main, 5)}

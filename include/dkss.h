@@ -55,12 +55,13 @@ enum {
     DKSS_DEBUG_CHECKS = 8, /* reserved: extra device-side range checks */
     DKSS_RMUL_DIRECT = 16, /* R-multiplications by the direct negacyclic convolution
                               (Section 2.9.2) instead of through the evaluation map of R */
-    DKSS_LEVELS_COEF = 128 /* every level's inner DFT by alpha-shifts on coefficients.  By
-                              default (m <= 32, NTT form) every radix-2m level but the
-                              first, and the last level, run in the evaluation coordinates
-                              of R (the CRT map of Section 3.2.3): their inner DFTs become m
-                              independent DFTs over Z/p^zZ and their bad twiddles pointwise
-                              products */
+    DKSS_LEVELS_EVAL = 128 /* every radix-2m level but the first, and the last level, in the
+                              evaluation coordinates of R (the CRT map of Section 3.2.3):
+                              their inner DFTs become m independent DFTs over Z/p^zZ with
+                              products instead of alpha-shifts, their bad twiddles pointwise
+                              products.  The same transform with fewer Montgomery products;
+                              NTT form and m <= 32 only, ignored otherwise.  By default every
+                              inner DFT is the thesis's alpha-shift DFT */
 };
 
 /*
@@ -73,12 +74,11 @@ enum {
  *           Z/p^zZ; p^z must exceed the largest product coefficient
  *           M*(m/2)*(2^u-1)^2 (Section 3.2.2); m*p^z < 2^127 (so that
  *           products in 26-bit limbs stay within 5 limbs).
- *   flags   0 (R-multiplications through the evaluation map of R on the
- *           integer pipe, inner levels in evaluation coordinates where m <= 32),
- *           DKSS_LEVELS_COEF (the same R-multiplications, every inner DFT by
- *           alpha-shifts), DKSS_RMUL_DIRECT (direct convolution, integer pipe)
- *           or DKSS_FORM_INT8TC (INT8 tensor cores; DKSS_EUNSUPPORTED if
- *           m < 32), optionally | DKSS_PROFILE.
+ *   flags   0 (inner DFTs by alpha-shifts, R-multiplications through the
+ *           evaluation map of R on the integer pipe), DKSS_LEVELS_EVAL (inner
+ *           levels in evaluation coordinates, m <= 32), DKSS_RMUL_DIRECT
+ *           (direct convolution, integer pipe) or DKSS_FORM_INT8TC (INT8 tensor
+ *           cores; DKSS_EUNSUPPORTED if m < 32), optionally | DKSS_PROFILE.
  * On the host it tests p (deterministic Miller-Rabin), finds the smallest
  * generator zeta of F_p^*, Hensel-lifts it to a (p-1)-th root of unity mod p^z,
  * forms omega = zeta_z^((p-1)/2M), gamma = omega^(2M/2m) and rho by Lagrange
@@ -184,13 +184,14 @@ dkss_status dkss_mul_batch(const dkss_job* jobs, size_t count, uint32_t flags, d
  * word, p^z high word, generator zeta, omega low, omega high, gamma low,
  * gamma high, LR (26-bit limbs of the product arithmetic), the form of the
  * R-multiplications (0 through the evaluation map, 1 direct convolution,
- * 2 INT8 tensor cores, 3 inner levels in evaluation coordinates (the default
- * where it applies);
+ * 2 INT8 tensor cores, 3 inner levels in evaluation coordinates
+ * (DKSS_LEVELS_EVAL);
  * a ring outside the evaluation-map form's limits on its unreduced sums gets
  * 1 unless the flags ask for 2), 1 when form 0 (every level on
  * coefficients) scales one factor of each componentwise product first (else
- * 0), and 1 when the ring allows the inner levels in evaluation coordinates
- * (else 0).
+ * 0), 1 when the ring allows the inner levels in evaluation coordinates
+ * (else 0), and the mask of the stages of their DFTs whose butterflies with
+ * twiddle 1 skip the product (bit s: stage s).
  */
 dkss_status dkss_plan_info(dkss_plan_t plan, uint64_t* consts, size_t n_consts, uint64_t* rho_out);
 

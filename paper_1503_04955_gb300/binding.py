@@ -27,7 +27,7 @@ EXPORTS = ["dkss_plan", "dkss_mul", "dkss_mul_host", "dkss_forward", "dkss_mul_b
            "dkss_batch_destroy", "dkss_plan_candidates", "dkss_mlp_forward", "dkss_mlp_grad", "dkss_mlp_adam"]
 FORM_PROFILE = 4
 RMUL_DIRECT = 16
-LEVELS_COEF = 128
+LEVELS_EVAL = 128
 PROFILE_KINDS = ["fwd_dft", "fwd_twiddle", "final_pointwise", "inv_twiddle", "inv_dft", "decode"]
 
 
@@ -103,10 +103,10 @@ def _words2_to_ints(arr):
     return [int(lo) | (int(hi) << 64) for lo, hi in zip(arr[0::2], arr[1::2])]
 
 
-N_CONSTS = 15
+N_CONSTS = 16
 CONST_NAMES = ["P2", "mu", "L", "levels", "pz_lo", "pz_hi", "zeta", "omega_lo", "omega_hi", "gamma_lo", "gamma_hi",
-               "LR", "rmul", "prescale", "eval_ok"]
-RMUL_FORMS = ("ntt", "direct", "int8tc", "eval")     # consts["rmul"] indexes this ("eval": default, m <= 32)
+               "LR", "rmul", "prescale", "eval_ok", "eval_skip"]
+RMUL_FORMS = ("ntt", "direct", "int8tc", "eval")     # consts["rmul"] indexes this
 
 
 def _consts_dict(c):

@@ -188,8 +188,8 @@ dkss_status plan_host(dkss_plan_s* pl, uint64_t n_bits, uint64_t M, uint32_t m, 
     for (uint32_t i = 0; i < 5; ++i) pl->kscale[i] = i < LR ? (uint32_t)(ks >> (26 * i)) & ((1u << 26) - 1) : 0;
     // limits of the lazy transform in R (NTT form of the R-multiplications)
     pl->ntt_ok = ntt_lazy_bounds(m, LR, q, &pl->ntt_bias);
-    pl->eval_levels = !(pl->flags & (DKSS_RMUL_DIRECT | DKSS_FORM_INT8TC | DKSS_LEVELS_COEF)) && m <= 32 &&
-                      pl->ntt_ok && pl->ntt_bias.eval_ok;
+    pl->eval_levels = (pl->flags & DKSS_LEVELS_EVAL) && !(pl->flags & (DKSS_RMUL_DIRECT | DKSS_FORM_INT8TC)) &&
+                      m <= 32 && pl->ntt_ok && pl->ntt_bias.eval_ok;
     return DKSS_OK;
 }
 
@@ -240,7 +240,7 @@ void build_ntt_consts(const dkss_plan_s* pl, std::vector<uint32_t>& out) {
     uint32_t lg = 0;
     while ((1u << lg) < m) ++lg;
     // layout of NttLayout<m> (ntt_rmul.cuh)
-    const uint32_t Q = 2 * m + lg + 2, COUNT = Q + 8 + 2 * m;
+    const uint32_t Q = 2 * m + lg + 2, PSI = Q + 7 + lg + 1, COUNT = PSI + 2 * m + 1;
     out.assign((size_t)COUNT * LR, 0);
     MontCtx c(pl->q);
     const u128 rdev = pow2_mod(26 * (int)LR, pl->q);
@@ -272,13 +272,15 @@ void build_ntt_consts(const dkss_plan_s* pl, std::vector<uint32_t>& out) {
     // last backwards stage after a prescaled componentwise product: 1 and psi^-1
     put_rr(&out[(size_t)(Q + 5) * LR], rdev, LR);
     put_rr(&out[(size_t)(Q + 6) * LR], to_dev(c, zlast, rdev), LR);
-    // DFTs in evaluation coordinates: their bias and the powers psi^t, t < 2m
-    for (uint32_t i = 0; i < LR; ++i) out[(size_t)(Q + 7) * LR + i] = pl->ntt_bias.evl[i];
+    // DFTs in evaluation coordinates: their stage biases and the powers psi^t, t < 2m
+    for (uint32_t st = 0; st <= lg; ++st)
+        for (uint32_t i = 0; i < LR; ++i) out[(size_t)(Q + 7 + st) * LR + i] = pl->ntt_bias.evl[st][i];
     u128 pt = c.to(1);
     for (uint32_t t = 0; t < 2 * m; ++t) {
-        put_rr(&out[(size_t)(Q + 8 + t) * LR], to_dev(c, pt, rdev), LR);
+        put_rr(&out[(size_t)(PSI + t) * LR], to_dev(c, pt, rdev), LR);
         pt = c.mul(pt, psi);
     }
+    put_rr(&out[(size_t)(PSI + 2 * m) * LR], to_dev(c, p2inv, rdev), LR);   // (2M)^-1 R'
 }
 
 // Bad twiddles of levels d >= 1 in evaluation coordinates (eval_levels.cuh):
@@ -391,13 +393,13 @@ void fill_consts(const dkss_plan_s* pl, uint64_t* consts, size_t n) {
                           : ((pl->flags & DKSS_RMUL_DIRECT) || !pl->ntt_ok)         ? 1
                           : pl->eval_levels                                          ? 3
                                                                                      : 0;
-    uint64_t v[15] = {pl->P2, pl->mu_top, pl->L, (uint64_t)pl->col_levels + 1, (uint64_t)pl->q,
+    uint64_t v[16] = {pl->P2, pl->mu_top, pl->L, (uint64_t)pl->col_levels + 1, (uint64_t)pl->q,
                       (uint64_t)(pl->q >> 64), pl->roots.zeta, (uint64_t)pl->roots.omega,
                       (uint64_t)(pl->roots.omega >> 64), (uint64_t)pl->roots.gamma,
                       (uint64_t)(pl->roots.gamma >> 64), pl->LR, form,
                       (uint64_t)(pl->ntt_ok && pl->ntt_bias.prescale),
-                      (uint64_t)(pl->ntt_ok && pl->ntt_bias.eval_ok && pl->m <= 32)};
-    for (size_t i = 0; i < n && i < 15; ++i) consts[i] = v[i];
+                      (uint64_t)(pl->ntt_ok && pl->ntt_bias.eval_ok && pl->m <= 32), pl->ntt_bias.eval_skip};
+    for (size_t i = 0; i < n && i < 16; ++i) consts[i] = v[i];
 }
 
 }  // namespace

@@ -66,6 +66,8 @@ struct LevelParams {
     uint32_t i8_S;               // bytes per residue (INT8 tensor-core form)
     uint32_t ntt_prescale;       // NTT form: scale b before the componentwise product
     const uint32_t* tw_lvl;      // inner levels in evaluation coordinates: this level's twiddles
+    uint32_t eval_skip;          // their DFTs: bit s = stage s adds t = b unreduced where the twiddle is 1
+    uint32_t eval_noscale;       // last level: multiply a b unscaled, scale by (2M)^-1 at the end
 };
 
 // How R-multiplications are computed.

@@ -1,5 +1,5 @@
-// Levels of the transform in the evaluation coordinates of R (the default for
-// m <= 32; DKSS_LEVELS_COEF keeps every level on coefficients).
+// Levels of the transform in the evaluation coordinates of R (DKSS_LEVELS_EVAL;
+// by default every level runs on coefficients with alpha-shift inner DFTs).
 //
 // The map x -> (x(gamma^(2j+1)))_j, j < m, is a ring isomorphism R -> P^m
 // (P = Z/p^zZ; the thesis builds rho through it, Section 3.2.3).  Under it
@@ -26,37 +26,46 @@
 
 namespace dkss {
 
-constexpr int kEvalKC = 16;   // coordinates per CTA of the evaluation-coordinate DFT kernels
+// coordinates per CTA of the evaluation-coordinate DFT kernels: a whole element
+// for m <= 32 (contiguous loads and stores of m residues)
+template <int m>
+struct EvalKC {
+    static constexpr int value = m < 32 ? m : 32;
+};
 
 // Radix-2 DIT over `arrays` consecutive arrays of n elements, each element
-// kEvalKC coordinates of LR words: residue (array a, slot s, coordinate c) at
-// buf + ((a n + s) kEvalKC + c) LR.  Input in bit-reversed slots, output in
+// KC = EvalKC<m> coordinates of LR words: residue (array a, slot s, coordinate c) at
+// buf + ((a n + s) KC + c) LR.  Input in bit-reversed slots, output in
 // natural slots.  Coordinate c is storage index i0 + c of the element, whose
 // root is gamma^((2 brv(i) + 1) rexp) (rexp: exponent of alpha of the DFT's
-// root).  Butterflies (t = b w; a + t; a + BE - t) are lazy; the first stage's
-// twiddle is 1.
+// root).  Butterflies (t = b w; a + t; a + B_s - t) are lazy; where the
+// twiddle is 1 (k = 0) and bit s of `skip` is set, t = b without a product (the
+// plan admits a stage only where its bounds allow).  Butterflies are dealt so
+// that the two of a warp share k, which keeps those warps uniform.
 template <int m, int LR>
-__device__ void eval_dit(uint32_t* buf, int arrays, int n, int rexp, int i0, const uint32_t* cst,
+__device__ void eval_dit(uint32_t* buf, int arrays, int n, int rexp, int i0, const uint32_t* cst, uint32_t skip,
                          const ModRR<LR>& md) {
+    constexpr int KC = EvalKC<m>::value;
     using NL = NttLayout<m>;
-    uint32_t be[LR];
-    ldg_rr<LR>(be, cst + NL::EVB * LR);
     const int log2n = 31 - __clz(n);
-    const int tasks = arrays * (n / 2) * kEvalKC;
+    const int tasks = arrays * (n / 2) * KC;
     for (int lh = 0; lh < log2n; ++lh) {
         const int half = 1 << lh;
         const int scale = n >> (lh + 1);
+        const int lg_groups = log2n - lh - 1;       // blocks of 2 half slots: n >> (lh + 1)
+        uint32_t bs[LR];
+        ldg_rr<LR>(bs, cst + (NL::EVB + lh) * LR);
         for (int task = threadIdx.x; task < tasks; task += kThreads) {
-            const int c = task % kEvalKC, rest = task / kEvalKC;
-            const int arr = rest >> (log2n - 1), bf = rest & (n / 2 - 1);
-            const int k_in = bf & (half - 1);
-            const int ia = ((bf >> lh) << (lh + 1)) + k_in, ib = ia + half;
-            uint32_t* pa = buf + ((arr * n + ia) * kEvalKC + c) * LR;
-            uint32_t* pb = buf + ((arr * n + ib) * kEvalKC + c) * LR;
+            const int c = task % KC, rest = task / KC;
+            const int arr = rest >> (log2n - 1), idx = rest & (n / 2 - 1);
+            const int g = idx & ((1 << lg_groups) - 1), k_in = idx >> lg_groups;
+            const int ia = g * 2 * half + k_in, ib = ia + half;
+            uint32_t* pa = buf + ((arr * n + ia) * KC + c) * LR;
+            uint32_t* pb = buf + ((arr * n + ib) * KC + c) * LR;
             uint32_t a[LR], b[LR], t[LR];
             ld_rr<LR>(a, pa);
             ld_rr<LR>(b, pb);
-            if (lh == 0) {
+            if (k_in == 0 && ((skip >> lh) & 1)) {
 #pragma unroll
                 for (int w = 0; w < LR; ++w) t[w] = b[w];
             } else {
@@ -68,7 +77,7 @@ __device__ void eval_dit(uint32_t* buf, int arrays, int n, int rexp, int i0, con
             }
             uint32_t s0[LR], s1[LR];
             lz_add<LR>(s0, a, t);
-            lz_sub<LR>(s1, a, be, t);
+            lz_sub<LR>(s1, a, bs, t);
             st_rr<LR>(pa, s0);
             st_rr<LR>(pb, s1);
         }
@@ -139,34 +148,35 @@ __global__ void __launch_bounds__(kThreads, 4) k_level0_fwd_eval(LevelParams prm
 
 // ---------------------------------------------------------------------------
 // Level d >= 1 forward in evaluation coordinates: one CTA per (column,
-// kEvalKC coordinates): 2m-point DFTs over P, then the pointwise twiddles
+// KC coordinates): 2m-point DFTs over P, then the pointwise twiddles
 // omega^(v l b_d (2j+1)) from the level's table (prm.tw_lvl).
 // ---------------------------------------------------------------------------
 template <int m, int L, int LR>
 __global__ void __launch_bounds__(kThreads) k_level_eval_fwd(LevelParams prm, ModRR<LR> mr) {
+    constexpr int KC = EvalKC<m>::value;
     using G = Geo<m, L>;
     extern __shared__ __align__(16) uint32_t smem[];
     constexpr int LOG2_TWO_M = ilog2<G::TWO_M>();
     const uint64_t column = blockIdx.x;
-    const int i0 = blockIdx.y * kEvalKC;
+    const int i0 = blockIdx.y * KC;
     uint32_t* poly = prm.data + (blockIdx.z ? prm.poly_words : 0);
     const int lg_mu = (__ffsll((long long)prm.len) - 1) - LOG2_TWO_M;
     const uint64_t mu_d = 1ull << lg_mu;
     const uint64_t blk = column >> lg_mu, l = column & (mu_d - 1);
     const uint64_t base = blk * prm.len;
-    for (int idx = threadIdx.x; idx < G::TWO_M * kEvalKC; idx += kThreads) {
-        const int j = idx / kEvalKC, c = idx % kEvalKC;
+    for (int idx = threadIdx.x; idx < G::TWO_M * KC; idx += kThreads) {
+        const int j = idx / KC, c = idx % KC;
         uint32_t x[L], y[LR];
         ld_res<L>(x, poly + (base + (uint64_t)j * mu_d + l) * G::EW + (i0 + c) * L);
         to_rr<L, LR>(y, x);
-        st_rr<LR>(smem + ((int)bitrev(j, LOG2_TWO_M) * kEvalKC + c) * LR, y);
+        st_rr<LR>(smem + ((int)bitrev(j, LOG2_TWO_M) * KC + c) * LR, y);
     }
     __syncthreads();
-    eval_dit<m, LR>(smem, 1, G::TWO_M, 1, i0, prm.ntt_cst, mr);
-    for (int idx = threadIdx.x; idx < G::TWO_M * kEvalKC; idx += kThreads) {
-        const int v = idx / kEvalKC, c = idx % kEvalKC;
+    eval_dit<m, LR>(smem, 1, G::TWO_M, 1, i0, prm.ntt_cst, prm.eval_skip, mr);
+    for (int idx = threadIdx.x; idx < G::TWO_M * KC; idx += kThreads) {
+        const int v = idx / KC, c = idx % KC;
         uint32_t x[LR], t[LR];
-        ld_rr<LR>(x, smem + (v * kEvalKC + c) * LR);
+        ld_rr<LR>(x, smem + (v * KC + c) * LR);
         ldg_rr<LR>(t, prm.tw_lvl + ((uint64_t)v * l * m + i0 + c) * LR);
         mmul<LR>(x, x, t, mr);
         store_canon<L, LR>(poly + (base + (uint64_t)v * mu_d + l) * G::EW + (i0 + c) * L, x, mr);
@@ -179,36 +189,37 @@ __global__ void __launch_bounds__(kThreads) k_level_eval_fwd(LevelParams prm, Mo
 // ---------------------------------------------------------------------------
 template <int m, int L, int LR>
 __global__ void __launch_bounds__(kThreads) k_level_eval_inv(LevelParams prm, ModRR<LR> mr) {
+    constexpr int KC = EvalKC<m>::value;
     using G = Geo<m, L>;
     using NL = NttLayout<m>;
     extern __shared__ __align__(16) uint32_t smem[];
     constexpr int LOG2_TWO_M = ilog2<G::TWO_M>();
     const uint64_t column = blockIdx.x;
-    const int i0 = blockIdx.y * kEvalKC;
+    const int i0 = blockIdx.y * KC;
     uint32_t* poly = prm.data;
     const int lg_mu = (__ffsll((long long)prm.len) - 1) - LOG2_TWO_M;
     const uint64_t mu_d = 1ull << lg_mu;
     const uint64_t blk = column >> lg_mu, l = column & (mu_d - 1);
     const uint64_t base = blk * prm.len;
     const uint64_t n_tw = prm.P2 / prm.bp;             // entries of the level's table
-    for (int idx = threadIdx.x; idx < G::TWO_M * kEvalKC; idx += kThreads) {
-        const int j = idx / kEvalKC, c = idx % kEvalKC;
+    for (int idx = threadIdx.x; idx < G::TWO_M * KC; idx += kThreads) {
+        const int j = idx / KC, c = idx % KC;
         uint32_t x[L], y[LR], t[LR];
         ld_res<L>(x, poly + (base + (uint64_t)j * mu_d + l) * G::EW + (i0 + c) * L);
         to_rr<L, LR>(y, x);
         const uint64_t e = (n_tw - (uint64_t)j * l) & (n_tw - 1);
         ldg_rr<LR>(t, prm.tw_lvl + (e * m + i0 + c) * LR);
         mmul<LR>(y, y, t, mr);
-        st_rr<LR>(smem + ((int)bitrev(j, LOG2_TWO_M) * kEvalKC + c) * LR, y);
+        st_rr<LR>(smem + ((int)bitrev(j, LOG2_TWO_M) * KC + c) * LR, y);
     }
     __syncthreads();
-    eval_dit<m, LR>(smem, 1, G::TWO_M, G::TWO_M - 1, i0, prm.ntt_cst, mr);
+    eval_dit<m, LR>(smem, 1, G::TWO_M, G::TWO_M - 1, i0, prm.ntt_cst, prm.eval_skip, mr);
     uint32_t one[LR];
     ldg_rr<LR>(one, prm.ntt_cst + NL::ONE * LR);
-    for (int idx = threadIdx.x; idx < G::TWO_M * kEvalKC; idx += kThreads) {
-        const int v = idx / kEvalKC, c = idx % kEvalKC;
+    for (int idx = threadIdx.x; idx < G::TWO_M * KC; idx += kThreads) {
+        const int v = idx / KC, c = idx % KC;
         uint32_t x[LR];
-        ld_rr<LR>(x, smem + (v * kEvalKC + c) * LR);
+        ld_rr<LR>(x, smem + (v * KC + c) * LR);
         mmul<LR>(x, x, one, mr);
         store_canon<L, LR>(poly + (base + (uint64_t)v * mu_d + l) * G::EW + (i0 + c) * L, x, mr);
     }
@@ -223,59 +234,63 @@ __host__ __device__ constexpr int final_eval_elems(int n) {
 // ---------------------------------------------------------------------------
 // Last level in evaluation coordinates: n-point DFTs over P (root
 // gamma^((2j+1) 2m/n)) of a and b, componentwise products scaled by (2M)^-1,
-// inverse DFTs; one CTA per (final_eval_elems elements, kEvalKC coordinates).
-// smem: A, B and C, final_eval_elems x kEvalKC residues each.
+// inverse DFTs; one CTA per (final_eval_elems elements, KC coordinates).
+// smem: A, B and C, final_eval_elems x KC residues each.
 // ---------------------------------------------------------------------------
 template <int m, int L, int LR>
 __global__ void __launch_bounds__(kThreads) k_final_eval(LevelParams prm, ModRR<LR> mr) {
+    constexpr int KC = EvalKC<m>::value;
     using G = Geo<m, L>;
     using NL = NttLayout<m>;
     extern __shared__ __align__(16) uint32_t smem[];
     const int n = (int)prm.len;
     const int log2n = 31 - __clz(n);
     const int nn = final_eval_elems<m>(n);
-    const int i0 = blockIdx.y * kEvalKC;
+    const int i0 = blockIdx.y * KC;
     const uint64_t base = (uint64_t)blockIdx.x * nn;
     uint32_t* sa = smem;
-    uint32_t* sb = sa + nn * kEvalKC * LR;
-    uint32_t* sc = sb + nn * kEvalKC * LR;
+    uint32_t* sb = sa + nn * KC * LR;
+    uint32_t* sc = sb + nn * KC * LR;
     uint32_t* pa = prm.data;
     uint32_t* pb = prm.data + prm.poly_words;
-    for (int idx = threadIdx.x; idx < nn * kEvalKC; idx += kThreads) {
-        const int j = idx / kEvalKC, c = idx % kEvalKC;
+    for (int idx = threadIdx.x; idx < nn * KC; idx += kThreads) {
+        const int j = idx / KC, c = idx % KC;
         const int slot = ((j >> log2n) << log2n) + (int)bitrev(j & (n - 1), log2n);
         uint32_t x[L], y[LR];
         ld_res<L>(x, pa + (base + j) * G::EW + (i0 + c) * L);
         to_rr<L, LR>(y, x);
-        st_rr<LR>(sa + (slot * kEvalKC + c) * LR, y);
+        st_rr<LR>(sa + (slot * KC + c) * LR, y);
         ld_res<L>(x, pb + (base + j) * G::EW + (i0 + c) * L);
         to_rr<L, LR>(y, x);
-        st_rr<LR>(sb + (slot * kEvalKC + c) * LR, y);
+        st_rr<LR>(sb + (slot * KC + c) * LR, y);
     }
     __syncthreads();
     const int rexp = G::TWO_M / n;
-    eval_dit<m, LR>(sa, 2 * (nn / n), n, rexp, i0, prm.ntt_cst, mr);   // a and b (sb follows sa)
+    eval_dit<m, LR>(sa, 2 * (nn / n), n, rexp, i0, prm.ntt_cst, prm.eval_skip, mr);   // a and b (sb follows sa)
+    // componentwise products a b (2M)^-1: b scaled first, or, where the plan's
+    // bounds allow, a b unscaled and (2M)^-1 taken by the final reduction
     uint32_t ks[LR];
 #pragma unroll
     for (int w = 0; w < LR; ++w) ks[w] = prm.kscale[w];      // (2M)^-1 R'^2
-    for (int idx = threadIdx.x; idx < nn * kEvalKC; idx += kThreads) {
-        const int v = idx / kEvalKC, c = idx % kEvalKC;
+    const bool noscale = prm.eval_noscale != 0;
+    for (int idx = threadIdx.x; idx < nn * KC; idx += kThreads) {
+        const int v = idx / KC, c = idx % KC;
         uint32_t x[LR], y[LR];
-        ld_rr<LR>(x, sa + (v * kEvalKC + c) * LR);
-        ld_rr<LR>(y, sb + (v * kEvalKC + c) * LR);
-        mmul<LR>(y, y, ks, mr);                               // b (2M)^-1 R'
-        mmul<LR>(x, x, y, mr);                                // a b (2M)^-1
+        ld_rr<LR>(x, sa + (v * KC + c) * LR);
+        ld_rr<LR>(y, sb + (v * KC + c) * LR);
+        if (!noscale) mmul<LR>(y, y, ks, mr);                 // b (2M)^-1 R'
+        mmul<LR>(x, x, y, mr);
         const int slot = ((v >> log2n) << log2n) + (int)bitrev(v & (n - 1), log2n);
-        st_rr<LR>(sc + (slot * kEvalKC + c) * LR, x);
+        st_rr<LR>(sc + (slot * KC + c) * LR, x);
     }
     __syncthreads();
-    eval_dit<m, LR>(sc, nn / n, n, (G::TWO_M - rexp) & (G::TWO_M - 1), i0, prm.ntt_cst, mr);
+    eval_dit<m, LR>(sc, nn / n, n, (G::TWO_M - rexp) & (G::TWO_M - 1), i0, prm.ntt_cst, prm.eval_skip, mr);
     uint32_t one[LR];
-    ldg_rr<LR>(one, prm.ntt_cst + NL::ONE * LR);
-    for (int idx = threadIdx.x; idx < nn * kEvalKC; idx += kThreads) {
-        const int v = idx / kEvalKC, c = idx % kEvalKC;
+    ldg_rr<LR>(one, prm.ntt_cst + (noscale ? NL::P2I : NL::ONE) * LR);
+    for (int idx = threadIdx.x; idx < nn * KC; idx += kThreads) {
+        const int v = idx / KC, c = idx % KC;
         uint32_t x[LR];
-        ld_rr<LR>(x, sc + (v * kEvalKC + c) * LR);
+        ld_rr<LR>(x, sc + (v * KC + c) * LR);
         mmul<LR>(x, x, one, mr);
         store_canon<L, LR>(pa + (base + v) * G::EW + (i0 + c) * L, x, mr);
     }
@@ -358,12 +373,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_level0_inv_eval(LevelParams prm
 
 template <int m, int L, int LR>
 constexpr size_t level_eval_smem_bytes() {
-    return sizeof(uint32_t) * (size_t)Geo<m, L>::TWO_M * kEvalKC * LR;
+    return sizeof(uint32_t) * (size_t)Geo<m, L>::TWO_M * EvalKC<m>::value * LR;
 }
 
 template <int m, int L, int LR>
 size_t final_eval_smem_bytes(int n) {
-    return sizeof(uint32_t) * 3 * (size_t)final_eval_elems<m>(n) * kEvalKC * LR;
+    return sizeof(uint32_t) * 3 * (size_t)final_eval_elems<m>(n) * EvalKC<m>::value * LR;
 }
 
 }  // namespace dkss

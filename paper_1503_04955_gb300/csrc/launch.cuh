@@ -42,6 +42,12 @@ static LevelParams make_level(const dkss_plan_s* pl) {
     lp.ntt_cst = pl->d_ntt;
     lp.i8_S = pl->i8_S;
     lp.ntt_prescale = pl->ntt_bias.prescale ? 1u : 0u;
+    lp.eval_skip = pl->ntt_bias.eval_skip;
+    {
+        uint32_t k = 0;
+        while ((1ull << k) < pl->r_last) ++k;
+        lp.eval_noscale = (pl->ntt_bias.eval_noscale >> k) & 1;
+    }
     return lp;
 }
 
@@ -276,7 +282,7 @@ static dkss_status run_eval_levels(dkss_plan_s* pl, LevelParams lp, cudaStream_t
     const Mod<L> md = make_mod<L>(pl);
     const ModRR<LR> mr = make_modrr<LR>(pl);
     const unsigned cols = (unsigned)(pl->P2 / G::TWO_M);
-    const unsigned slices = (unsigned)(m / kEvalKC);
+    const unsigned slices = (unsigned)(m / EvalKC<m>::value);
     for (uint32_t d = 0; d < pl->col_levels; ++d) {
         {
             ProfScope ps(pl, st, kProfFwdTwiddle);

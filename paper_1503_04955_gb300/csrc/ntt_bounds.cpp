@@ -263,20 +263,42 @@ bool ntt_lazy_bounds(uint32_t m, uint32_t LR, u128 q, NttBiases* out) {
     // 2q normalised, Cooley-Tukey butterflies t = b w (the first stage t = b), lo + t,
     // lo + BE - t for log2(2m) stages; then a product by a canonical constant, or a
     // by b after b is scaled (the last level's componentwise products)
-    {
+    // Butterflies whose twiddle is 1 may take t = b unreduced (stage s with bit
+    // s of eval_skip; always at stage 0, whose inputs are reduced), and then
+    // stage s's bias covers the stage's inputs too.  Stages are admitted
+    // greedily while the whole DFT stays within the limits.
+    auto eval_dft = [&](uint32_t skip, NttBiases* o, Bnd* xout) {
         const Bnd E0 = t_need;   // below 2q, normalised
-        Bnd BE;
-        out->eval_ok = c.bias(E0, out->evl, &BE);
         Bnd x = E0;
-        for (uint32_t s = 0; s <= lg && out->eval_ok; ++s) {
-            Bnd t = E0;
-            if (s > 0) out->eval_ok = c.mmul(x, C, &t) && c.below_2q(t);
-            x = c.add(x, BE);
-            out->eval_ok = out->eval_ok && c.limbs_ok(x);
+        if (lg + 1 > 8) return false;
+        o->eval_noscale = 0;
+        for (uint32_t s = 0; s <= lg; ++s) {
+            Bnd t;
+            if (!c.mmul(x, C, &t) || !c.below_2q(t)) return false;
+            const Bnd need = (skip >> s) & 1 ? c.max(t, x) : t;
+            Bnd B;
+            if (!c.bias(need, o->evl[s], &B)) return false;
+            x = c.add(x, B);
+            if (!c.limbs_ok(x)) return false;
+            Bnd ab;   // after 2^(s+1)-point DFTs: a b without scaling b first
+            if (c.mmul(x, x, &ab) && c.below_2q(ab)) o->eval_noscale |= 1u << (s + 1);
         }
         Bnd r1, r2, r3;
-        out->eval_ok = out->eval_ok && c.mmul(x, C, &r1) && c.below_2q(r1) && c.mmul(x, r1, &r2) && c.below_2q(r2) &&
-                       c.mmul(r2, C, &r3);
+        if (!(c.mmul(x, C, &r1) && c.below_2q(r1) && c.mmul(x, r1, &r2) && c.below_2q(r2) && c.mmul(r2, C, &r3)))
+            return false;
+        *xout = x;
+        return true;
+    };
+    {
+        Bnd xe;
+        uint32_t skip = 1;
+        out->eval_ok = eval_dft(skip, out, &xe);
+        for (uint32_t s = 1; s <= lg && out->eval_ok; ++s) {
+            NttBiases trial = *out;
+            if (eval_dft(skip | (1u << s), &trial, &xe)) skip |= 1u << s;
+        }
+        if (out->eval_ok) out->eval_ok = eval_dft(skip, out, &xe);
+        out->eval_skip = skip;
     }
     // componentwise: by a canonical twiddle, or a by b (b scaled first when a b would not fit)
     Bnd P_tw, P_fin;

@@ -26,7 +26,10 @@ struct NttBiases {
     uint32_t neg[5];      // negated input coefficients: K p^z, limbs >= those of a canonical residue
     uint32_t bwd[7][5];   // backwards stage b: K_b p^z, limbs >= those of any stage input
     bool prescale;        // componentwise products scale one factor first (keeps the product in range)
-    uint32_t evl[5];      // DFTs in evaluation coordinates: K p^z, limbs >= those of any value below 2 p^z
+    uint32_t evl[8][5];   // DFTs in evaluation coordinates, stage s: K_s p^z, limbs >= those of t
+    uint32_t eval_skip;   // bit s: stage s takes t = b unreduced where its twiddle is 1
+    uint32_t eval_noscale;  // bit k: after 2^k-point DFTs the product of two lazy factors
+                            // fits, so the last level scales at its final reduction instead
     bool eval_ok;         // the limits of those DFTs (log2(2m) lazy stages) hold
 };
 

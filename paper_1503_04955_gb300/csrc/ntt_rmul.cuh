@@ -51,9 +51,10 @@ struct NttLayout {
     static constexpr int PW_HI = Q + 4;     // psi^-1 m^-1 (2M)^-1 R'^2   two normal-form factors)
     static constexpr int ONE = Q + 5;       // R'                 (last backwards stage after a
     static constexpr int ZLAST = Q + 6;     // psi^-1 R'           prescaled componentwise product)
-    static constexpr int EVB = Q + 7;       // bias of the DFTs in evaluation coordinates
-    static constexpr int PSI = Q + 8;       // psi^t R', t in [0, 2m)
-    static constexpr int COUNT = PSI + 2 * m;
+    static constexpr int EVB = Q + 7;       // biases of the DFTs in evaluation coordinates, LG + 1 stages
+    static constexpr int PSI = EVB + LG + 1;  // psi^t R', t in [0, 2m)
+    static constexpr int P2I = PSI + 2 * m;   // (2M)^-1 R'
+    static constexpr int COUNT = P2I + 1;
 };
 
 template <int LR>

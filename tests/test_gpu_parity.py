@@ -49,9 +49,9 @@ def check_product(dk, oc, cfg, A, B, with_oracle=True, with_forward=True, flags=
     par = o.Params(*cfg).check()
     roots = o.compute_roots(par)
     with dk.Plan(*cfg, flags=flags) as plan:
-        # the default runs the inner levels in evaluation coordinates for m <= 32 and
-        # the evaluation-map form of the R-multiplications on every ring tested here
-        want = 2 if flags & 2 else 1 if flags & 16 else 0 if (flags & 128 or cfg[2] > 32) else 3
+        # the default runs the evaluation-map form of the R-multiplications on every
+        # ring tested here; levels in evaluation coordinates apply for m <= 32
+        want = 2 if flags & 2 else 1 if flags & 16 else 3 if (flags & 128 and cfg[2] <= 32) else 0
         assert plan.info()["rmul"] == want
         c = plan.mul(to_dev(A), to_dev(B))
         fwd = plan.forward(to_dev(A)) if with_forward else None
@@ -66,9 +66,9 @@ def check_product(dk, oc, cfg, A, B, with_oracle=True, with_forward=True, flags=
             assert residues(fwd_host) == residues(dumps["a_hat"])
 
 
-# inner levels in evaluation coordinates (default), every level on
-# coefficients with R-multiplications through the evaluation map of R
-# (DKSS_LEVELS_COEF), and the direct negacyclic convolution (DKSS_RMUL_DIRECT)
+# alpha-shift inner DFTs with R-multiplications through the evaluation map of
+# R (default), inner levels in evaluation coordinates (DKSS_LEVELS_EVAL), and
+# the direct negacyclic convolution (DKSS_RMUL_DIRECT)
 FORMS = [0, 128, 16]
 
 

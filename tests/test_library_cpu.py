@@ -104,15 +104,16 @@ def test_int8_form_needs_m_32(dk):
 
 def test_rings_take_the_evaluation_map_form(dk):
     """Every workload ring and every tested small ring stays within the lazy
-    transform's limits (else the plan falls back to the direct convolution):
-    m <= 32 runs its inner levels in evaluation coordinates (form 3), m = 64
-    every level on coefficients (form 0); the m = 16, p^z = 40961^3 ring is
-    one whose coefficient-level form prescales its componentwise products."""
+    transform's limits (else the plan falls back to the direct convolution),
+    and those with m <= 32 within the limits of the inner levels in
+    evaluation coordinates; the m = 16, p^z = 40961^3 ring is one whose
+    componentwise products are prescaled."""
     for cfg in [syn.workload_params(k) for k in syn.WORKLOADS] + GPU_SMALL:
         _, consts = dk.plan_rho(*cfg)
-        assert consts["rmul"] == (3 if cfg[2] <= 32 else 0), cfg
+        assert consts["rmul"] == 0, cfg
         assert consts["eval_ok"] == (1 if cfg[2] <= 32 else 0), cfg
+        assert consts["eval_skip"] & 1, cfg
     _, consts = dk.plan_rho(4096, 32, 16, 16, 40961, 3)
-    assert consts["rmul"] == 3 and consts["prescale"] == 1
+    assert consts["rmul"] == 0 and consts["prescale"] == 1
     _, consts = dk.plan_rho(*syn.workload_params("dkss_2p24b"))
     assert consts["prescale"] == 0
