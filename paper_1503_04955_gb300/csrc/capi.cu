@@ -240,7 +240,7 @@ void build_ntt_consts(const dkss_plan_s* pl, std::vector<uint32_t>& out) {
     uint32_t lg = 0;
     while ((1u << lg) < m) ++lg;
     // layout of NttLayout<m> (ntt_rmul.cuh)
-    const uint32_t Q = 2 * m + lg + 2, PSI = Q + 7 + lg + 1, COUNT = PSI + 2 * m + 1;
+    const uint32_t Q = 2 * m + lg + 2, PSI = Q + 7 + lg + 1, COUNT = PSI + 2 * m;
     out.assign((size_t)COUNT * LR, 0);
     MontCtx c(pl->q);
     const u128 rdev = pow2_mod(26 * (int)LR, pl->q);
@@ -280,7 +280,6 @@ void build_ntt_consts(const dkss_plan_s* pl, std::vector<uint32_t>& out) {
         put_rr(&out[(size_t)(PSI + t) * LR], to_dev(c, pt, rdev), LR);
         pt = c.mul(pt, psi);
     }
-    put_rr(&out[(size_t)(PSI + 2 * m) * LR], to_dev(c, p2inv, rdev), LR);   // (2M)^-1 R'
 }
 
 // Bad twiddles of levels d >= 1 in evaluation coordinates (eval_levels.cuh):

@@ -285,8 +285,14 @@ __global__ void __launch_bounds__(kThreads) k_final_eval(LevelParams prm, ModRR<
     }
     __syncthreads();
     eval_dit<m, LR>(sc, nn / n, n, (G::TWO_M - rexp) & (G::TWO_M - 1), i0, prm.ntt_cst, prm.eval_skip, mr);
+    // final reduction: by 1, or by (2M)^-1 R'^2 where the products were unscaled
+    // (a Montgomery product of two plain residues leaves a factor R'^-1)
     uint32_t one[LR];
-    ldg_rr<LR>(one, prm.ntt_cst + (noscale ? NL::P2I : NL::ONE) * LR);
+    ldg_rr<LR>(one, prm.ntt_cst + NL::ONE * LR);
+    if (noscale) {
+#pragma unroll
+        for (int w = 0; w < LR; ++w) one[w] = ks[w];
+    }
     for (int idx = threadIdx.x; idx < nn * KC; idx += kThreads) {
         const int v = idx / KC, c = idx % KC;
         uint32_t x[LR];

@@ -53,8 +53,7 @@ struct NttLayout {
     static constexpr int ZLAST = Q + 6;     // psi^-1 R'           prescaled componentwise product)
     static constexpr int EVB = Q + 7;       // biases of the DFTs in evaluation coordinates, LG + 1 stages
     static constexpr int PSI = EVB + LG + 1;  // psi^t R', t in [0, 2m)
-    static constexpr int P2I = PSI + 2 * m;   // (2M)^-1 R'
-    static constexpr int COUNT = P2I + 1;
+    static constexpr int COUNT = PSI + 2 * m;
 };
 
 template <int LR>
