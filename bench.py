@@ -77,6 +77,24 @@ def workload_config(name):
             "z": w["z"], "products_per_step": 1}
 
 
+def max_over_ranks(x, device, world):
+    """Largest x over the ranks: a job's time is its slowest rank's (replicas
+    only; no collective touches the data path)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gbit_s(bits_per_rank_step, world, ms_per_step):
+    """Whole-job operand Gbit/s: the operand bits all ranks multiplied in one
+    step over the slowest rank's step time."""
+    return bits_per_rank_step * world / (ms_per_step * 1e-3) / 1e9
+
+
 def dist_info():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -269,14 +287,10 @@ def run_ours(args):
     step_ms = [e0.elapsed_time(e1) for e0, e1 in events]
     prof = plan.profile_read()
     plan.sync_status()
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dev, world)
     ms_per_step = total_ms / args.steps
     bits_per_step = 2 * n_bits * world
-    value = bits_per_step / (ms_per_step * 1e-3) / 1e9
+    value = job_gbit_s(2 * n_bits, world, ms_per_step)
     ok = check_product(out.cpu().numpy().view(np.uint64), A, B)
 
     # end to end through dkss_mul_host from pinned host memory
@@ -290,9 +304,9 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         plan.mul_host(an, bn, cn)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dev, world)
     ok = ok and check_product(cn, A, B)
-    e2e_value = bits_per_step / e2e_s / 1e9
+    e2e_value = job_gbit_s(2 * n_bits, world, e2e_s * 1e3)
 
     # roofline of the kernel group with the most device time
     work = stage_work(info, cfg[2], args.form)
