@@ -334,13 +334,11 @@ dkss_status dkss_batch_plan(dkss_batch_t* out, const uint64_t* n_bits, size_t co
     // stage list and per-stage job offsets
     std::vector<std::pair<uint32_t, uint32_t>> st;
     for (uint32_t d = 0; d < max_levels; ++d) {
-        st.push_back({dkss::kStFwdDft, d});
-        st.push_back({dkss::kStFwdTwiddle, d});
+        st.push_back({dkss::kStFwdLevel, d});
     }
     st.push_back({dkss::kStFinal, 0});
     for (int d = (int)max_levels - 1; d >= 0; --d) {
-        st.push_back({dkss::kStInvTwiddle, (uint32_t)d});
-        st.push_back({dkss::kStInvDft, (uint32_t)d});
+        st.push_back({dkss::kStInvLevel, (uint32_t)d});
     }
     st.push_back({dkss::kStDecTiles, 0});
     st.push_back({dkss::kStDecScan, 0});
@@ -380,13 +378,14 @@ dkss_status dkss_batch_plan(dkss_batch_t* out, const uint64_t* n_bits, size_t co
 
     // persistent grid: as many CTAs as can be resident
     // column DFTs; the fused last level with the NTT exchange buffers after its
-    // two blocks; twiddle exchange buffers; decode tiles
+    // two blocks; twiddle exchange buffers; fused levels (column + exchange
+    // buffers); decode tiles
     const size_t xbuf = sizeof(uint32_t) * (size_t)dkss::NttTeam<kBm>::NTEAMS * kBm * kBLR;
     size_t fin = 0;
     for (const auto& t : b->tables)
         fin = std::max(fin, dkss::final_smem_bytes<kBm, kBL, kBLR>((int)t->host.r_last, dkss::kFormNtt));
     b->smem = std::max({sizeof(uint32_t) * (size_t)G::TWO_M * G::EW, fin, xbuf,
-                        sizeof(uint32_t) * (size_t)dkss::kDecSmemWords});
+                        dkss::level_ntt_smem_bytes<kBm, kBL, kBLR>(), sizeof(uint32_t) * (size_t)dkss::kDecSmemWords});
     int per_sm = 0, sms = 0, optin = 0;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device) != cudaSuccess ||
         (int)b->smem > optin ||

@@ -2,9 +2,10 @@
 //
 // A batch groups its jobs into size classes that share the residue ring (m,
 // p, z, hence L and LR) and differ in M and u.  The persistent kernel walks a
-// host-built list of stages (forward inner DFTs and twiddles per level, the
-// fused last level with the componentwise products, backwards twiddles and
-// DFTs per level, decode tiles, carry scan, carry fix-up).  In each stage
+// host-built list of stages (per level the fused column DFT and its
+// R-multiplications, forward; the fused last level with the componentwise
+// products; per level backwards the fused R-multiplications and column DFT;
+// decode tiles, carry scan, carry fix-up).  In each stage
 // every CTA takes work items -- a column, a group of elements, a block, a
 // tile -- from all jobs at once, then the grid synchronises (a cooperative
 // launch keeps every CTA resident, so the grid barrier cannot wait on a CTA
@@ -28,7 +29,9 @@ enum BatchStageType : uint32_t {
     kStInvDft = 4,
     kStDecTiles = 5,
     kStDecScan = 6,
-    kStDecFix = 7
+    kStDecFix = 7,
+    kStFwdLevel = 8,    // column DFT and its R-multiplications fused (level_fwd_ntt)
+    kStInvLevel = 9     // R-multiplications and column DFT fused (level_inv_ntt)
 };
 
 // Per-job parameters (device copy).  lp.len / lp.bp are set per stage.
@@ -65,6 +68,8 @@ __host__ __device__ inline uint64_t batch_items(uint32_t type, uint32_t level, u
         case kStDecTiles: return n_tiles;
         case kStDecScan: return 1;
         case kStDecFix: return (n_tiles + kThreads - 1) / kThreads;
+        case kStFwdLevel: return level < col_levels ? 2 * cols : 0;
+        case kStInvLevel: return level < col_levels ? cols : 0;
     }
     return 0;
 }
@@ -94,6 +99,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(const BatchJob* __restric
             lp.len = lp.P2 / bp;
             const uint64_t cols = lp.P2 / G::TWO_M;
             switch (st.type) {
+                case kStFwdLevel:
+                    if (st.level == 0) level_fwd_ntt<m, L, LR, true>(lp, md, mr, smem, local % cols, (int)(local / cols));
+                    else level_fwd_ntt<m, L, LR, false>(lp, md, mr, smem, local % cols, (int)(local / cols));
+                    break;
+                case kStInvLevel:
+                    level_inv_ntt<m, L, LR>(lp, md, mr, smem, local);
+                    break;
                 case kStFwdDft:
                     if (st.level == 0) dft_fwd_column<m, L, true>(lp, md, smem, local % cols, (int)(local / cols));
                     else dft_fwd_column<m, L, false>(lp, md, smem, local % cols, (int)(local / cols));
