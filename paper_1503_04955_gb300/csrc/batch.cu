@@ -250,7 +250,7 @@ dkss_status dkss_batch_plan(dkss_batch_t* out, const uint64_t* n_bits, size_t co
         if (s == DKSS_OK && (t->host.L != kBL || t->host.LR != kBLR || !t->host.ntt_ok)) s = DKSS_EUNSUPPORTED;
         if (s == DKSS_OK) {
             std::vector<uint32_t> ev, nt;
-            dkss_planning::build_eval_table(&t->host, ev);
+            dkss_planning::build_eval_table(&t->host, ev, true);
             dkss_planning::build_ntt_consts(&t->host, nt);
             if (cudaMalloc(&t->d_eval, ev.size() * 4) != cudaSuccess || cudaMalloc(&t->d_ntt, nt.size() * 4) != cudaSuccess ||
                 cudaMemcpy(t->d_eval, ev.data(), ev.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||

@@ -331,8 +331,11 @@ void build_eval_level_tables(const dkss_plan_s* pl, std::vector<uint32_t>& out, 
 }
 
 // Evaluations of the bad twiddles: rho^s(gamma^(2j+1)) = omega^(s(2j+1)), stored
-// for s < mu_top at index i with j = brv(i), in device Montgomery form.
-void build_eval_table(const dkss_plan_s* pl, std::vector<uint32_t>& out) {
+// for s < mu_top at index i with j = brv(i), in device Montgomery form; for the
+// R-multiplications of the coefficient levels each entry also carries the
+// backward transform's m^-1 (ntt_backward<RAW_LO>), for the levels in
+// evaluation coordinates not.
+void build_eval_table(const dkss_plan_s* pl, std::vector<uint32_t>& out, bool with_minv) {
     const uint32_t m = pl->m, LR = pl->LR;
     uint32_t lg = 0;
     while ((1u << lg) < m) ++lg;
@@ -341,6 +344,8 @@ void build_eval_table(const dkss_plan_s* pl, std::vector<uint32_t>& out) {
     MontCtx c(pl->q);
     const u128 rdev = pow2_mod(26 * (int)LR, pl->q);
     const u128 om = c.to(pl->roots.omega);
+    const u128 phi = pl->q / pl->p * (pl->p - 1);
+    const u128 scale = with_minv ? c.pow(c.to(m), phi - 1) : c.to(1);   // m^-1 or 1
     unsigned hw = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
     uint64_t chunks = std::min<uint64_t>(hw, mu);
     std::vector<std::thread> th;
@@ -356,7 +361,7 @@ void build_eval_table(const dkss_plan_s* pl, std::vector<uint32_t>& out) {
                     cur = c.mul(cur, w2);
                 }
                 for (uint32_t i = 0; i < m; ++i)
-                    put_rr(&out[(s * m + i) * LR], to_dev(c, val[brv(i, lg)], rdev), LR);
+                    put_rr(&out[(s * m + i) * LR], to_dev(c, c.mul(val[brv(i, lg)], scale), rdev), LR);
                 ws = c.mul(ws, om);
             }
         });
@@ -377,8 +382,10 @@ void free_device(dkss_plan_s* pl) {
     cudaFree(pl->d_stage);
     cudaFree(pl->d_ntt);
     cudaFree(pl->d_evtw);
+    cudaFree(pl->d_table_minv);
     pl->d_ntt = nullptr;
     pl->d_evtw = nullptr;
+    pl->d_table_minv = nullptr;
     pl->d_table = nullptr; pl->d_work = nullptr; pl->d_agg = nullptr; pl->d_status = nullptr; pl->d_stage = nullptr;
 }
 
@@ -431,7 +438,10 @@ dkss_status dkss_plan(dkss_plan_t* plan, uint64_t n_bits, uint64_t M, uint32_t m
     }
     std::vector<uint32_t> table, ntt;
     if (pl->flags & (DKSS_RMUL_DIRECT | DKSS_FORM_INT8TC)) build_table(pl, table);
-    else build_eval_table(pl, table);
+    else build_eval_table(pl, table, !pl->eval_levels);
+    // levels in evaluation coordinates: dkss_forward still runs coefficient levels
+    std::vector<uint32_t> table_minv;
+    if (pl->eval_levels) build_eval_table(pl, table_minv, true);
     build_ntt_consts(pl, ntt);
     std::vector<uint32_t> evtw;
     if (pl->eval_levels) build_eval_level_tables(pl, evtw, pl->evtw_offs);
@@ -443,7 +453,8 @@ dkss_status dkss_plan(dkss_plan_t* plan, uint64_t n_bits, uint64_t M, uint32_t m
               cudaMalloc(&pl->d_agg, pl->n_tiles * sizeof(uint32_t)) == cudaSuccess &&
               cudaMalloc(&pl->d_status, sizeof(uint32_t)) == cudaSuccess &&
               cudaMalloc(&pl->d_ntt, ntt.size() * sizeof(uint32_t)) == cudaSuccess &&
-              (evtw.empty() || cudaMalloc(&pl->d_evtw, evtw.size() * sizeof(uint32_t)) == cudaSuccess);
+              (evtw.empty() || cudaMalloc(&pl->d_evtw, evtw.size() * sizeof(uint32_t)) == cudaSuccess) &&
+              (table_minv.empty() || cudaMalloc(&pl->d_table_minv, table_minv.size() * sizeof(uint32_t)) == cudaSuccess);
     if (!ok) {
         cudaGetLastError();
         free_device(pl);
@@ -454,6 +465,8 @@ dkss_status dkss_plan(dkss_plan_t* plan, uint64_t n_bits, uint64_t M, uint32_t m
         cudaMemcpy(pl->d_ntt, ntt.data(), ntt.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
         (!evtw.empty() &&
          cudaMemcpy(pl->d_evtw, evtw.data(), evtw.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess) ||
+        (!table_minv.empty() && cudaMemcpy(pl->d_table_minv, table_minv.data(), table_minv.size() * sizeof(uint32_t),
+                                           cudaMemcpyHostToDevice) != cudaSuccess) ||
         cudaMemset(pl->d_status, 0, sizeof(uint32_t)) != cudaSuccess) {
         free_device(pl);
         delete pl;

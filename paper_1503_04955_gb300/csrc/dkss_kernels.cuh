@@ -554,12 +554,15 @@ __device__ __forceinline__ void twiddle_ntt_group(const LevelParams& prm, const 
         ldg_rr<LR>(t, tw + j * LR);
         mmul<LR>(vv[j], vv[j], t, mr);
     }
-    ntt_backward<m, LR>(vv, buf, lane, tm.mask, prm.ntt_cst, NttLayout<m>::TW_LO, NttLayout<m>::TW_HI, mr);
+    // the table carries m^-1: the last stage multiplies only by psi^-1 and
+    // slots 0 and 1 are reduced without a product
+    ntt_backward<m, LR, true>(vv, buf, lane, tm.mask, prm.ntt_cst, 0, NttLayout<m>::ZLAST, mr);
     __syncwarp(tm.mask);   // every lane has read its shifted inputs before any write
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         uint32_t c[LR], o[L];
-        canon<LR>(c, vv[j], mr);
+        if (j < 2) reduce_raw<LR>(c, vv[j], mr);
+        else canon<LR>(c, vv[j], mr);
         from_rr<L, LR>(o, c);
         st_res<L>(x + (lane + j * NT::TEAM) * L, o);
     }
@@ -598,11 +601,14 @@ __device__ __forceinline__ void level_rmul_element(const LevelParams& prm, const
         ldg_rr<LR>(t, tw + j * LR);
         mmul<LR>(vv[j], vv[j], t, mr);
     }
-    ntt_backward<m, LR>(vv, buf, lane, mask, prm.ntt_cst, NttLayout<m>::TW_LO, NttLayout<m>::TW_HI, mr);
+    // the table carries m^-1: the last stage multiplies only by psi^-1 and
+    // slots 0 and 1 are reduced without a product
+    ntt_backward<m, LR, true>(vv, buf, lane, mask, prm.ntt_cst, 0, NttLayout<m>::ZLAST, mr);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         uint32_t c[LR], o[L];
-        canon<LR>(c, vv[j], mr);
+        if (j < 2) reduce_raw<LR>(c, vv[j], mr);
+        else canon<LR>(c, vv[j], mr);
         from_rr<L, LR>(o, c);
         st_res<L>(dst + (lane + j * NT::TEAM) * L, o);
     }

@@ -385,6 +385,7 @@ dkss_status run_forward(dkss_plan_s* pl, const uint64_t* a, uint64_t* out, cudaS
     LevelParams lp = make_level(pl);
     lp.raw_a = a;
     lp.raw_b = a;
+    if (pl->d_table_minv) lp.table_eval = pl->d_table_minv;   // coefficient levels for a plan in evaluation coordinates
     dkss_status s = launch_forward_levels<m, L, LR>(pl, lp, 1, st);
     if (s != DKSS_OK) return s;
     lp.len = pl->r_last;

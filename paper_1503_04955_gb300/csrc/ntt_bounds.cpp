@@ -323,6 +323,10 @@ bool ntt_lazy_bounds(uint32_t m, uint32_t LR, u128 q, NttBiases* out) {
         if (!c.mmul(d, C, &r2)) return false;
         if (b + 1 == lg) {
             if (!c.mmul(s, C, &r1) || !c.below_2q(r1) || !c.below_2q(r2)) return false;
+            // with the twiddle table carrying m^-1, s itself is reduced (reduce_raw):
+            // a quotient below 2^12, and q's top two limbs at least 2^18
+            if (s.v.cmp(c.qb * Big::of((u128)1 << 12)) >= 0 || c.qb.shr(26 * (LR - 2)).cmp(Big::pow2(18)) < 0)
+                return false;
         } else {
             U = c.max(s, r2);
         }

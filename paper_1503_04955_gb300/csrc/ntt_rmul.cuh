@@ -130,6 +130,37 @@ __device__ __forceinline__ void lz_norm(uint32_t (&x)[LR]) {
     x[LR - 1] += carry;
 }
 
+// Canonical residue of a lazy value x (limbs below 2^32, value below 2^20 q):
+// quotient estimate k from the top two limbs in single precision, one
+// multi-limb subtraction of (k - 1) q, then two conditional subtractions.  The
+// estimate is within one of floor(x / q) because q's top two limbs (26 (LR-2)
+// bits down) hold at least 2^18 (the plan's limb choice), so x - (k - 1) q is
+// in [0, 3q).
+template <int LR>
+__device__ __forceinline__ void reduce_raw(uint32_t (&r)[LR], const uint32_t (&x)[LR], const ModRR<LR>& md) {
+    uint32_t y[LR];
+#pragma unroll
+    for (int i = 0; i < LR; ++i) y[i] = x[i];
+    lz_norm<LR>(y);
+    const float vf = __uint2float_rz(y[LR - 1]) * 67108864.0f + __uint2float_rz(y[LR - 2]);
+    const float qf = __uint2float_rz(md.q[LR - 1]) * 67108864.0f + __uint2float_rz(md.q[LR - 2]);
+    const uint32_t ke = __float2uint_rz(__fdiv_rz(vf, qf));
+    const uint32_t k = ke > 0 ? ke - 1 : 0;
+    int64_t carry = 0;
+#pragma unroll
+    for (int i = 0; i < LR; ++i) {
+        const int64_t acc = (int64_t)y[i] - (int64_t)((uint64_t)k * md.q[i]) + carry;
+        if (i + 1 < LR) {
+            r[i] = (uint32_t)acc & kM26;
+            carry = acc >> 26;
+        } else {
+            r[i] = (uint32_t)acc;
+        }
+    }
+    canon<LR>(r, r, md);
+    canon<LR>(r, r, md);
+}
+
 // Position of index i in a team's exchange buffer: an XOR swizzle of its
 // low bits by its high bits, so that in every layout below the eight lanes of
 // a quarter warp touch eight different 16-byte bank groups (m = 32, 64).
@@ -195,8 +226,10 @@ __device__ __forceinline__ void ntt_forward(uint32_t (&v)[4][LR], uint32_t* buf,
 // the evaluation at bit-reversed position 4l + j; on exit coefficient
 // l + j m/4 of the interpolated element times c (normalised, below 2q), where
 // the last stage multiplies by cst[lo_c] and cst[hi_c] (= c and psi^-1 c,
-// times R').
-template <int m, int LR>
+// times R').  With RAW_LO (c = 1, already folded into the inputs) the last
+// stage leaves slots 0 and 1 as the plain sums, unreduced (reduce_raw), and
+// multiplies only slots 2 and 3 by cst[hi_c].
+template <int m, int LR, bool RAW_LO = false>
 __device__ __forceinline__ void ntt_backward(uint32_t (&v)[4][LR], uint32_t* buf, int lane, unsigned mask,
                                              const uint32_t* cst, int lo_c, int hi_c, const ModRR<LR>& md) {
     using NL = NttLayout<m>;
@@ -223,10 +256,15 @@ __device__ __forceinline__ void ntt_backward(uint32_t (&v)[4][LR], uint32_t* buf
             lz_add<LR>(s, v[jl], v[jh]);                 // u + v
             lz_sub<LR>(d, v[jl], bias, v[jh]);           // u - v
             if (b == LG - 1) {
-                uint32_t c[LR];
-                ldg_rr<LR>(c, cst + lo_c * LR);
                 ldg_rr<LR>(z, cst + hi_c * LR);
-                mmul<LR>(v[jl], s, c, md);
+                if constexpr (RAW_LO) {
+#pragma unroll
+                    for (int w = 0; w < LR; ++w) v[jl][w] = s[w];
+                } else {
+                    uint32_t c[LR];
+                    ldg_rr<LR>(c, cst + lo_c * LR);
+                    mmul<LR>(v[jl], s, c, md);
+                }
                 mmul<LR>(v[jh], d, z, md);
             } else {
                 const int k = (1 << (LG - 1 - b)) + (lidx(lane, jl, h) >> (b + 1));

@@ -35,6 +35,7 @@ struct dkss_plan_s {
     uint32_t* d_ntt = nullptr;    // constants of the transform in R
     bool eval_levels = false;     // inner levels in evaluation coordinates (eval_levels.cuh)
     uint32_t* d_evtw = nullptr;   // their bad twiddles of levels d >= 1
+    uint32_t* d_table_minv = nullptr;  // their plans: the level-twiddle table with m^-1 (dkss_forward)
     std::vector<uint64_t> evtw_offs;  // word offset of level d's table in d_evtw
     uint32_t* d_work = nullptr;   // two transformed polynomials
     uint64_t poly_words = 0;
@@ -57,7 +58,7 @@ namespace dkss_planning {
 // Host parts of a plan, shared by single plans and batches (capi.cu).
 dkss_status plan_host(dkss_plan_s* pl, uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, uint64_t p, uint32_t z);
 void build_table(const dkss_plan_s* pl, std::vector<uint32_t>& out);
-void build_eval_table(const dkss_plan_s* pl, std::vector<uint32_t>& out);
+void build_eval_table(const dkss_plan_s* pl, std::vector<uint32_t>& out, bool with_minv);
 void build_ntt_consts(const dkss_plan_s* pl, std::vector<uint32_t>& out);
 void build_eval_level_tables(const dkss_plan_s* pl, std::vector<uint32_t>& out, std::vector<uint64_t>& offs);
 }  // namespace dkss_planning
