@@ -49,7 +49,7 @@ HBM_GBS = 6782.1                  # measured copy bandwidth of this machine's GB300
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture
 # (profiles/stage_kernels_dkss_2p24b.md); valid only for the kernel version captured.
 FORM_FLAGS = {"ntt": 0, "eval": 128, "direct": 16}   # binding.LEVELS_EVAL, binding.RMUL_DIRECT
-NCU_TRAFFIC_BYTES = {("dkss_2p24b", "ntt", "fwd_twiddle"): 46.6e6, ("dkss_2p24b", "eval", "fwd_twiddle"): 44.4e6}
+NCU_TRAFFIC_BYTES = {("dkss_2p24b", "ntt", "fwd_twiddle"): 46.6e6}
 
 
 def parse_args():
