@@ -8,9 +8,10 @@
 // (Section 3.2.5 i.-iii.), done in place level by level: level d splits each
 // block of len = 2M/(2m)^(d-1) elements into 2m rows of len/2m columns; one
 // CTA takes one column and runs the 2m-point inner DFT with root alpha (shifts
-// only) in shared memory, then an element-parallel kernel multiplies output v
-// of column l by the bad twiddle rho^(v*l*(2m)^(d-1)), one team of m/2 lanes
-// per element.  After the last level the elements sit in
+// only) in shared memory, then multiplies output v of column l by the bad
+// twiddle rho^(v*l*(2m)^(d-1)) (k_level_fwd_ntt; for m = 64, or the direct and
+// INT8 forms, a column-DFT kernel followed by an element-parallel twiddle
+// kernel).  After the last level the elements sit in
 // mixed-radix digit-reversed order.  Componentwise products do not care about
 // order; the backwards transform runs the same levels in reverse as
 // decimation in frequency with rho^-1 and alpha^-1 (the backwards transform
@@ -32,7 +33,8 @@ template <int m, int L>
 struct Geo {
     static constexpr int TWO_M = 2 * m;
     static constexpr int EW = m * L;                     // words per element of R
-    static constexpr int TEAM = m / 2;                   // lanes per element (2 coefficients each)
+    static constexpr int TEAM = m / 2;                   // lanes per element in the DFTs and the direct
+                                                         // form (2 coefficients each)
     static constexpr int TEAMS_PER_WARP = 32 / TEAM;
     static constexpr int NTEAMS = kWarps * TEAMS_PER_WARP;
     static constexpr int CPL = m / TEAM;                 // coefficients per lane
