@@ -48,7 +48,8 @@ SM_MAX_MHZ = 2070.0
 HBM_GBS = 6782.1                  # measured copy bandwidth of the GB300s (MEASURED_PEAKS.json)
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture
 # (profiles/stage_kernels_dkss_2p24b.md); valid only for the kernel version captured.
-FORM_FLAGS = {"ntt": 0, "eval": 128, "direct": 16}   # binding.LEVELS_EVAL, binding.RMUL_DIRECT
+FORM_FLAGS = {"ntt": 0, "eval": 128, "direct": 16, "int8tc": 2}   # binding.LEVELS_EVAL, RMUL_DIRECT, FORM_INT8TC
+I8_TOPS = 150.0                   # mma.sync.m16n8k32 u8 throughput measured on this machine's GB300 (2 ops per MAC)
 NCU_TRAFFIC_BYTES = {("dkss_2p24b", "ntt", "fwd_twiddle"): 46.6e6}
 
 
@@ -65,9 +66,10 @@ def parse_args():
     ap.add_argument("--batched-steps", type=int, default=10)
     ap.add_argument("--no-forms", action="store_true", help="skip the R-multiplication form comparison")
     ap.add_argument("--form-steps", type=int, default=20)
-    ap.add_argument("--form", default="ntt", choices=["ntt", "eval", "direct"],
+    ap.add_argument("--form", default="ntt", choices=["ntt", "eval", "direct", "int8tc"],
                     help="alpha-shift inner DFTs with R-multiplications through the evaluation map of R (ntt, the "
-                         "default), inner levels in evaluation coordinates (eval), or the direct convolution")
+                         "default), inner levels in evaluation coordinates (eval), the direct convolution, or "
+                         "INT8 tensor-core byte-slice convolutions (int8tc)")
     return ap.parse_args()
 
 
@@ -200,6 +202,26 @@ def stage_work_eval(info, m, L):
             "inv_twiddle": (inv * k, col_levels)}
 
 
+def stage_work_i8(info, m):
+    """Tensor-core operations of the INT8 form by kernel group (2 per u8
+    multiply-accumulate): an R-multiplication of residues of S bytes is, for
+    each of the S byte planes of one factor, an m x m Toeplitz matrix times
+    the m x S matrix of the other factor's bytes, S^2 m^2 MACs.  Twiddles
+    rho^0 = 1 are not work; every componentwise product is one
+    R-multiplication.  The integer recombination and reduction are not
+    counted (they run on the integer pipe)."""
+    P2, col_levels = info["P2"], info["levels"] - 1
+    S = (info["pz"].bit_length() + 7) // 8
+    nontrivial, length = [], P2
+    for _ in range(col_levels):
+        mu_d = length // (2 * m)
+        nontrivial.append((P2 // length) * (mu_d - 1) * (2 * m - 1))
+        length //= 2 * m
+    r = 2 * S * S * m * m
+    return {"fwd_twiddle": (2 * sum(nontrivial) * r, col_levels), "final_pointwise": (P2 * r, 1),
+            "inv_twiddle": (sum(nontrivial) * r, col_levels)}
+
+
 def stage_work(info, m, form):
     """Per kernel group: (algorithmic 32-bit multiply-adds per step, launches
     per step).  Twiddles rho^0 = 1 are not work; every other twiddle and every
@@ -209,6 +231,8 @@ def stage_work(info, m, form):
     P2, L, col_levels = info["P2"], info["L"], info["levels"] - 1
     if form == "eval":
         return stage_work_eval(info, m, L)
+    if form == "int8tc":
+        return stage_work_i8(info, m)
     nontrivial = []
     length = P2
     for _ in range(col_levels):
@@ -316,7 +340,13 @@ def run_ours(args):
     ops_per_launch = ops_per_step / max(1, launches_per_step)
     avg_launch_ms = dom_ms / max(1, dom_n)
     achieved = ops_per_launch / (avg_launch_ms * 1e-3) / 1e12
-    peak = SM_COUNT_GB300 * IMAD_PER_SM_PER_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    if args.form == "int8tc":
+        bound, unit, peak = "tensor", "TOPS", I8_TOPS
+        peak_basis = "mma.sync.m16n8k32 u8 throughput measured on this pool's GB300 (2 ops per MAC)"
+    else:
+        bound, unit = "alu", "TIMAD/s"
+        peak = SM_COUNT_GB300 * IMAD_PER_SM_PER_CLK * SM_MAX_MHZ * 1e6 / 1e12
+        peak_basis = "152 SMs x 64 IMAD/clk x 2070 MHz (recipe unit counts and max clock)"
     # memory-bound groups: algorithmic bytes = one read and one write of the
     # polynomials they pass over (DFT levels), or of the product polynomial and
     # the product words (decode)
@@ -331,18 +361,18 @@ def run_ours(args):
             continue
         if k in work:
             ach = work[k][0] / (ms * 1e-3) / 1e12
-            stages[k] = {"bound": "alu", "ms": round(ms, 4), "achieved": round(ach, 3), "unit": "TIMAD/s",
+            stages[k] = {"bound": bound, "ms": round(ms, 4), "achieved": round(ach, 3), "unit": unit,
                          "frac": round(ach / peak, 4)}
         elif k in mem_bytes:
             ach = mem_bytes[k] / (ms * 1e-3) / 1e9
             stages[k] = {"bound": "hbm", "ms": round(ms, 4), "achieved": round(ach, 1), "unit": "GB/s",
                          "frac": round(ach / HBM_GBS, 4)}
-    roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 3),
-                "unit": "TIMAD/s", "frac": round(achieved / peak, 4),
+    roofline = {"bound": bound, "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 3),
+                "unit": unit, "frac": round(achieved / peak, 4),
                 "traffic": NCU_TRAFFIC_BYTES.get((args.workload, args.form, dom)),
                 "stages": stages,
                 "avg_launch_ms": round(avg_launch_ms, 4), "ops_per_launch": int(ops_per_launch),
-                "peak_basis": "152 SMs x 64 IMAD/clk x 2070 MHz (recipe unit counts and max clock)"}
+                "peak_basis": peak_basis}
 
     batched = run_batched(args, dev, flush) if (rank == 0 and not args.no_batched) else None
     forms = compare_forms(args, dev, flush, a, b, out, ms_per_step) if (rank == 0 and not args.no_forms) else None
@@ -355,9 +385,11 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": round(value, 4), "unit": "Gbit/s", "n_gpus": world,
             "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(ms_per_step, 5),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u8" if args.form == "int8tc" else "u32",
             "data": "synthetic: SplitMix64 uniform operands in [0, 2^N)",
-            "config": dict(workload_config(args.workload), form="imad", rmul=args.form,
+            "config": dict(workload_config(args.workload), form="int8tc" if args.form == "int8tc" else "imad",
+                           rmul=args.form,
                            l2="flushed between steps (256 MiB write outside the timed events)",
                            parallelism="replicas" if world > 1 else "single GPU"),
             "products_per_s": round(world / (ms_per_step * 1e-3), 3),

@@ -1,7 +1,7 @@
 """GB300 (sm_103a) DKSS integer multiplication: Python binding of libdkss.so.
 
 The arithmetic runs in hand-written CUDA kernels behind the C ABI declared in
-include/dkss.h; this package builds the library (build.py) and marshals
+include/dkss.h; this package builds the library (buildlib.py) and marshals
 arguments to it (binding.py).
 """
 from .binding import Plan, Batch, DkssError, plan_rho, load, lib_path, mul_batch, EXPORTS  # noqa: F401
