@@ -45,12 +45,13 @@ L2_FLUSH_BYTES = 256 << 20
 SM_COUNT_GB300 = 152
 IMAD_PER_SM_PER_CLK = 64          # 32-bit integer multiply-add lanes per SM per clock
 SM_MAX_MHZ = 2070.0
-HBM_GBS = 6782.1                  # measured copy bandwidth of the GB300s (MEASURED_PEAKS.json)
+HBM_GBS = 6782.1                  # STREAM-style copy bandwidth measured on a GB300 (HBM roofline denominator)
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture
-# (profiles/stage_kernels_dkss_2p24b.md); valid only for the kernel version captured.
+# (profiles/stage_kernels_dkss_2p24b*.md); valid only for the kernel version captured.
 FORM_FLAGS = {"ntt": 0, "eval": 128, "direct": 16, "int8tc": 2}   # binding.LEVELS_EVAL, RMUL_DIRECT, FORM_INT8TC
-I8_TOPS = 150.0                   # mma.sync.m16n8k32 u8 throughput measured on this machine's GB300 (2 ops per MAC)
-NCU_TRAFFIC_BYTES = {("dkss_2p24b", "ntt", "fwd_twiddle"): 46.6e6}
+I8_TOPS = 150.0                   # mma.sync.m16n8k32 u8 throughput measured on a GB300 (2 ops per MAC)
+NCU_TRAFFIC_BYTES = {("dkss_2p24b", "ntt", "fwd_twiddle"): 46.6e6,
+                     ("dkss_2p24b", "eval", "fwd_twiddle"): 44.3e6}
 
 
 def parse_args():
@@ -342,7 +343,7 @@ def run_ours(args):
     achieved = ops_per_launch / (avg_launch_ms * 1e-3) / 1e12
     if args.form == "int8tc":
         bound, unit, peak = "tensor", "TOPS", I8_TOPS
-        peak_basis = "mma.sync.m16n8k32 u8 throughput measured on this pool's GB300 (2 ops per MAC)"
+        peak_basis = "mma.sync.m16n8k32 u8 throughput measured on a GB300 (2 ops per MAC)"
     else:
         bound, unit = "alu", "TIMAD/s"
         peak = SM_COUNT_GB300 * IMAD_PER_SM_PER_CLK * SM_MAX_MHZ * 1e6 / 1e12
