@@ -333,6 +333,20 @@ def run_ours(args):
     ok = ok and check_product(cn, A, B)
     e2e_value = job_gbit_s(2 * n_bits, world, e2e_s * 1e3)
 
+    # squares of the same operand (dkss_mul with a == b: one forward transform)
+    sq_steps = max(1, min(args.steps, 50))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(sq_steps)]
+    for e0, e1 in ev:
+        flush.fill_(1)
+        e0.record(stream)
+        plan.mul(a, a, out)
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    sq_ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / sq_steps
+    square = {"ms_per_step": round(sq_ms, 5), "speedup_vs_product": round(ms_per_step / sq_ms, 3),
+              "bit_exact": bool(check_product(out.cpu().numpy().view(np.uint64), A, A))}
+    plan.profile_read()
+
     # roofline of the kernel group with the most device time
     work = stage_work(info, cfg[2], args.form)
     dom = max((k for k in prof if k in work), key=lambda k: prof[k][0])
@@ -402,6 +416,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "batched": batched,
             "forms": forms,
+            "square": square,
             "clocks": clocks,
             "wall_s": round(wall, 3),
         }

@@ -96,10 +96,42 @@ dkss_status dkss_plan(dkss_plan_t* plan, uint64_t n_bits, uint64_t M, uint32_t m
  * out = a * b (thesis Section 3.2 steps 4-8).  a, b: device pointers to
  * ceil(N/64) words each; out: device pointer to 2*ceil(N/64) words, which must
  * not overlap a or b.  Queued on `stream`; the caller keeps a, b, out alive
- * until the stream reaches this work.  Errors: DKSS_EINVAL, DKSS_ECUDA.
+ * until the stream reaches this work.  When a == b (the same pointer) the
+ * product is a square and takes dkss_sqr's path.  Errors: DKSS_EINVAL,
+ * DKSS_ECUDA.
  */
 dkss_status dkss_mul(dkss_plan_t plan, const uint64_t* a, const uint64_t* b, uint64_t* out,
                      dkss_stream_t stream);
+
+/*
+ * out = a^2.  The forward transform (Section 3.2 step 5) runs once, on a
+ * alone, and the componentwise products (step 6) square each element
+ * (through the evaluation map of R, one forward transform per element instead
+ * of two); the rest is the product's path.  This is the operation of the
+ * thesis's system test, the Lucas-Lehmer test of Mersenne numbers
+ * (implementation chapter, "system test"; see dkss_ll_step).  a: device
+ * pointer to ceil(N/64) words; out: 2*ceil(N/64) words, not overlapping a.
+ * Errors: as dkss_mul.
+ */
+dkss_status dkss_sqr(dkss_plan_t plan, const uint64_t* a, uint64_t* out, dkss_stream_t stream);
+
+/*
+ * One step of the Lucas-Lehmer test of M_p = 2^p - 1 after the square:
+ * s = (c - 2) mod M_p for c = s_prev^2 < 2^(2p) (the thesis's system test, as
+ * above; the test itself: s_0 = 4, s_(k+1) = s_k^2 - 2 mod M_p, and M_p is
+ * prime iff s_(p-2) = 0 for odd prime p).  The thesis has no kernel for it;
+ * the modular reduction folds c's high part onto its low part, since
+ * 2^p = 1 mod M_p, and the result is the canonical residue in [0, M_p).
+ *   c  device pointer, 2*w words (w = ceil(p/64)), little-endian, c < 2^(2p).
+ *   s  device pointer, w words; receives the residue, bits >= p zero.  May
+ *      not overlap c.
+ *   p  2 < p < 2^26.
+ * One thread of one CTA works through the words in order (a short serial
+ * step beside the square; not part of the product's path).  Queued on
+ * `stream`.  Errors: DKSS_EINVAL (null pointer, p out of range, overlap),
+ * DKSS_ECUDA.
+ */
+dkss_status dkss_ll_step(const uint64_t* c, uint64_t* s, uint32_t p, dkss_stream_t stream);
 
 /*
  * Same product from host memory: copies a and b (ceil(N/64) words each) to the

@@ -383,3 +383,20 @@ def omul(a_words, b_words):
             carry = t // base
         c[i + len(b_words)] += carry
     return c
+
+
+# ---------------------------------------------------------------------------
+# System test of the implementation chapter: the Lucas-Lehmer test
+# ---------------------------------------------------------------------------
+
+def lucas_lehmer(p):
+    """Last residue of the Lucas-Lehmer test of M_p = 2^p - 1, which the thesis
+    runs with its DKSS square as a system test (implementation chapter, "system
+    test"; the test as in Crandall-Pomerance Section 4.2.1): s_0 = 4,
+    s_(k+1) = s_k^2 - 2 mod M_p for k < p - 2.  For an odd prime p, M_p is
+    prime iff the result is 0.  Python integers throughout."""
+    mp = (1 << p) - 1
+    s = 4
+    for _ in range(p - 2):
+        s = (s * s - 2) % mp
+    return s

@@ -21,8 +21,8 @@ FORM_IMAD = 1
 FORM_INT8TC = 2
 
 # Names exported by libdkss.so (include/dkss.h)
-EXPORTS = ["dkss_plan", "dkss_mul", "dkss_mul_host", "dkss_forward", "dkss_mul_batch", "dkss_plan_info",
-           "dkss_plan_rho", "dkss_profile_read", "dkss_plan_launches", "dkss_sync_status", "dkss_plan_destroy",
+EXPORTS = ["dkss_plan", "dkss_mul", "dkss_sqr", "dkss_ll_step", "dkss_mul_host", "dkss_forward", "dkss_mul_batch",
+           "dkss_plan_info", "dkss_plan_rho", "dkss_profile_read", "dkss_plan_launches", "dkss_sync_status", "dkss_plan_destroy",
            "dkss_status_str", "dkss_decode_static", "dkss_batch_plan", "dkss_batch_run", "dkss_batch_job_params",
            "dkss_batch_destroy", "dkss_plan_candidates", "dkss_mlp_forward", "dkss_mlp_grad", "dkss_mlp_adam"]
 FORM_PROFILE = 4
@@ -57,6 +57,8 @@ def load():
     lib.dkss_plan.argtypes = [ctypes.POINTER(P), u64, u64, u32, u32, u64, u32, u32]
     lib.dkss_mul.argtypes = [P, P, P, P, P]
     lib.dkss_mul_host.argtypes = [P, P, P, P, P]
+    lib.dkss_sqr.argtypes = [P, P, P, P]
+    lib.dkss_ll_step.argtypes = [P, P, u32, P]
     lib.dkss_forward.argtypes = [P, P, P, P]
     lib.dkss_mul_batch.argtypes = [P, sz, u32, P]
     lib.dkss_plan_info.argtypes = [P, P, sz, P]
@@ -77,7 +79,7 @@ def load():
     lib.dkss_plan_destroy.argtypes = [P]
     lib.dkss_status_str.argtypes = [ctypes.c_int]
     lib.dkss_status_str.restype = ctypes.c_char_p
-    for name in ("dkss_plan", "dkss_mul", "dkss_mul_host", "dkss_forward", "dkss_mul_batch",
+    for name in ("dkss_plan", "dkss_mul", "dkss_sqr", "dkss_ll_step", "dkss_mul_host", "dkss_forward", "dkss_mul_batch",
                  "dkss_plan_info", "dkss_plan_rho", "dkss_profile_read", "dkss_sync_status", "dkss_plan_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -182,6 +184,16 @@ class Plan:
                "dkss_mul")
         return out
 
+    def sqr(self, a, out=None, stream=None):
+        """out = a*a on the GPU (dkss_sqr: one forward transform)."""
+        import torch
+        self._check_operand(a, self.words)
+        if out is None:
+            out = torch.empty(2 * self.words, dtype=a.dtype, device=a.device)
+        self._check_operand(out, 2 * self.words)
+        _check(load().dkss_sqr(self._h, a.data_ptr(), out.data_ptr(), _stream_handle(stream)), "dkss_sqr")
+        return out
+
     def mul_host(self, a, b, out=None, stream=None):
         """Product of host arrays (numpy uint64) through dkss_mul_host."""
         a = np.ascontiguousarray(a, dtype=np.uint64)
@@ -228,6 +240,17 @@ def decode_static(c, n_bits, M, m, u, L, out=None, stream=None):
     _check(load().dkss_decode_static(c.data_ptr(), n_bits, M, m, u, L, out.data_ptr(), _stream_handle(stream)),
            "dkss_decode_static")
     return out
+
+
+def ll_step(c, s, p, stream=None):
+    """dkss_ll_step: s = (c - 2) mod (2^p - 1), the Lucas-Lehmer step after the
+    square.  c: CUDA tensor of 2*ceil(p/64) 64-bit words; s: ceil(p/64) words."""
+    w = (p + 63) // 64
+    for t, n in ((c, 2 * w), (s, w)):
+        if not t.is_cuda or t.element_size() != 8 or not t.is_contiguous() or t.numel() != n:
+            raise ValueError("expected a contiguous CUDA tensor of %d 64-bit words" % n)
+    _check(load().dkss_ll_step(c.data_ptr(), s.data_ptr(), p, _stream_handle(stream)), "dkss_ll_step")
+    return s
 
 
 BATCH_RULE = 32

@@ -37,6 +37,7 @@ def _flags(extra_ptxas=False):
 def _units():
     units = [("capi.o", os.path.join(CSRC, "capi.cu"), []),
              ("decode_static.o", os.path.join(CSRC, "decode_static.cu"), []),
+             ("mersenne.o", os.path.join(CSRC, "mersenne.cu"), []),
              ("batch.o", os.path.join(CSRC, "batch.cu"), []),
              ("mlp.o", os.path.join(CSRC, "mlp.cu"), []),
              ("host_math.o", os.path.join(CSRC, "host_math.cpp"), ["-x", "cu"]),

@@ -493,6 +493,10 @@ dkss_status dkss_mul(dkss_plan_t pl, const uint64_t* a, const uint64_t* b, uint6
     return k.mul(pl, a, b, out, (cudaStream_t)stream);
 }
 
+dkss_status dkss_sqr(dkss_plan_t pl, const uint64_t* a, uint64_t* out, dkss_stream_t stream) {
+    return dkss_mul(pl, a, a, out, stream);
+}
+
 dkss_status dkss_mul_host(dkss_plan_t pl, const uint64_t* a_host, const uint64_t* b_host, uint64_t* out_host,
                           dkss_stream_t stream) {
     if (!pl || !a_host || !b_host || !out_host) return DKSS_EINVAL;

@@ -70,6 +70,7 @@ struct LevelParams {
     const uint32_t* tw_lvl;      // inner levels in evaluation coordinates: this level's twiddles
     uint32_t eval_skip;          // their DFTs: bit s = stage s adds t = b unreduced where the twiddle is 1
     uint32_t eval_noscale;       // last level: multiply a b unscaled, scale by (2M)^-1 at the end
+    uint32_t square;             // last level of a square (b is a): one forward transform per element
 };
 
 // How R-multiplications are computed.
@@ -801,12 +802,15 @@ __device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) st_rr<LR>(park + j * NT::TEAM * LR, x[j]);
+            // a square keeps the unscaled evaluations of a = b in registers
+            if (!prm.square || prm.ntt_prescale) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                ld_res<L>(w, sa + v * G::EW + (lane + j * NT::TEAM) * L);
-                to_rr<L, LR>(x[j], w);
+                for (int j = 0; j < 4; ++j) {
+                    ld_res<L>(w, sa + v * G::EW + (lane + j * NT::TEAM) * L);
+                    to_rr<L, LR>(x[j], w);
+                }
+                ntt_forward<m, LR>(x, buf, lane, nt.mask, prm.ntt_cst, mr);
             }
-            ntt_forward<m, LR>(x, buf, lane, nt.mask, prm.ntt_cst, mr);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 uint32_t y[LR];

@@ -335,9 +335,15 @@ dkss_status run_mul(dkss_plan_s* pl, const uint64_t* a, const uint64_t* b, uint6
             return launch_decode<m, L, LR>(pl, out, st);
         }
     }
-    s = launch_forward_levels<m, L, LR>(pl, lp, 2, st);
+    // a square (a == b) transforms one polynomial; the last level reads it as both factors
+    const bool square = a == b;
+    s = launch_forward_levels<m, L, LR>(pl, lp, square ? 1 : 2, st);
     if (s != DKSS_OK) return s;
     lp.len = pl->r_last;
+    if (square) {
+        lp.poly_words = 0;
+        lp.square = 1;
+    }
     {
         ProfScope ps(pl, st, kProfFinal);
         const unsigned blocks = (unsigned)(pl->P2 / pl->r_last);
@@ -356,6 +362,8 @@ dkss_status run_mul(dkss_plan_s* pl, const uint64_t* a, const uint64_t* b, uint6
         }
         DKSS_CHECK_LAUNCH();
     }
+    lp.poly_words = pl->poly_words;
+    lp.square = 0;
     const bool fused = fused_levels<m, L, LR>(pl);
     for (int d = (int)pl->col_levels - 1; d >= 0; --d) {
         level_geometry(pl, (uint32_t)d, &lp.len, &lp.bp);

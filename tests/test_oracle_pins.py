@@ -407,3 +407,44 @@ def test_mlp_oracle_first_adam_step():
     g = np.array([0.3, -2.0, 1e-3, 0.0])
     p, m1, m2 = mo.adam_step(np.zeros(4), g, np.zeros(4), np.zeros(4), 0.01, 1)
     assert np.allclose(p, -0.01 * g / (np.abs(g) + 1e-8))
+
+
+# ---- Lucas-Lehmer system test (implementation chapter) ----------------------
+
+def _is_prime_trial(n):
+    if n < 2:
+        return False
+    f = 2
+    while f * f <= n:
+        if n % f == 0:
+            return False
+        f += 1
+    return True
+
+
+def test_lucas_lehmer_small_exponents_by_trial_division():
+    """For odd prime p <= 31 the oracle's test says "prime" exactly when trial
+    division finds no factor of 2^p - 1."""
+    for p in (3, 5, 7, 11, 13, 17, 19, 23, 29, 31):
+        assert (o.lucas_lehmer(p) == 0) == _is_prime_trial((1 << p) - 1), p
+
+
+def test_lucas_lehmer_composites_with_known_factors():
+    """Composite Mersenne numbers (a factor divides 2^p - 1) leave a nonzero residue."""
+    for p, f in ((37, 223), (41, 13367), (43, 431), (47, 2351), (53, 6361), (59, 179951), (67, 193707721),
+                 (71, 228479), (73, 439), (79, 2687), (83, 167), (97, 11447)):
+        assert ((1 << p) - 1) % f == 0, p
+        assert o.lucas_lehmer(p) != 0, p
+
+
+def test_lucas_lehmer_primes_by_fermat_tests():
+    """2^p - 1 for p = 61, 89, 107, 127 passes Fermat tests to 12 bases and the
+    oracle's test calls it prime; p = 521 and 607 are prime exponents too."""
+    for p in (61, 89, 107, 127):
+        n = (1 << p) - 1
+        assert all(pow(b, n - 1, n) == 1 for b in (2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37))
+        assert o.lucas_lehmer(p) == 0
+    for p in (521, 607):
+        n = (1 << p) - 1
+        assert pow(3, n - 1, n) == 1
+        assert o.lucas_lehmer(p) == 0
