@@ -117,3 +117,19 @@ def test_rings_take_the_evaluation_map_form(dk):
     assert consts["rmul"] == 0 and consts["prescale"] == 1
     _, consts = dk.plan_rho(*syn.workload_params("dkss_2p24b"))
     assert consts["prescale"] == 0
+
+
+def test_square_and_lucas_lehmer_argument_errors(dk):
+    """dkss_sqr and dkss_ll_step reject bad arguments on the host, before any
+    launch (DKSS_EINVAL = 1)."""
+    lib = dk.load()
+    buf = (ctypes.c_uint64 * 64)()
+    base = ctypes.addressof(buf)
+    assert lib.dkss_sqr(None, base, base + 256, None) == 1            # no plan
+    assert lib.dkss_ll_step(None, base, 127, None) == 1               # no c
+    assert lib.dkss_ll_step(base, None, 127, None) == 1               # no s
+    for p in (0, 1, 2, 1 << 26):                                      # p out of range
+        assert lib.dkss_ll_step(base, base + 256, p, None) == 1
+    # s overlapping c: c holds 2 ceil(p/64) words, s ceil(p/64)
+    assert lib.dkss_ll_step(base, base + 8, 127, None) == 1
+    assert lib.dkss_ll_step(base + 16, base + 8, 127, None) == 1
