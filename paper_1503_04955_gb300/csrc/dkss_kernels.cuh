@@ -718,7 +718,8 @@ constexpr size_t level_ntt_smem_bytes() {
 // Last level of both forward transforms, componentwise products scaled by
 // (2M)^-1 (Section 3.2.6), and the first level of the backwards transform,
 // fused.  One CTA per block of n = len contiguous elements (len <= 2m, root
-// alpha^(2m/len)).
+// alpha^(2m/len)).  For a square the caller passes poly_words = 0 (b is a) and
+// square = 1: the NTT form then reuses a's evaluations for both factors.
 // ---------------------------------------------------------------------------
 template <int m, int L, int LR, int FORM>
 __device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>& md, const ModRR<LR>& mr,
