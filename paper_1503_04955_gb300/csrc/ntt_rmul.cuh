@@ -64,14 +64,14 @@ __device__ __forceinline__ void ldg_rr(uint32_t (&x)[LR], const uint32_t* p) {
 
 // r = a + b, limbwise
 template <int LR>
-__device__ __forceinline__ void lz_add(uint32_t (&r)[LR], const uint32_t (&a)[LR], const uint32_t (&b)[LR]) {
+DKSS_HD void lz_add(uint32_t (&r)[LR], const uint32_t (&a)[LR], const uint32_t (&b)[LR]) {
 #pragma unroll
     for (int i = 0; i < LR; ++i) r[i] = a[i] + b[i];
 }
 
 // r = a + B - b, limbwise (B[i] >= b[i] for every i)
 template <int LR>
-__device__ __forceinline__ void lz_sub(uint32_t (&r)[LR], const uint32_t (&a)[LR], const uint32_t (&B)[LR],
+DKSS_HD void lz_sub(uint32_t (&r)[LR], const uint32_t (&a)[LR], const uint32_t (&B)[LR],
                                        const uint32_t (&b)[LR]) {
 #pragma unroll
     for (int i = 0; i < LR; ++i) r[i] = a[i] + B[i] - b[i];
@@ -80,7 +80,7 @@ __device__ __forceinline__ void lz_sub(uint32_t (&r)[LR], const uint32_t (&a)[LR
 // Montgomery product a b 2^(-26 LR) mod q as normalised limbs of a value
 // below a b / R' + q (the top limb holds every bit above 26 (LR - 1)).
 template <int LR>
-__device__ __forceinline__ void mmul(uint32_t (&r)[LR], const uint32_t (&a)[LR], const uint32_t (&b)[LR],
+DKSS_HD void mmul(uint32_t (&r)[LR], const uint32_t (&a)[LR], const uint32_t (&b)[LR],
                                      const ModRR<LR>& md) {
     uint64_t col[2 * LR];
 #pragma unroll
@@ -105,7 +105,7 @@ __device__ __forceinline__ void mmul(uint32_t (&r)[LR], const uint32_t (&a)[LR],
 
 // canonical residue of normalised limbs of a value below 2q
 template <int LR>
-__device__ __forceinline__ void canon(uint32_t (&r)[LR], const uint32_t (&x)[LR], const ModRR<LR>& md) {
+DKSS_HD void canon(uint32_t (&r)[LR], const uint32_t (&x)[LR], const ModRR<LR>& md) {
     uint32_t d[LR], borrow = 0;
 #pragma unroll
     for (int i = 0; i < LR; ++i) {
@@ -119,7 +119,7 @@ __device__ __forceinline__ void canon(uint32_t (&r)[LR], const uint32_t (&x)[LR]
 
 // carry-propagate limbs (each below 2^32) to 26 bits; the top limb keeps the rest
 template <int LR>
-__device__ __forceinline__ void lz_norm(uint32_t (&x)[LR]) {
+DKSS_HD void lz_norm(uint32_t (&x)[LR]) {
     uint32_t carry = 0;
 #pragma unroll
     for (int i = 0; i + 1 < LR; ++i) {

@@ -16,6 +16,10 @@ namespace dkss {
 
 constexpr uint32_t kM26 = (1u << 26) - 1;
 
+// the limb arithmetic below is plain integer code: also callable on the host,
+// where the CPU tests check it against exact integers
+#define DKSS_HD __host__ __device__ __forceinline__
+
 template <int LR>
 struct ModRR {
     uint32_t q[LR];    // p^z in 26-bit limbs
@@ -24,7 +28,7 @@ struct ModRR {
 
 // 32-bit limbs -> 26-bit limbs (x < 2^(26 LR))
 template <int L, int LR>
-__device__ __forceinline__ void to_rr(uint32_t (&out)[LR], const uint32_t (&x)[L]) {
+DKSS_HD void to_rr(uint32_t (&out)[LR], const uint32_t (&x)[L]) {
 #pragma unroll
     for (int i = 0; i < LR; ++i) {
         const int bit = 26 * i, w = bit >> 5, s = bit & 31;
@@ -36,7 +40,7 @@ __device__ __forceinline__ void to_rr(uint32_t (&out)[LR], const uint32_t (&x)[L
 
 // 26-bit limbs -> 32-bit limbs (value < 2^(32 L))
 template <int L, int LR>
-__device__ __forceinline__ void from_rr(uint32_t (&out)[L], const uint32_t (&r)[LR]) {
+DKSS_HD void from_rr(uint32_t (&out)[L], const uint32_t (&r)[LR]) {
 #pragma unroll
     for (int w = 0; w < L; ++w) out[w] = 0;
 #pragma unroll
@@ -49,7 +53,7 @@ __device__ __forceinline__ void from_rr(uint32_t (&out)[L], const uint32_t (&r)[
 
 // r = (q - y) mod q in 26-bit limbs
 template <int LR>
-__device__ __forceinline__ void neg_rr(uint32_t (&r)[LR], const uint32_t (&y)[LR], const ModRR<LR>& md) {
+DKSS_HD void neg_rr(uint32_t (&r)[LR], const uint32_t (&y)[LR], const ModRR<LR>& md) {
     uint32_t nz = 0, borrow = 0;
 #pragma unroll
     for (int i = 0; i < LR; ++i) {
@@ -64,7 +68,7 @@ __device__ __forceinline__ void neg_rr(uint32_t (&r)[LR], const uint32_t (&y)[LR
 
 // col[a+b] += x_a * y_b
 template <int LR>
-__device__ __forceinline__ void mac_cols(uint64_t (&col)[2 * LR], const uint32_t (&x)[LR], const uint32_t (&y)[LR]) {
+DKSS_HD void mac_cols(uint64_t (&col)[2 * LR], const uint32_t (&x)[LR], const uint32_t (&y)[LR]) {
 #pragma unroll
     for (int a = 0; a < LR; ++a)
 #pragma unroll
@@ -74,7 +78,7 @@ __device__ __forceinline__ void mac_cols(uint64_t (&col)[2 * LR], const uint32_t
 // Montgomery reduction of the column sum T = sum_t col[t] 2^(26t):
 // r = T * 2^(-26 LR) mod q, canonical, for T < q * 2^(26 LR).
 template <int LR>
-__device__ __forceinline__ void redc_cols(uint32_t (&r)[LR], uint64_t (&col)[2 * LR], const ModRR<LR>& md) {
+DKSS_HD void redc_cols(uint32_t (&r)[LR], uint64_t (&col)[2 * LR], const ModRR<LR>& md) {
 #pragma unroll
     for (int i = 0; i < LR; ++i) {
         const uint32_t d = (uint32_t)col[i] & kM26;
@@ -109,7 +113,7 @@ __device__ __forceinline__ void redc_cols(uint32_t (&r)[LR], uint64_t (&col)[2 *
 
 // r = a * b * 2^(-26 LR) mod q
 template <int LR>
-__device__ __forceinline__ void mont_mul_rr(uint32_t (&r)[LR], const uint32_t (&a)[LR], const uint32_t (&b)[LR],
+DKSS_HD void mont_mul_rr(uint32_t (&r)[LR], const uint32_t (&a)[LR], const uint32_t (&b)[LR],
                                             const ModRR<LR>& md) {
     uint64_t col[2 * LR];
 #pragma unroll
