@@ -110,7 +110,7 @@ def lucas_lehmer_gpu(dk, p):
         return syn.to_int(to_host(s))
 
 
-@pytest.mark.parametrize("p", [521, 607, 1279, 2203, 2281])
+@pytest.mark.parametrize("p", [521, 607, 1279, 2203, 2281, 3217, 4253, 4423])
 def test_lucas_lehmer_mersenne_primes(dk, p):
     assert lucas_lehmer_gpu(dk, p) == 0
 

@@ -127,6 +127,10 @@ def test_rho_invariants(cfg):
     for i in range(1, 2 * m, 2):
         gi = pow(r.gamma, i, q)
         assert sum(c * pow(gi, k, q) for k, c in enumerate(r.rho)) % q == pow(r.omega, i, q)
+    # the interpolation divides by gamma^i - gamma^j (i != j odd): units of P,
+    # i.e. not divisible by p (Section 3.2.3)
+    pts = [pow(r.gamma, i, q) for i in range(1, 2 * m, 2)]
+    assert all((x - y) % par.p != 0 for a, x in enumerate(pts) for y in pts[:a])
 
 
 @pytest.mark.parametrize("cfg", TINY[:3])
