@@ -334,6 +334,20 @@ dkss_status dkss_mlp_grad(const float* params, const float* x, const float* t, s
 dkss_status dkss_mlp_adam(float* params, const float* grad, float* m1, float* m2, float lr, uint32_t step,
                           dkss_stream_t stream);
 
+/*
+ * Host-side fault injection for tests (the thesis has no counterpart).  mask
+ * is process-wide and 0 by default; set it only while no other thread plans.
+ *   DKSS_FAULT_RHO        plan math perturbs one coefficient of rho before it
+ *                         checks rho^(2M/2m) = alpha and rho^M = -1 (Section
+ *                         3.2.3), which must then reject it: dkss_plan and
+ *                         dkss_plan_rho return DKSS_EPARAM.
+ *   DKSS_FAULT_HOST_ALLOC dkss_plan's host allocation fails: it returns
+ *                         DKSS_ENOMEM and sets *plan to NULL.
+ * Nothing here touches a GPU.  Returns the previous mask.
+ */
+enum { DKSS_FAULT_RHO = 1, DKSS_FAULT_HOST_ALLOC = 2 };
+uint32_t dkss_fault_inject(uint32_t mask);
+
 /* Kernel launches one dkss_mul call queues (for launch accounting). */
 uint32_t dkss_plan_launches(dkss_plan_t plan);
 

@@ -24,7 +24,8 @@ FORM_INT8TC = 2
 EXPORTS = ["dkss_plan", "dkss_mul", "dkss_sqr", "dkss_ll_step", "dkss_mul_host", "dkss_forward", "dkss_mul_batch",
            "dkss_plan_info", "dkss_plan_rho", "dkss_profile_read", "dkss_plan_launches", "dkss_sync_status", "dkss_plan_destroy",
            "dkss_status_str", "dkss_decode_static", "dkss_batch_plan", "dkss_batch_run", "dkss_batch_job_params",
-           "dkss_batch_destroy", "dkss_plan_candidates", "dkss_mlp_forward", "dkss_mlp_grad", "dkss_mlp_adam"]
+           "dkss_batch_destroy", "dkss_plan_candidates", "dkss_mlp_forward", "dkss_mlp_grad", "dkss_mlp_adam",
+           "dkss_fault_inject"]
 FORM_PROFILE = 4
 RMUL_DIRECT = 16
 LEVELS_EVAL = 128
@@ -73,6 +74,8 @@ def load():
     for f in (lib.dkss_mlp_forward, lib.dkss_mlp_grad, lib.dkss_mlp_adam):
         f.restype = ctypes.c_int
     lib.dkss_decode_static.restype = ctypes.c_int
+    lib.dkss_fault_inject.argtypes = [u32]
+    lib.dkss_fault_inject.restype = u32
     lib.dkss_plan_launches.argtypes = [P]
     lib.dkss_plan_launches.restype = u32
     lib.dkss_sync_status.argtypes = [P, P]

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <new>
 #include <thread>
@@ -12,6 +13,9 @@
 using dkss_host::MontCtx;
 using dkss_host::Relem;
 using dkss_host::u128;
+
+// test hook: DKSS_FAULT_* bits set by dkss_fault_inject (0 in normal use)
+static std::atomic<uint32_t> g_fault{0};
 
 namespace dkss_planning {
 
@@ -170,6 +174,7 @@ dkss_status plan_host(dkss_plan_s* pl, uint64_t n_bits, uint64_t M, uint32_t m, 
     r.omega = c.from(omega_m);
     r.gamma = c.from(gamma_m);
     Relem rho_m = dkss_host::rho_lagrange(c, omega_m, gamma_m, m, phi - 1);
+    if (g_fault.load() & DKSS_FAULT_RHO) rho_m[1] = c.add(rho_m[1], c.r1);   // test hook: the checks must fail
     // checks the thesis fixes: rho^(2M/2m) = alpha, rho^M = -1
     Relem t1 = dkss_host::r_pow(c, rho_m, pl->mu_top);
     Relem t2 = dkss_host::r_pow(c, rho_m, M);
@@ -412,11 +417,13 @@ void fill_consts(const dkss_plan_s* pl, uint64_t* consts, size_t n) {
 
 extern "C" {
 
+uint32_t dkss_fault_inject(uint32_t mask) { return g_fault.exchange(mask); }
+
 dkss_status dkss_plan(dkss_plan_t* plan, uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, uint64_t p, uint32_t z,
                       uint32_t flags) {
     if (!plan) return DKSS_EINVAL;
     *plan = nullptr;
-    dkss_plan_s* pl = new (std::nothrow) dkss_plan_s;
+    dkss_plan_s* pl = (g_fault.load() & DKSS_FAULT_HOST_ALLOC) ? nullptr : new (std::nothrow) dkss_plan_s;
     if (!pl) return DKSS_ENOMEM;
     pl->flags = flags;
     dkss_status s = plan_host(pl, n_bits, M, m, u, p, z);

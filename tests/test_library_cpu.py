@@ -133,3 +133,35 @@ def test_square_and_lucas_lehmer_argument_errors(dk):
     # s overlapping c: c holds 2 ceil(p/64) words, s ceil(p/64)
     assert lib.dkss_ll_step(base, base + 8, 127, None) == 1
     assert lib.dkss_ll_step(base + 16, base + 8, 127, None) == 1
+
+
+def test_fault_injection_wrong_rho_is_rejected(dk):
+    """A perturbed rho fails the plan's checks rho^(2M/2m) = alpha and rho^M = -1
+    (Section 3.2.3): DKSS_EPARAM; without the fault the same plan is fine."""
+    lib = dk.load()
+    cfg = syn.workload_params("dkss_65536b")
+    old = lib.dkss_fault_inject(1)
+    try:
+        with pytest.raises(dk.DkssError) as e:
+            dk.plan_rho(*cfg)
+        assert e.value.code == 2
+        plan = ctypes.c_void_p()
+        assert lib.dkss_plan(ctypes.byref(plan), *cfg, 0) == 2 and plan.value is None
+    finally:
+        lib.dkss_fault_inject(old)
+    rho, consts = dk.plan_rho(*cfg)
+    assert rho == o.compute_roots(o.Params(*cfg).check()).rho
+
+
+def test_fault_injection_host_allocation(dk):
+    """dkss_plan's host allocation fails: DKSS_ENOMEM, *plan set to NULL."""
+    lib = dk.load()
+    cfg = syn.workload_params("dkss_65536b")
+    plan = ctypes.c_void_p(1)
+    old = lib.dkss_fault_inject(2)
+    try:
+        assert lib.dkss_plan(ctypes.byref(plan), *cfg, 0) == 3
+        assert plan.value is None
+    finally:
+        lib.dkss_fault_inject(old)
+    assert lib.dkss_fault_inject(0) == 0
