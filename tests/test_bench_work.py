@@ -1,0 +1,75 @@
+"""The algorithmic work counts behind bench.py's rooflines, checked by
+enumeration on small transforms (CPU).
+
+A bad twiddle of level d multiplies element (v, l) of a block by
+rho^(v l (2m)^d); it is work unless v l = 0 (Section 3.2.5 ii.).  A radix-2
+decimation-in-time DFT of n points multiplies by a power of its root in every
+butterfly; those with exponent 0 are products by 1 and not work.
+"""
+import pytest
+
+import bench
+
+
+def enumerate_nontrivial(P2, m, levels):
+    """Bad twiddles with exponent != 0, by level, counted element by element."""
+    out, length = [], P2
+    for d in range(levels - 1):
+        mu_d = length // (2 * m)
+        bp = (2 * m) ** d
+        n = 0
+        for blk in range(P2 // length):
+            for v in range(2 * m):
+                for l in range(mu_d):
+                    if (v * l * bp) % P2 != 0:
+                        n += 1
+        out.append(n)
+        length //= 2 * m
+    return out
+
+
+def enumerate_dit_products(n):
+    """Butterflies of an n-point radix-2 DIT whose twiddle exponent is not 0."""
+    count, half = 0, 1
+    while half < n:
+        scale = n // (2 * half)
+        for start in range(0, n, 2 * half):
+            for k in range(half):
+                if (k * scale) % n != 0:
+                    count += 1
+        half *= 2
+    return count
+
+
+@pytest.mark.parametrize("P2,m", [(64, 4), (256, 4), (512, 8), (2048, 16), (4096, 32)])
+def test_nontrivial_twiddles_match_enumeration(P2, m):
+    levels = 1
+    while P2 // (2 * m) ** (levels - 1) > 2 * m:
+        levels += 1
+    info = {"P2": P2, "L": 3, "levels": levels, "pz": (1 << 80) + 1}
+    brute = enumerate_nontrivial(P2, m, levels)
+    r = bench.rmul_imads(m, 3, "ntt")
+    work = bench.stage_work(info, m, "ntt")
+    assert work["fwd_twiddle"] == (2 * sum(brute) * r, levels - 1)
+    assert work["inv_twiddle"] == (sum(brute) * r, levels - 1)
+    rd = bench.rmul_imads(m, 3, "direct")
+    assert bench.stage_work(info, m, "direct")["fwd_twiddle"][0] == 2 * sum(brute) * rd
+    S = 11
+    assert bench.stage_work_i8(info, m)["fwd_twiddle"][0] == 2 * sum(brute) * 2 * S * S * m * m
+
+
+@pytest.mark.parametrize("n", [2, 4, 8, 16, 32, 64, 128])
+def test_dit_products_match_enumeration(n):
+    assert bench.nontrivial_dft_products(n) == enumerate_dit_products(n)
+
+
+def test_montgomery_product_count():
+    """A Montgomery product of L-limb residues: L^2 limb products (lo and hi
+    halves each) and L(L+1) for the reduction's digits and q multiples,
+    2 L^2 + L (2L + 1) 32-bit multiply-adds."""
+    for L in (2, 3, 4, 5):
+        limb_products = 2 * L * L
+        reduction = L + 2 * L * L
+        assert bench.modmul_imads(L) == limb_products + reduction
+    # the NTT form's R-multiplication at m = 32: 80 + 32 + 96 = 208 products
+    assert bench.rmul_imads(32, 4, "ntt") == 208 * bench.modmul_imads(4)
