@@ -7,11 +7,17 @@
 //   <op> <LR> <nprime> q[0..LR) x[0..LR) y[0..LR)
 // op: mont (mont_mul_rr), mmul (lazy Montgomery product), canon, norm
 // (lz_norm of x), neg (neg_rr of x), rt<L> (to_rr then from_rr of the L
-// words x[0..L), LR = limbs).  One output line per request: the result words.
+// words x[0..L), LR = limbs).  And the Lucas-Lehmer reduction of
+// csrc/mersenne.cuh:
+//   ll <p> c[0..2w)   (w = ceil(p/64), decimal 64-bit words)
+// One output line per request: the result words.
+#include <cinttypes>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <vector>
 
+#include "../../paper_1503_04955_gb300/csrc/mersenne.cuh"
 #include "../../paper_1503_04955_gb300/csrc/ntt_rmul.cuh"
 
 namespace {
@@ -76,7 +82,19 @@ int main() {
     char op[16];
     int LR;
     unsigned nprime;
-    while (std::scanf("%15s %d %u", op, &LR, &nprime) == 3) {
+    while (std::scanf("%15s", op) == 1) {
+        if (!std::strcmp(op, "ll")) {
+            unsigned p;
+            if (std::scanf("%u", &p) != 1 || p < 3) return 4;
+            const uint32_t w = (p + 63) / 64;
+            std::vector<uint64_t> c(2 * w), s(w);
+            for (uint32_t i = 0; i < 2 * w; ++i)
+                if (std::scanf("%" SCNu64, &c[i]) != 1) return 4;
+            dkss::ll_fold(c.data(), s.data(), p, w);
+            for (uint32_t i = 0; i < w; ++i) std::printf("%" PRIu64 "%s", s[i], i + 1 < w ? " " : "\n");
+            continue;
+        }
+        if (std::scanf("%d %u", &LR, &nprime) != 2) return 3;
         uint32_t q[5] = {0}, x[5] = {0}, y[5] = {0};
         if (LR < 2 || LR > 5) return 2;
         for (int i = 0; i < LR; ++i) if (std::scanf("%u", &q[i]) != 1) return 3;

@@ -141,3 +141,23 @@ def test_word_limb_round_trip(driver, L, LR):
         rr, back = g[:LR], g[LR:]
         assert value(rr) == v and all(x <= M26 for x in rr)
         assert back == words
+
+
+def test_lucas_lehmer_fold(driver):
+    """The reduction of dkss_ll_step (csrc/mersenne.cuh) on the host:
+    s = (c - 2) mod (2^p - 1) for c < 2^(2p), including c = 0, 1, 2, M_p,
+    M_p^2, 2^(2p) - 1 and word-boundary exponents."""
+    rng = random.Random(5)
+    lines, want = [], []
+    for p in list(range(3, 200)) + [521, 607, 1277, 1279, 2203, 4423]:
+        mp = (1 << p) - 1
+        w = (p + 63) // 64
+        cases = [0, 1, 2, 3, mp - 1, mp, mp + 1, 2 * mp, mp * mp, (1 << (2 * p)) - 1, 1 << p, (1 << p) + 1]
+        cases += [rng.getrandbits(2 * p) for _ in range(12)] + [rng.randrange(mp) ** 2 for _ in range(4)]
+        for c in cases:
+            words = [(c >> (64 * i)) & ((1 << 64) - 1) for i in range(2 * w)]
+            lines.append("ll %d %s\n" % (p, " ".join(str(x) for x in words)))
+            want.append((c - 2) % mp)
+    r = subprocess.run([driver], input="".join(lines), capture_output=True, text=True, check=True)
+    got = [sum(int(t) << (64 * i) for i, t in enumerate(line.split())) for line in r.stdout.strip().split("\n")]
+    assert got == want
