@@ -80,6 +80,10 @@ def test_plan_roots_match_oracle(dk, cfg):
     (1 << 16, 8, 16, 16, 12289, 4),       # M < m
     (1 << 20, 512, 16, 16, 12289, 4),     # M (m/2) u < N
     (1 << 16, 512, 16, 0, 12289, 4),      # u = 0
+    (1 << 16, 512, 16, 33, 12289, 4),     # u above 32
+    (0, 512, 16, 16, 12289, 4),           # empty operands
+    (1 << 16, 512, 16, 16, 12289, 0),     # z = 0
+    (1 << 16, 512, 1, 16, 12289, 4),      # m < 2
 ])
 def test_plan_rejects_invalid_parameters(dk, bad):
     with pytest.raises(dk.DkssError) as e:
