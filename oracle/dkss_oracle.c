@@ -20,10 +20,21 @@
  * Pins: tests/test_oracle_pins.py checks this file against the Python oracle
  * on small parameter sets, against brute-force DFTs and against exact integer
  * products (Python int and schoolbook) on every size it runs.
+ *
+ * Threads: when built with OpenMP, the loops whose iterations the thesis's
+ * steps leave independent run on several host threads -- the inner DFTs of
+ * the columns (step i.), the bad multiplications (step ii.), the outer DFTs of
+ * the rows (step iii., top level only; deeper levels run inside one thread),
+ * encoding, the componentwise products and the scaling.  Every iteration
+ * writes its own outputs, so the result does not depend on the thread count;
+ * oracle_set_threads() picks it (1 = the plain serial program).
  */
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef unsigned __int128 u128;
 
@@ -152,31 +163,40 @@ static void dkss_fft(u128* a, uint64_t n, uint64_t base_pow, const u128* table, 
     }
     uint64_t mu_n = n / two_m;
     u128* abar = malloc(sizeof(u128) * m * n);   /* row v, column l at (v*mu_n + l) */
-    u128* el = malloc(sizeof(u128) * m * two_m);
     /* i. inner DFTs of the columns e_l(y) = sum_j a_{j mu + l} y^j */
-    for (uint64_t l = 0; l < mu_n; l++) {
-        for (uint32_t j = 0; j < two_m; j++)
-            memcpy(el + j * m, a + (j * mu_n + l) * m, sizeof(u128) * m);
-        alpha_dft(el, two_m, 1, par);
-        for (uint32_t v = 0; v < two_m; v++)
-            memcpy(abar + (v * mu_n + l) * m, el + v * m, sizeof(u128) * m);
+#pragma omp parallel
+    {
+        u128* el = malloc(sizeof(u128) * m * two_m);
+#pragma omp for schedule(static)
+        for (int64_t li = 0; li < (int64_t)mu_n; li++) {
+            uint64_t l = (uint64_t)li;
+            for (uint32_t j = 0; j < two_m; j++)
+                memcpy(el + j * m, a + (j * mu_n + l) * m, sizeof(u128) * m);
+            alpha_dft(el, two_m, 1, par);
+            for (uint32_t v = 0; v < two_m; v++)
+                memcpy(abar + (v * mu_n + l) * m, el + v * m, sizeof(u128) * m);
+        }
+        free(el);
     }
     /* ii. bad multiplications abar_{v,l} *= rho^(v l base_pow) */
-    u128 tw[64];
-    for (uint32_t v = 0; v < two_m; v++)
-        for (uint64_t l = 1; l < mu_n; l++) {
-            u128* x = abar + (v * mu_n + l) * m;
-            rho_power(tw, (uint64_t)v * l * base_pow, table, par);
-            r_mul(x, x, tw, par);
-        }
+#pragma omp parallel for schedule(static)
+    for (int64_t vl = 0; vl < (int64_t)(two_m * mu_n); vl++) {
+        uint64_t v = (uint64_t)vl / mu_n, l = (uint64_t)vl % mu_n;
+        if (l == 0) continue;
+        u128 tw[64];
+        u128* x = abar + (v * mu_n + l) * m;
+        rho_power(tw, v * l * base_pow, table, par);
+        r_mul(x, x, tw, par);
+    }
     /* iii. outer DFTs of the rows, root rho^(2m base_pow); output f -> 2m f + v */
-    for (uint32_t v = 0; v < two_m; v++) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int32_t vi = 0; vi < (int32_t)two_m; vi++) {
+        uint32_t v = (uint32_t)vi;
         u128* row = abar + v * mu_n * m;
         dkss_fft(row, mu_n, base_pow * two_m, table, par);
         for (uint64_t f = 0; f < mu_n; f++)
             memcpy(a + (two_m * f + v) * m, row + f * m, sizeof(u128) * m);
     }
-    free(el);
     free(abar);
 }
 
@@ -193,6 +213,7 @@ static uint64_t get_bits(const uint64_t* a, uint64_t n_words, uint64_t pos, uint
 
 static void encode(u128* out, const uint64_t* a, uint64_t n_words, const par_t* par) {
     memset(out, 0, sizeof(u128) * par->m * par->P2);
+#pragma omp parallel for schedule(static)
     for (uint64_t i = 0; i < par->M; i++)
         for (uint32_t t = 0; t < par->h; t++)
             out[i * par->m + t] = get_bits(a, n_words, (uint64_t)par->u * (i * par->h + t), par->u);
@@ -243,6 +264,18 @@ static u128* build_table(const u128* rho, const par_t* par) {
     return table;
 }
 
+/* Host threads for the loops above (OpenMP builds); returns the count in
+ * effect, 1 when the library was built without OpenMP. */
+int oracle_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 /* Negacyclic product of two elements of R (m residues of 2 words each). */
 int oracle_r_mul(uint32_t m, const uint64_t pz[2], const uint64_t* x, const uint64_t* y, uint64_t* out) {
     par_t par;
@@ -291,6 +324,7 @@ int oracle_dkss_mul(uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, const u
     dkss_fft(eb, par.P2, 1, table, &par);
     if (a_hat) store_r(a_hat, ea, len);
     if (b_hat) store_r(b_hat, eb, len);
+#pragma omp parallel for schedule(static)
     for (uint64_t i = 0; i < par.P2; i++) r_mul(ea + i * m, ea + i * m, eb + i * m, &par);
     if (c_hat) store_r(c_hat, ea, len);
     dkss_fft(ea, par.P2, 1, table, &par);
@@ -307,6 +341,7 @@ int oracle_dkss_mul(uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, const u
         inv = (u128)(t0 < 0 ? t0 + (__int128)par.q : t0);
     }
     memset(eb, 0, sizeof(u128) * len);
+#pragma omp parallel for schedule(static)
     for (uint64_t l = 0; l < par.P2; l++) {
         uint64_t src = (par.P2 - l) % par.P2;
         for (uint32_t t = 0; t < m; t++) {

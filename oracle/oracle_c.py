@@ -19,11 +19,16 @@ _lib = None
 
 
 def build(force=False):
-    """Compile the oracle's C part (plain -O2, no target-specific flags)."""
+    """Compile the oracle's C part (plain -O2, no target-specific flags), with
+    OpenMP over its independent loops when the compiler supports it."""
     os.makedirs(BUILD_DIR, exist_ok=True)
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
         tmp = LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-shared", "-fPIC", "-std=c11", SRC, "-o", tmp])
+        base = ["gcc", "-O2", "-shared", "-fPIC", "-std=c11", SRC, "-o", tmp]
+        try:
+            subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, LIB)
     return LIB
 
@@ -41,7 +46,9 @@ def load():
                                         u64p, u64p, u64p, u64p]
         lib.oracle_fft_alpha_point.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
                                                ctypes.c_uint32, u64p, u64p, ctypes.c_uint64, u64p]
-        for f in (lib.oracle_r_mul, lib.oracle_fft, lib.oracle_dkss_mul, lib.oracle_fft_alpha_point):
+        lib.oracle_set_threads.argtypes = [ctypes.c_int]
+        for f in (lib.oracle_r_mul, lib.oracle_fft, lib.oracle_dkss_mul, lib.oracle_fft_alpha_point,
+                  lib.oracle_set_threads):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -69,6 +76,12 @@ def from_words2(flat):
     return [l | (h << 64) for l, h in zip(lo, hi)]
 
 
+def set_threads(n):
+    """Host threads of the oracle's parallel loops (0: leave as is); returns
+    the count in effect (1 without OpenMP)."""
+    return load().oracle_set_threads(int(n))
+
+
 def r_mul(x, y, pz):
     lib = load()
     m = len(x)
@@ -89,10 +102,14 @@ def fft(a_elems, M, m, pz, rho):
     return [vals[i * m:(i + 1) * m] for i in range(2 * M)]
 
 
+DUMP_NAMES = ("a_hat", "b_hat", "c_hat", "c")
+
+
 def dkss_mul(a_limbs, b_limbs, par, rho, dumps=False):
     """c = a*b with the C oracle.  a_limbs, b_limbs: uint64 arrays of
     ceil(N/64) limbs.  Returns (c_limbs, dumps) where dumps maps 'a_hat',
-    'b_hat', 'c_hat', 'c' to uint64 arrays of shape (2M, m, 2) or is None."""
+    'b_hat', 'c_hat', 'c' to uint64 arrays of shape (2M, m, 2) or is None.
+    dumps may also be a collection of those names (only they are kept)."""
     lib = load()
     nw = (par.n_bits + 63) // 64
     a = np.ascontiguousarray(a_limbs, dtype=np.uint64)
@@ -100,11 +117,11 @@ def dkss_mul(a_limbs, b_limbs, par, rho, dumps=False):
     assert a.size == nw and b.size == nw
     c = np.zeros(2 * nw, dtype=np.uint64)
     shape = (par.P2, par.m, 2)
-    d = {k: np.zeros(shape, dtype=np.uint64) for k in ("a_hat", "b_hat", "c_hat", "c")} if dumps else None
+    names = DUMP_NAMES if dumps is True else tuple(dumps) if dumps else ()
+    d = {k: np.zeros(shape, dtype=np.uint64) for k in names} if names else None
     rc = lib.oracle_dkss_mul(par.n_bits, par.M, par.m, par.u, _ptr(words2([par.pz])),
                              _ptr(words2(rho)), _ptr(a), _ptr(b), _ptr(c),
-                             _ptr(d["a_hat"]) if d else None, _ptr(d["b_hat"]) if d else None,
-                             _ptr(d["c_hat"]) if d else None, _ptr(d["c"]) if d else None)
+                             *[_ptr(d[k]) if d and k in d else None for k in DUMP_NAMES])
     assert rc == 0
     return c, d
 
