@@ -1,25 +1,33 @@
 #!/usr/bin/env python3
 """Throughput of the DKSS_MUL hot path on GB300; prints one JSON line.
 
-A step is one full product c = a*b of the 2^24-bit workload (M = 2^15,
-m = 32, u = 32, p = 65537, z = 6): encode, forward transforms of both
-operands, componentwise products, backwards transform, decode and carry scan,
-all in libdkss's CUDA kernels.  Operands are seeded uniform random integers.
+A step is one full product c = a*b of the 2^32-bit workload (M = 2^22,
+m = 64, u = 32, p = 998244353, z = 4; the largest single-GPU workload):
+encode, forward transforms of both operands, componentwise products,
+backwards transform, decode and carry scan, all in libdkss's CUDA kernels.
+Operands are seeded uniform random integers (--workload picks another size).
 
 value      operand Gbit/s = 2N bits per product / device time per product
-           (CUDA events on the launching stream; L2 flushed between steps
-           by writing a 256 MiB buffer outside the timed events).
+           (CUDA events on the launching stream; the transformed polynomials
+           are 8 GiB each, far larger than L2, which is also flushed between
+           steps by writing a 256 MiB buffer outside the timed events).
 e2e        the same metric through dkss_mul_host (pinned host buffers,
            host->device copies of a and b and device->host copy of c inside
            the timed region).
 roofline   the kernel group with the most device time, timed live with the
            library's per-stage CUDA events over the timed steps.
-cpu_baseline  the CPU oracle (oracle/dkss_oracle.c, single thread) on one full
-           product of the same workload.
+forms      the same product with every R-multiplication form (IMAD forms and
+           the INT8 tensor-core form) and the TC-vs-IMAD ratios.
+workloads  the other single-product workloads (65,536, 2^24 and 2^28 bits),
+           each with its own form comparison.
+batched    the 4096-product batch (one persistent kernel from a CUDA graph)
+           against plain per-product launches.
+cpu_baseline  the CPU oracle (oracle/dkss_oracle.c) on all host cores and on
+           one, on a bounded sample of the workload (oracle_sample).
 
---impl reference times that oracle alone on the host cores, same metric.
-With torchrun (N > 1) every rank multiplies its own pair on its own GPU
-(independent replicas; the product itself is not sharded).
+--impl reference times that oracle alone on the host cores, same metric and
+sample.  With torchrun (N > 1) every rank multiplies its own pair on its own
+GPU (independent replicas; the product itself is not sharded).
 """
 import argparse
 import json
@@ -40,7 +48,7 @@ import numpy as np  # noqa: E402
 import dkss_synth as syn  # noqa: E402
 
 METRIC = "DKSS_MUL operand Gbit/s and batched products/s on 1 GB300, bit-exact; TC vs IMAD"
-WORKLOAD = "dkss_2p24b"
+WORKLOAD = "dkss_2p32b"
 L2_FLUSH_BYTES = 256 << 20
 SM_COUNT_GB300 = 152
 IMAD_PER_SM_PER_CLK = 64          # 32-bit integer multiply-add lanes per SM per clock
@@ -57,8 +65,8 @@ NCU_TRAFFIC_BYTES = {("dkss_2p24b", "ntt", "fwd_twiddle"): 46.6e6,
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(syn.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -66,7 +74,10 @@ def parse_args():
     ap.add_argument("--no-batched", action="store_true", help="skip the 4096-product batched workload")
     ap.add_argument("--batched-steps", type=int, default=10)
     ap.add_argument("--no-forms", action="store_true", help="skip the R-multiplication form comparison")
-    ap.add_argument("--form-steps", type=int, default=20)
+    ap.add_argument("--form-budget-ms", type=float, default=4000.0,
+                    help="device time per form and workload in the form comparison")
+    ap.add_argument("--no-others", action="store_true", help="skip the other single-product workloads")
+    ap.add_argument("--other-budget-ms", type=float, default=1000.0)
     ap.add_argument("--form", default="ntt", choices=["ntt", "eval", "direct", "int8tc"],
                     help="alpha-shift inner DFTs with R-multiplications through the evaluation map of R (ntt, the "
                          "default), inner levels in evaluation coordinates (eval), the direct convolution, or "
@@ -252,14 +263,68 @@ def stage_work(info, m, form):
 
 # ----------------------------------------------------------------- ours ----
 
-def check_product(got, A, B):
+CHECK_PRIMES = (2147483647, 2147483629, 2147483587)   # the three largest primes below 2^31
+
+
+def limb_residues(limbs, primes=CHECK_PRIMES):
+    """sum_k limbs[k] 2^(64k) mod q for each q < 2^31, vectorised: the powers
+    2^(64k) mod q come from an outer product of block powers (every partial
+    product stays below 2^62)."""
+    x = np.asarray(limbs, dtype=np.uint64).reshape(-1)
+    n = x.size
+    out = []
+    blk = 1 << 12
+    nb = (n + blk - 1) // blk
+    for q in primes:
+        r = pow(2, 64, q)
+        small = np.empty(blk, dtype=np.uint64)
+        big = np.empty(nb, dtype=np.uint64)
+        acc = 1
+        for i in range(blk):
+            small[i] = acc
+            acc = acc * r % q
+        rb, acc = acc, 1
+        for j in range(nb):
+            big[j] = acc
+            acc = acc * rb % q
+        total = 0
+        for j0 in range(0, nb, 1 << 12):                       # slabs of 2^24 limbs
+            j1 = min(nb, j0 + (1 << 12))
+            pw = (big[j0:j1, None] * small[None, :]) % np.uint64(q)
+            seg = x[j0 * blk:j1 * blk]
+            pw = pw.reshape(-1)[:seg.size]
+            total += int(np.sum(((seg % np.uint64(q)) * pw) % np.uint64(q), dtype=np.uint64))
+        out.append(total % q)
+    return out
+
+
+def check_product(got, A, B, ra=None, rb=None):
+    """Low word and residues mod three 31-bit primes against the operands'
+    (a bounded check at any size; never the full product)."""
     if int(got[0]) != (int(A[0]) * int(B[0])) % (1 << 64):
         return False
-    ga, ia, ib = syn.to_int(got), syn.to_int(A), syn.to_int(B)
-    for q in ((1 << 61) - 1, (1 << 89) - 1, (1 << 107) - 1):   # Mersenne primes
-        if ga % q != (ia % q) * (ib % q) % q:                  # never the full product
-            return False
-    return True
+    ra = ra or limb_residues(A)
+    rb = rb or limb_residues(B)
+    rc = limb_residues(got)
+    return all(c == x * y % q for c, x, y, q in zip(rc, ra, rb, CHECK_PRIMES))
+
+
+def time_steps(fn, steps, flush, stream):
+    """Device ms per call of fn(): CUDA events on the launching stream around
+    each call, L2 flushed (256 MiB write) outside the events."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for e0, e1 in ev:
+        flush.fill_(1)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    return [e0.elapsed_time(e1) for e0, e1 in ev]
+
+
+def steps_for(ms_estimate, budget_ms, lo=2, hi=200):
+    return int(max(lo, min(hi, budget_ms // max(ms_estimate, 1e-3))))
 
 
 def run_ours(args):
@@ -314,9 +379,9 @@ def run_ours(args):
     plan.sync_status()
     total_ms = max_over_ranks(sum(step_ms), dev, world)
     ms_per_step = total_ms / args.steps
-    bits_per_step = 2 * n_bits * world
     value = job_gbit_s(2 * n_bits, world, ms_per_step)
-    ok = check_product(out.cpu().numpy().view(np.uint64), A, B)
+    rab = (limb_residues(A), limb_residues(B))
+    ok = check_product(out.cpu().numpy().view(np.uint64), A, B, *rab)
 
     # end to end through dkss_mul_host from pinned host memory
     a_h = torch.from_numpy(A.view(np.int64)).pin_memory()
@@ -324,30 +389,72 @@ def run_ours(args):
     c_h = torch.empty(2 * A.size, dtype=torch.int64).pin_memory()
     an, bn, cn = (x.numpy().view(np.uint64) for x in (a_h, b_h, c_h))
     plan.mul_host(an, bn, cn)
-    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    e2e_steps = max(1, min(args.steps, args.e2e_steps, steps_for(ms_per_step, 8000)))
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         plan.mul_host(an, bn, cn)
     e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dev, world)
-    ok = ok and check_product(cn, A, B)
+    ok = ok and check_product(cn, A, B, *rab)
     e2e_value = job_gbit_s(2 * n_bits, world, e2e_s * 1e3)
+    del a_h, b_h, c_h
 
     # squares of the same operand (dkss_mul with a == b: one forward transform)
-    sq_steps = max(1, min(args.steps, 50))
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(sq_steps)]
-    for e0, e1 in ev:
-        flush.fill_(1)
-        e0.record(stream)
-        plan.mul(a, a, out)
-        e1.record(stream)
-    torch.cuda.synchronize(dev)
-    sq_ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / sq_steps
+    sq_steps = max(1, min(args.steps, 50, steps_for(ms_per_step, 4000)))
+    sq_ms = sum(time_steps(lambda: plan.mul(a, a, out), sq_steps, flush, stream)) / sq_steps
     square = {"ms_per_step": round(sq_ms, 5), "speedup_vs_product": round(ms_per_step / sq_ms, 3),
-              "bit_exact": bool(check_product(out.cpu().numpy().view(np.uint64), A, A))}
+              "bit_exact": bool(check_product(out.cpu().numpy().view(np.uint64), A, A, rab[0], rab[0]))}
     plan.profile_read()
+    roofline = main_roofline(args, info, cfg, A, prof)
+    launches = plan.launches * args.steps
+    plan.close()
 
-    # roofline of the kernel group with the most device time
+    forms = compare_forms(args.workload, args.form, dev, flush, a, b, out, ms_per_step, args.form_budget_ms, A, B,
+                          rab) \
+        if (rank == 0 and not args.no_forms) else None
+    del a, b, out
+    others = other_workloads(args, dev, flush) if (rank == 0 and not args.no_others) else None
+    batched = run_batched(args, dev, flush) if (rank == 0 and not args.no_batched) else None
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.workload)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 4), "unit": "Gbit/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(ms_per_step, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u8" if args.form == "int8tc" else "u32",
+            "data": "synthetic: SplitMix64 uniform operands in [0, 2^N)",
+            "config": dict(workload_config(args.workload), form="int8tc" if args.form == "int8tc" else "imad",
+                           rmul=args.form,
+                           l2="inputs larger than L2 at 2^28 bits and up; also flushed between steps "
+                              "(256 MiB write outside the timed events)",
+                           parallelism="replicas" if world > 1 else "single GPU"),
+            "products_per_s": round(world / (ms_per_step * 1e-3), 3),
+            "bit_exact": bool(ok),
+            "gpu_launches": launches,
+            "e2e": {"value": round(e2e_value, 4), "unit": "Gbit/s", "h2d_bytes_per_step": 2 * A.nbytes,
+                    "d2h_bytes_per_step": 4 * A.nbytes, "steps": e2e_steps},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "forms": forms,
+            "square": square,
+            "workloads": others,
+            "batched": batched,
+            "clocks": clocks,
+            "wall_s": round(wall, 3),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main_roofline(args, info, cfg, A, prof):
+    """Roofline of the kernel group with the most device time (per-stage CUDA
+    events of the library, on the launching stream, over the timed steps), and
+    every group's own figure under 'stages'."""
     work = stage_work(info, cfg[2], args.form)
     dom = max((k for k in prof if k in work), key=lambda k: prof[k][0])
     dom_ms, dom_n = prof[dom]
@@ -382,65 +489,67 @@ def run_ours(args):
             ach = mem_bytes[k] / (ms * 1e-3) / 1e9
             stages[k] = {"bound": "hbm", "ms": round(ms, 4), "achieved": round(ach, 1), "unit": "GB/s",
                          "frac": round(ach / HBM_GBS, 4)}
-    roofline = {"bound": bound, "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 3),
-                "unit": unit, "frac": round(achieved / peak, 4),
-                "traffic": NCU_TRAFFIC_BYTES.get((args.workload, args.form, dom)),
-                "stages": stages,
-                "avg_launch_ms": round(avg_launch_ms, 4), "ops_per_launch": int(ops_per_launch),
-                "peak_basis": peak_basis}
-
-    batched = run_batched(args, dev, flush) if (rank == 0 and not args.no_batched) else None
-    forms = compare_forms(args, dev, flush, a, b, out, ms_per_step) if (rank == 0 and not args.no_forms) else None
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.workload, A, B)
-
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": round(value, 4), "unit": "Gbit/s", "n_gpus": world,
-            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(ms_per_step, 5),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "u8" if args.form == "int8tc" else "u32",
-            "data": "synthetic: SplitMix64 uniform operands in [0, 2^N)",
-            "config": dict(workload_config(args.workload), form="int8tc" if args.form == "int8tc" else "imad",
-                           rmul=args.form,
-                           l2="flushed between steps (256 MiB write outside the timed events)",
-                           parallelism="replicas" if world > 1 else "single GPU"),
-            "products_per_s": round(world / (ms_per_step * 1e-3), 3),
-            "bit_exact": bool(ok),
-            "gpu_launches": plan.launches * args.steps,
-            "e2e": {"value": round(e2e_value, 4), "unit": "Gbit/s", "h2d_bytes_per_step": 2 * A.nbytes,
-                    "d2h_bytes_per_step": 4 * A.nbytes},
-            "roofline": roofline,
-            "cpu_baseline": cpu,
-            "batched": batched,
-            "forms": forms,
-            "square": square,
-            "clocks": clocks,
-            "wall_s": round(wall, 3),
-        }
-        print(json.dumps(line), flush=True)
-    plan.close()
-    if world > 1:
-        dist.destroy_process_group()
+    return {"bound": bound, "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 3),
+            "unit": unit, "frac": round(achieved / peak, 4),
+            "traffic": NCU_TRAFFIC_BYTES.get((args.workload, args.form, dom)),
+            "stages": stages,
+            "avg_launch_ms": round(avg_launch_ms, 4), "ops_per_launch": int(ops_per_launch),
+            "peak_basis": peak_basis}
 
 
-def compare_forms(args, dev, flush, a, b, out, ms_main):
-    """Device time per product of the same workload with each R-multiplication
-    form: through the evaluation map of R and the direct convolution on the
-    integer pipe (IMAD), and INT8 tensor-core byte-slice products (TC)."""
+def other_workloads(args, dev, flush):
+    """The other single-product workloads, default form, with the TC-vs-IMAD
+    comparison of each: device ms per product, operand Gbit/s, products/s."""
+    import torch
+
+    import paper_1503_04955_gb300 as dk
+
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    for name in ("dkss_65536b", "dkss_2p24b", "dkss_2p28b", "dkss_2p32b"):
+        if name == args.workload:
+            continue
+        cfg = syn.workload_params(name)
+        A, B = syn.operand_pair(cfg[0], syn.config_seed(syn.WORKLOADS[name]["index"]))
+        a = torch.from_numpy(A.view(np.int64)).to(dev)
+        b = torch.from_numpy(B.view(np.int64)).to(dev)
+        out = torch.empty(2 * A.size, dtype=torch.int64, device=dev)
+        with dk.Plan(*cfg) as plan:
+            for _ in range(3):
+                plan.mul(a, b, out)
+            torch.cuda.synchronize(dev)
+            t = time_steps(lambda: plan.mul(a, b, out), 2, flush, stream)
+            steps = steps_for(min(t), args.other_budget_ms)
+            ms = sum(time_steps(lambda: plan.mul(a, b, out), steps, flush, stream)) / steps
+            rab = (limb_residues(A), limb_residues(B))
+            ok = check_product(out.cpu().numpy().view(np.uint64), A, B, *rab)
+        entry = {"ms_per_step": round(ms, 5), "latency_us": round(1e3 * ms, 2), "steps": steps,
+                 "gbit_s": round(2 * cfg[0] / (ms * 1e-3) / 1e9, 4),
+                 "products_per_s": round(1 / (ms * 1e-3), 2), "bit_exact": bool(ok)}
+        if not args.no_forms:
+            entry["forms"] = compare_forms(name, "ntt", dev, flush, a, b, out, ms, args.form_budget_ms, A, B, rab)
+        res[name] = entry
+        del a, b, out
+    return res
+
+
+def compare_forms(workload, main_form, dev, flush, a, b, out, ms_main, budget_ms, A, B, rab):
+    """Device time per product of one workload with each R-multiplication
+    form: through the evaluation map of R (alpha-shift inner DFTs, ntt; or
+    inner levels in evaluation coordinates, eval) and the direct convolution
+    on the integer pipe (IMAD), and INT8 tensor-core byte-slice products (TC).
+    Each form's product is checked (low word and prime residues)."""
     import torch
 
     import paper_1503_04955_gb300 as dk
     from paper_1503_04955_gb300 import binding
 
-    cfg = syn.workload_params(args.workload)
+    cfg = syn.workload_params(workload)
     res = {}
     stream = torch.cuda.current_stream(dev)
     for name, flags in (("ntt", 0), ("eval", binding.LEVELS_EVAL), ("direct", binding.RMUL_DIRECT),
                         ("int8tc", binding.FORM_INT8TC)):
-        if name == args.form:
+        if name == main_form:
             res[name] = {"ms_per_step": round(ms_main, 5)}
             continue
         try:
@@ -448,18 +557,15 @@ def compare_forms(args, dev, flush, a, b, out, ms_main):
         except dk.DkssError as e:
             res[name] = {"unsupported": str(e)}
             continue
-        for _ in range(3):
+        for _ in range(2):
             plan.mul(a, b, out)
-        steps = max(1, args.form_steps)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        for e0, e1 in ev:
-            flush.fill_(1)
-            e0.record(stream)
-            plan.mul(a, b, out)
-            e1.record(stream)
         torch.cuda.synchronize(dev)
+        t = time_steps(lambda: plan.mul(a, b, out), 1, flush, stream)
+        steps = steps_for(t[0], budget_ms, lo=1, hi=50)
+        ms = sum(time_steps(lambda: plan.mul(a, b, out), steps, flush, stream)) / steps
+        ok = check_product(out.cpu().numpy().view(np.uint64), A, B, *rab)
         plan.close()
-        res[name] = {"ms_per_step": round(sum(e0.elapsed_time(e1) for e0, e1 in ev) / steps, 5)}
+        res[name] = {"ms_per_step": round(ms, 5), "steps": steps, "bit_exact": bool(ok)}
     if all("ms_per_step" in res.get(k, {}) for k in ("int8tc", "direct", "ntt")):
         res["tc_vs_imad_direct"] = round(res["direct"]["ms_per_step"] / res["int8tc"]["ms_per_step"], 3)
         res["tc_vs_imad_ntt"] = round(res["ntt"]["ms_per_step"] / res["int8tc"]["ms_per_step"], 3)
@@ -559,26 +665,55 @@ def run_batched(args, dev, flush):
 
 # ------------------------------------------------------------- reference ----
 
-def oracle_product_seconds(name, A, B):
+# The oracle's full product at 2^32 bits takes about half an hour on 8 host
+# threads; a bench step takes a bounded sample of the workload instead: one
+# full product of operands 2^(32-SAMPLE_SHIFT) bits long with the same ring
+# and encoding (m, u, p, z; M scaled with N), 2^23 bits for the 2^32-bit
+# workload.  Smaller workloads are timed whole.
+SAMPLE_MAX_BITS = 1 << 23
+
+
+def oracle_sample(name):
+    """(params, operands, description) of the oracle's timed sample of workload `name`."""
+    cfg = list(syn.workload_params(name))
+    n_bits = cfg[0]
+    if n_bits <= SAMPLE_MAX_BITS:
+        A, B = syn.operand_pair(n_bits, syn.config_seed(syn.WORKLOADS[name]["index"]))
+        return cfg, A, B, "one full %s product" % name
+    shift = (n_bits // SAMPLE_MAX_BITS).bit_length() - 1
+    cfg[0] = n_bits >> shift
+    cfg[1] = cfg[1] >> shift
+    A, B = syn.operand_pair(cfg[0], syn.config_seed(syn.WORKLOADS[name]["index"]))
+    desc = ("one full product of %d-bit operands with the %s ring and encoding (M=%d, m=%d, u=%d, p=%d, z=%d), "
+            "the bounded sample of the %d-bit workload" % (cfg[0], name, cfg[1], cfg[2], cfg[3], cfg[4], cfg[5],
+                                                            n_bits))
+    return cfg, A, B, desc
+
+
+def oracle_product_seconds(cfg, A, B, threads):
     import dkss_oracle
     import oracle_c
-    cfg = syn.workload_params(name)
     par = dkss_oracle.Params(*cfg).check()
     rho = dkss_oracle.compute_roots(par).rho
-    oracle_c.load()
+    used = oracle_c.set_threads(threads)
     t0 = time.perf_counter()
     c, _ = oracle_c.dkss_mul(A, B, par, rho)
     dt = time.perf_counter() - t0
-    return dt, c
+    return dt, c, used
 
 
-def cpu_baseline(name, A, B):
-    dt, c = oracle_product_seconds(name, A, B)
-    ok = syn.to_int(c[:2]) == (syn.to_int(A[:2]) * syn.to_int(B[:2])) % (1 << 128)
-    n_bits = syn.WORKLOADS[name]["n_bits"]
-    return {"value": round(2 * n_bits / dt / 1e9, 6), "unit": "Gbit/s", "cores": 1, "kind": "oracle",
-            "sample": "one full %s product (C oracle, single thread, %.2f s)" % (name, dt),
-            "low_words_ok": bool(ok)}
+def cpu_baseline(name):
+    """The oracle (oracle/dkss_oracle.c as it stands) on the host cores: all of
+    them (OpenMP over its independent loops) and one thread, on the workload's
+    bounded sample; operand Gbit/s of the sample."""
+    cfg, A, B, desc = oracle_sample(name)
+    dt_all, c, cores = oracle_product_seconds(cfg, A, B, os.cpu_count() or 1)
+    ok = check_product(c, A, B)
+    dt_one, _, _ = oracle_product_seconds(cfg, A, B, 1)
+    return {"value": round(2 * cfg[0] / dt_all / 1e9, 6), "unit": "Gbit/s", "cores": cores, "kind": "oracle",
+            "sample": "%s: %.2f s on %d host threads" % (desc, dt_all, cores),
+            "single_thread": {"value": round(2 * cfg[0] / dt_one / 1e9, 6), "cores": 1, "seconds": round(dt_one, 3)},
+            "bit_exact_checked": bool(ok)}
 
 
 def run_reference(args):
@@ -586,31 +721,33 @@ def run_reference(args):
     if rank != 0:
         return
     name = args.workload
-    n_bits = syn.WORKLOADS[name]["n_bits"]
-    A, B = syn.operand_pair(n_bits, syn.config_seed(syn.WORKLOADS[name]["index"]))
+    cfg, A, B, desc = oracle_sample(name)
     small = syn.workload_params("dkss_65536b")
     Aw, Bw = syn.operand_pair(small[0], 7)
+    cores = os.cpu_count() or 1
     for _ in range(max(3, args.warmup)):      # warm-up on the small workload (bounded)
-        oracle_product_seconds("dkss_65536b", Aw, Bw)
+        oracle_product_seconds(small, Aw, Bw, cores)
     budget_s = 150.0
     times = []
     while len(times) < args.steps:
-        dt, _ = oracle_product_seconds(name, A, B)
+        dt, c, used = oracle_product_seconds(cfg, A, B, cores)
         times.append(dt)
         if sum(times) + dt > budget_s:
             break
     mean = sum(times) / len(times)
-    value = 2 * n_bits / mean / 1e9
-    sample = "%d full %s product(s) by the C oracle, single thread (of %d steps requested; capped at %.0f s)" % (
-        len(times), name, args.steps, budget_s)
+    value = 2 * cfg[0] / mean / 1e9
+    sample = "%s per step, %d host threads; %d of %d steps requested (capped at %.0f s)" % (
+        desc, used, len(times), args.steps, budget_s)
     line = {
         "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "Gbit/s", "n_gpus": world,
         "steps": len(times), "warmup": max(3, args.warmup), "ms_per_step": round(mean * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u128",
         "data": "synthetic: SplitMix64 uniform operands in [0, 2^N)",
         "config": dict(workload_config(name), form="cpu oracle"),
-        "cpu_baseline": {"value": round(value, 6), "unit": "Gbit/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": round(value, 6), "unit": "Gbit/s", "cores": used, "kind": "oracle",
+                         "sample": sample},
         "e2e": {"value": round(value, 6), "unit": "Gbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "bit_exact": bool(check_product(c, A, B)),
     }
     print(json.dumps(line), flush=True)
 

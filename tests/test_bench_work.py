@@ -73,3 +73,33 @@ def test_montgomery_product_count():
         assert bench.modmul_imads(L) == limb_products + reduction
     # the NTT form's R-multiplication at m = 32: 80 + 32 + 96 = 208 products
     assert bench.rmul_imads(32, 4, "ntt") == 208 * bench.modmul_imads(4)
+
+
+def test_limb_residues_match_python_int():
+    """bench's product check: vectorised residues mod 31-bit primes equal the
+    residues of the Python integer (sizes across the 2^12-limb blocks)."""
+    import numpy as np
+    import dkss_synth as syn
+    for n_bits in (64, 4096 * 64, 4096 * 64 + 64, 100000):
+        x = syn.operand(n_bits, 77, 0)
+        v = syn.to_int(x)
+        assert bench.limb_residues(x) == [v % q for q in bench.CHECK_PRIMES]
+    A, B = syn.operand_pair(70000, 3)
+    c = syn.from_int(syn.to_int(A) * syn.to_int(B), 2 * A.size)
+    assert bench.check_product(c, A, B)
+    c[123] ^= np.uint64(1 << 17)
+    assert not bench.check_product(c, A, B)
+
+
+def test_oracle_sample_is_a_valid_plan():
+    """The CPU baseline's bounded sample of each workload: the workload itself
+    up to 2^23 bits, else 2^23-bit operands with the same ring and encoding,
+    which must satisfy the thesis's conditions (Section 3.2 steps 1-2)."""
+    import dkss_oracle as o
+    import dkss_synth as syn
+    for name in syn.WORKLOADS:
+        cfg, A, B, desc = bench.oracle_sample(name)
+        full = syn.workload_params(name)
+        assert cfg[2:] == list(full[2:])
+        assert cfg[0] == min(full[0], bench.SAMPLE_MAX_BITS) and A.size == (cfg[0] + 63) // 64
+        o.Params(*cfg).check()
