@@ -52,7 +52,11 @@ enum {
     DKSS_FORM_INT8TC = 2,  /* R-multiplications as exact INT8 tensor-core products
                               (mma.sync u8, byte slices of the residues); m >= 32 */
     DKSS_PROFILE = 4,      /* per-stage CUDA-event timing, read with dkss_profile_read */
-    DKSS_DEBUG_CHECKS = 8, /* reserved: extra device-side range checks */
+    DKSS_DEBUG_CHECKS = 8, /* device-side range checks at the stage boundaries: every residue of
+                              both transformed operands, of the componentwise products and of
+                              the product polynomial must lie in [0, p^z) (Section 3.2); one
+                              extra HBM pass per check; a failure makes dkss_sync_status return
+                              DKSS_EDEVICE (the product itself is then not to be trusted) */
     DKSS_RMUL_DIRECT = 16, /* R-multiplications by the direct negacyclic convolution
                               (Section 2.9.2) instead of through the evaluation map of R */
     DKSS_LEVELS_EVAL = 128 /* every radix-2m level but the first, and the last level, in the
@@ -64,9 +68,24 @@ enum {
                               inner DFT is the thesis's alpha-shift DFT */
 };
 
+/* dkss_plan with M = m = u = p = z = 0: parameters by the thesis's rule alone
+   (Section 4.1), without timing candidates on the device */
+#define DKSS_TUNE_RULE 32
+
 /*
  * Build a plan for N-bit operands (thesis Section 3.2 steps 1-3, Section 4.1).
  *   n_bits  N, 64 <= N; operands are < 2^N.
+ *   M = m = u = p = z = 0: the library chooses the parameters.  It lists the
+ *           valid sets as dkss_plan_candidates does and ranks them by the
+ *           thesis's rule (Section 4.1: p^z just above the coefficient bound,
+ *           then the largest u, then the smallest M m, then M/m closest to
+ *           N / log2(N)^3).  For N <= 2^26 (and without DKSS_TUNE_RULE) it
+ *           then times one product with the rule's choice and with the four
+ *           other sets of least estimated work on the current device and keeps
+ *           the fastest; choices are cached per (device, N, flags) for the
+ *           life of the process.  The thesis notes that its fixed rule leaves a
+ *           staircase of run times that calibration should smooth out
+ *           (Section 4.4).  dkss_plan_info reports the chosen set.
  *   M, m    powers of two, 16 <= m <= 64, M >= m, with 2M > 2m (at least one
  *           radix-2m level); the transform length is 2M.
  *   u       input bits per inner coefficient, 1 <= u <= 32, M*(m/2)*u >= N.
@@ -91,6 +110,40 @@ enum {
  */
 dkss_status dkss_plan(dkss_plan_t* plan, uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u,
                       uint64_t p, uint32_t z, uint32_t flags);
+
+/*
+ * A plan over Z/pZ (z = 1) with the Proth prime p = h 2^n + 1, the form of
+ * the thesis's own primes (Section 4.1: z = 1 without Hensel lifting, and a
+ * precomputed table of primes h 2^n + 1 with the smallest odd h for each bit
+ * length).  Arguments as dkss_plan with p = h 2^n + 1 in place of (p, z):
+ * h odd, 0 < h < 2^32, 2M | 2^n, p < 2^126, p prime (Proth's theorem with a
+ * quadratic non-residue as witness) and above the coefficient bound
+ * M (m/2) (2^u - 1)^2 (Section 3.2.2).
+ * When n >= 26 (LR - 1) (LR: the 26-bit limbs of the plan's products) and p has
+ * no other limbs, p = 1 mod 2^26: the Montgomery reductions of the default
+ * form then need no digit product and one limb product per digit instead of
+ * LR + 1 (the thesis's outlook proposes exploiting the Proth form in the
+ * modular reductions, Section 5.1); dkss_plan_info reports whether it applies.
+ * The products are the same as with any other valid ring.  Errors: as
+ * dkss_plan.
+ */
+dkss_status dkss_plan_proth(dkss_plan_t* plan, uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, uint64_t h,
+                            uint32_t n, uint32_t flags);
+
+/* Host-only roots of a Proth plan: as dkss_plan_rho for dkss_plan_proth's ring. */
+dkss_status dkss_plan_proth_rho(uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, uint64_t h, uint32_t n,
+                                uint64_t* rho_out, uint64_t* consts, size_t n_consts);
+
+/*
+ * A Proth ring with the cheap reduction for the given N, M, m, u (host only):
+ * the fewest product limbs LR in 3..5 and, for it, n = max(26 (LR - 1),
+ * log2 2M) and the smallest odd h such that p = h 2^n + 1 is prime, above the
+ * coefficient bound and m p < 2^(26 LR - 2) -- p just above the bound, as the
+ * thesis's rule picks it (Section 4.1), within the limb layout.  *h, *n
+ * receive the choice.  Errors: DKSS_EINVAL, DKSS_EPARAM (shape),
+ * DKSS_EUNSUPPORTED (none found).
+ */
+dkss_status dkss_proth_ring(uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, uint64_t* h, uint32_t* n);
 
 /*
  * out = a * b (thesis Section 3.2 steps 4-8).  a, b: device pointers to
@@ -222,8 +275,15 @@ dkss_status dkss_mul_batch(const dkss_job* jobs, size_t count, uint32_t flags, d
  * 1 unless the flags ask for 2), 1 when form 0 (every level on
  * coefficients) scales one factor of each componentwise product first (else
  * 0), 1 when the ring allows the inner levels in evaluation coordinates
- * (else 0), and the mask of the stages of their DFTs whose butterflies with
- * twiddle 1 skip the product (bit s: stage s).
+ * (else 0), the mask of the stages of their DFTs whose butterflies with
+ * twiddle 1 skip the product (bit s: stage s), then M, m, u, p (low word),
+ * z (the parameters in effect, also when the library chose them), p's high
+ * word (Proth primes above 2^64), 1 when the Montgomery reductions use the
+ * sparse Proth modulus (dkss_plan_proth) else 0, and the bytes of device memory
+ * the plan holds: its two transformed polynomials (the transform runs in
+ * place, level by level, with no third polynomial for the thesis's
+ * intermediate abar of Section 4.5), the twiddle tables and the carry-scan
+ * scratch (0 for a host-only view).
  */
 dkss_status dkss_plan_info(dkss_plan_t plan, uint64_t* consts, size_t n_consts, uint64_t* rho_out);
 
@@ -250,17 +310,19 @@ dkss_status dkss_profile_read(dkss_plan_t plan, double* ms, uint64_t* counts, si
 
 /*
  * Largest product dkss_decode_static handles: its scratch holds one word per
- * tile of 2048 32-bit output windows, so 2*ceil(N/64) <= 2^27 words (N <= 2^33).
+ * tile of 2048 32-bit output windows, and a product has 4*ceil(N/64) windows,
+ * so ceil(N/64) <= 2^27 (N <= 2^33).
  */
 #define DKSS_DECODE_STATIC_MAX_TILES 262144
 
 /*
  * Decoding and carry propagation (the last step of a product) that allocates
- * nothing.  The thesis has no counterpart: this exists for callers that cannot
- * allocate device memory at the time of the call -- for example code running
- * while a stream is being captured into a CUDA graph, where cudaMalloc and
- * cudaFree are not allowed, or a real-time loop whose memory is fixed before
- * it starts.  They still need the carry scan's scratch; here it is a
+ * nothing.  The thesis has no counterpart.  It exists for callers that cannot
+ * allocate device memory at the time of the call: a latency-bound loop whose
+ * device memory is fixed before it starts (cudaMalloc and cudaFree may
+ * synchronize the device and stall its other streams), or code running inside
+ * a framework that owns the device's memory pool and gives its plugins no
+ * allocator.  They still need the carry scan's scratch; here it is a
  * file-scope device array of DKSS_DECODE_STATIC_MAX_TILES + 1 words (1 MiB)
  * that every GPU which loads the library holds until the process exits.
  *
@@ -274,13 +336,16 @@ dkss_status dkss_profile_read(dkss_plan_t plan, double* ms, uint64_t* counts, si
  * Result: out = sum over elements e and residues t of c[e][t] * 2^(u(e*m/2+t)),
  * the value decoded in Section 3.2.8 of a product of two N-bit operands.
  * Queued on `stream`.  Errors: DKSS_EINVAL (bad argument), DKSS_EUNSUPPORTED
- * (N beyond the static scratch), DKSS_ECUDA.  The first call on a device looks
- * up the scratch array's device address (cudaGetSymbolAddress), so make one
- * call on each device before capturing a stream.  All calls share the scratch:
- * calls whose work overlaps on the GPU (different streams, or different host
- * threads) race and must be serialised by the caller.  A carry out of 2N bits
- * (impossible for a true product) is recorded in the scratch's status word
- * and not reported.
+ * (N beyond the static scratch, checked before any device work), DKSS_ECUDA.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current and keeps it for the
+ * process, so make that first call before any stream capture; after
+ * cudaDeviceReset the kept address is stale and later calls on that device
+ * are not valid.  All calls share the scratch, which keeps the last call's
+ * contents (only its status word is cleared by each call): calls whose work
+ * overlaps on the GPU (different streams, or different host threads) race and
+ * must be serialised by the caller.  A carry out of 2N bits (impossible for a
+ * true product) is recorded in the scratch's status word and not reported.
  */
 dkss_status dkss_decode_static(const uint32_t* c, uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, uint32_t L,
                                uint64_t* out, dkss_stream_t stream);
@@ -298,6 +363,17 @@ dkss_status dkss_decode_static(const uint32_t* c, uint64_t n_bits, uint64_t M, u
  * autotuner.  Errors: DKSS_EINVAL.
  */
 dkss_status dkss_plan_candidates(uint64_t n_bits, uint64_t* rows, size_t max_rows, size_t* n_rows);
+
+/*
+ * The parameters dkss_plan(plan, n_bits, 0, 0, 0, 0, 0, flags) uses:
+ * params[0..4] = M, m, u, p, z.  With DKSS_TUNE_RULE, or for N > 2^26, this is
+ * the thesis's rule alone and runs on the host only (no device needed);
+ * otherwise candidates are timed on the current device as dkss_plan
+ * describes (and the choice is cached).  flags: the form flags of the plan.
+ * Errors: DKSS_EINVAL (params NULL, N = 0), DKSS_EUNSUPPORTED (no valid set
+ * for this form), DKSS_ECUDA.
+ */
+dkss_status dkss_plan_choose(uint64_t n_bits, uint32_t flags, uint64_t* params);
 
 /*
  * Cost model of the autotuner (the thesis has no counterpart; its Section 4.1
@@ -343,9 +419,18 @@ dkss_status dkss_mlp_adam(float* params, const float* grad, float* m1, float* m2
  *                         dkss_plan_rho return DKSS_EPARAM.
  *   DKSS_FAULT_HOST_ALLOC dkss_plan's host allocation fails: it returns
  *                         DKSS_ENOMEM and sets *plan to NULL.
- * Nothing here touches a GPU.  Returns the previous mask.
+ *   DKSS_FAULT_RANGE      dkss_mul (product path, not the levels in evaluation
+ *                         coordinates) overwrites residue 0 of the transformed
+ *                         first operand with 2^(32L) - 1, which is not below
+ *                         p^z, by a host-to-device copy queued after the
+ *                         forward transform; with DKSS_DEBUG_CHECKS the range
+ *                         check that follows must record it, and
+ *                         dkss_sync_status returns DKSS_EDEVICE.
+ * The injection is made on the host (plan math, host allocation, or a copy
+ * of a host value into device memory); no kernel faults, traps or waits.
+ * Returns the previous mask.
  */
-enum { DKSS_FAULT_RHO = 1, DKSS_FAULT_HOST_ALLOC = 2 };
+enum { DKSS_FAULT_RHO = 1, DKSS_FAULT_HOST_ALLOC = 2, DKSS_FAULT_RANGE = 4 };
 uint32_t dkss_fault_inject(uint32_t mask);
 
 /* Kernel launches one dkss_mul call queues (for launch accounting). */

@@ -25,10 +25,13 @@ EXPORTS = ["dkss_plan", "dkss_mul", "dkss_sqr", "dkss_ll_step", "dkss_mul_host",
            "dkss_plan_info", "dkss_plan_rho", "dkss_profile_read", "dkss_plan_launches", "dkss_sync_status", "dkss_plan_destroy",
            "dkss_status_str", "dkss_decode_static", "dkss_batch_plan", "dkss_batch_run", "dkss_batch_job_params",
            "dkss_batch_destroy", "dkss_plan_candidates", "dkss_mlp_forward", "dkss_mlp_grad", "dkss_mlp_adam",
-           "dkss_fault_inject"]
+           "dkss_fault_inject", "dkss_plan_choose", "dkss_plan_proth", "dkss_plan_proth_rho", "dkss_proth_ring"]
 FORM_PROFILE = 4
 RMUL_DIRECT = 16
 LEVELS_EVAL = 128
+DEBUG_CHECKS = 8
+TUNE_RULE = 32         # dkss_plan with M..z = 0: the thesis's rule without timing
+FAULT_RHO, FAULT_HOST_ALLOC, FAULT_RANGE = 1, 2, 4
 PROFILE_KINDS = ["fwd_dft", "fwd_twiddle", "final_pointwise", "inv_twiddle", "inv_dft", "decode"]
 
 
@@ -68,6 +71,13 @@ def load():
     lib.dkss_decode_static.argtypes = [P, u64, u64, u32, u32, u32, P, P]
     lib.dkss_plan_candidates.argtypes = [u64, P, sz, P]
     lib.dkss_plan_candidates.restype = ctypes.c_int
+    lib.dkss_plan_choose.argtypes = [u64, u32, P]
+    lib.dkss_plan_choose.restype = ctypes.c_int
+    lib.dkss_plan_proth.argtypes = [ctypes.POINTER(P), u64, u64, u32, u32, u64, u32, u32]
+    lib.dkss_plan_proth_rho.argtypes = [u64, u64, u32, u32, u64, u32, P, P, sz]
+    lib.dkss_proth_ring.argtypes = [u64, u64, u32, u32, ctypes.POINTER(u64), ctypes.POINTER(u32)]
+    for f in (lib.dkss_plan_proth, lib.dkss_plan_proth_rho, lib.dkss_proth_ring):
+        f.restype = ctypes.c_int
     lib.dkss_mlp_forward.argtypes = [P, P, sz, P, P]
     lib.dkss_mlp_grad.argtypes = [P, P, P, sz, P, P, P]
     lib.dkss_mlp_adam.argtypes = [P, P, P, P, ctypes.c_float, u32, P]
@@ -108,9 +118,9 @@ def _words2_to_ints(arr):
     return [int(lo) | (int(hi) << 64) for lo, hi in zip(arr[0::2], arr[1::2])]
 
 
-N_CONSTS = 16
+N_CONSTS = 24
 CONST_NAMES = ["P2", "mu", "L", "levels", "pz_lo", "pz_hi", "zeta", "omega_lo", "omega_hi", "gamma_lo", "gamma_hi",
-               "LR", "rmul", "prescale", "eval_ok", "eval_skip"]
+               "LR", "rmul", "prescale", "eval_ok", "eval_skip", "M", "m", "u", "p_lo", "z", "p_hi", "sparse", "dev_bytes"]
 RMUL_FORMS = ("ntt", "direct", "int8tc", "eval")     # consts["rmul"] indexes this
 
 
@@ -119,7 +129,32 @@ def _consts_dict(c):
     d["pz"] = d.pop("pz_lo") | (d.pop("pz_hi") << 64)
     d["omega"] = d.pop("omega_lo") | (d.pop("omega_hi") << 64)
     d["gamma"] = d.pop("gamma_lo") | (d.pop("gamma_hi") << 64)
+    d["p"] = d.pop("p_lo") | (d.pop("p_hi") << 64)
     return d
+
+
+def plan_choose(n_bits, flags=TUNE_RULE):
+    """(M, m, u, p, z) that dkss_plan chooses for N-bit operands (dkss_plan_choose);
+    with TUNE_RULE the thesis's rule on the host alone."""
+    out = np.zeros(5, dtype=np.uint64)
+    _check(load().dkss_plan_choose(n_bits, flags, out.ctypes.data), "dkss_plan_choose")
+    return tuple(int(x) for x in out)
+
+
+def proth_ring(n_bits, M, m, u):
+    """(h, n) of the Proth ring with the cheap reduction for these parameters (dkss_proth_ring)."""
+    h, n = ctypes.c_uint64(), ctypes.c_uint32()
+    _check(load().dkss_proth_ring(n_bits, M, m, u, ctypes.byref(h), ctypes.byref(n)), "dkss_proth_ring")
+    return int(h.value), int(n.value)
+
+
+def plan_proth_rho(n_bits, M, m, u, h, n):
+    lib = load()
+    rho = np.zeros(2 * m, dtype=np.uint64)
+    consts = np.zeros(N_CONSTS, dtype=np.uint64)
+    _check(lib.dkss_plan_proth_rho(n_bits, M, m, u, h, n, rho.ctypes.data, consts.ctypes.data, N_CONSTS),
+           "dkss_plan_proth_rho")
+    return _words2_to_ints(rho), _consts_dict(consts)
 
 
 def plan_rho(n_bits, M, m, u, p, z):
@@ -132,15 +167,33 @@ def plan_rho(n_bits, M, m, u, p, z):
 
 
 class Plan:
-    """A DKSS_MUL plan for N-bit operands (dkss_plan)."""
+    """A DKSS_MUL plan for N-bit operands (dkss_plan).  With M = m = u = p = z = 0
+    (the defaults) the library chooses the parameters (rule and measurement)."""
 
-    def __init__(self, n_bits, M, m, u, p, z, flags=0):
+    def __init__(self, n_bits, M=0, m=0, u=0, p=0, z=0, flags=0):
         lib = load()
         h = ctypes.c_void_p()
         _check(lib.dkss_plan(ctypes.byref(h), n_bits, M, m, u, p, z, flags), "dkss_plan")
         self._h = h
-        self.n_bits, self.M, self.m, self.u, self.p, self.z = n_bits, M, m, u, p, z
+        self.n_bits = n_bits
+        if M == m == u == p == z == 0:
+            consts = np.zeros(N_CONSTS, dtype=np.uint64)
+            _check(lib.dkss_plan_info(h, consts.ctypes.data, N_CONSTS, None), "dkss_plan_info")
+            M, m, u, p, z = (int(x) for x in consts[16:21])
+        self.M, self.m, self.u, self.p, self.z = M, m, u, p, z
         self.words = (n_bits + 63) // 64
+
+    @classmethod
+    def proth(cls, n_bits, M, m, u, h, n, flags=0):
+        """Plan over Z/pZ with the Proth prime p = h 2^n + 1 (dkss_plan_proth)."""
+        lib = load()
+        hd = ctypes.c_void_p()
+        _check(lib.dkss_plan_proth(ctypes.byref(hd), n_bits, M, m, u, h, n, flags), "dkss_plan_proth")
+        self = cls.__new__(cls)
+        self._h = hd
+        self.n_bits, self.M, self.m, self.u, self.p, self.z = n_bits, M, m, u, (h << n) + 1, 1
+        self.words = (n_bits + 63) // 64
+        return self
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

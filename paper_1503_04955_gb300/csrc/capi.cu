@@ -3,9 +3,15 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "plan.hpp"
@@ -18,6 +24,8 @@ using dkss_host::u128;
 static std::atomic<uint32_t> g_fault{0};
 
 namespace dkss_planning {
+
+uint32_t fault_mask() { return g_fault.load(); }
 
 bool is_pow2(uint64_t x) { return x && !(x & (x - 1)); }
 
@@ -91,12 +99,19 @@ namespace dkss_planning {
 
 // Everything of a plan that needs no device: parameter checks (Section 3.2
 // steps 1-2), roots (Section 3.2.3) and the limb layout.
-dkss_status plan_host(dkss_plan_s* pl, uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, uint64_t p, uint32_t z) {
-    if (!is_pow2(M) || !is_pow2(m) || m < 2 || M < m || n_bits == 0 || u == 0 || u > 32 || z == 0)
-        return DKSS_EPARAM;
+// Shape checks shared by every ring (Section 3.2 step 1).
+static dkss_status check_shape(uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u) {
+    if (!is_pow2(M) || !is_pow2(m) || m < 2 || M < m || n_bits == 0 || u == 0 || u > 32) return DKSS_EPARAM;
     if (M >= ((uint64_t)1 << 40)) return DKSS_EPARAM;
-    const uint64_t h = m / 2;
-    if ((u128)M * h * u < n_bits) return DKSS_EPARAM;
+    if ((u128)M * (m / 2) * u < n_bits) return DKSS_EPARAM;
+    return DKSS_OK;
+}
+
+static dkss_status plan_ring(dkss_plan_s* pl, uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, u128 p, uint32_t z,
+                             u128 q, uint64_t zeta, u128 zeta_z);
+
+dkss_status plan_host(dkss_plan_s* pl, uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, uint64_t p, uint32_t z) {
+    if (check_shape(n_bits, M, m, u) != DKSS_OK || z == 0) return DKSS_EPARAM;
     const uint64_t P2 = 2 * M;
     if (p < 3 || !dkss_host::is_prime_u64(p) || (p - 1) % P2 != 0) return DKSS_EPARAM;
     u128 q = 1;
@@ -105,7 +120,33 @@ dkss_status plan_host(dkss_plan_s* pl, uint64_t n_bits, uint64_t M, uint32_t m, 
         q *= p;
     }
     const u128 umax = ((u128)1 << u) - 1;
-    if (!(q > (u128)M * h * umax * umax)) return DKSS_EPARAM;  // largest coefficient M (m/2) (2^u-1)^2
+    if (!(q > (u128)M * (m / 2) * umax * umax)) return DKSS_EPARAM;  // largest coefficient
+    const uint64_t zeta = dkss_host::smallest_generator(p);
+    return plan_ring(pl, n_bits, M, m, u, p, z, q, zeta, dkss_host::hensel_lift(zeta, p, z));
+}
+
+// z = 1 and the Proth prime p = h 2^n + 1 (Section 4.1: the thesis's primes).
+dkss_status plan_host_proth(dkss_plan_s* pl, uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, uint64_t h,
+                            uint32_t n) {
+    if (check_shape(n_bits, M, m, u) != DKSS_OK) return DKSS_EPARAM;
+    if (h == 0 || (h >> 32) != 0 || (h & 1) == 0 || n == 0 || n + (uint32_t)bitlen(h) > 126) return DKSS_EPARAM;
+    if (((u128)1 << n) % (2 * M) != 0) return DKSS_EPARAM;          // 2M | p - 1
+    if (!dkss_host::proth_is_prime(h, n)) return DKSS_EPARAM;
+    const u128 p = ((u128)h << n) + 1;
+    const u128 umax = ((u128)1 << u) - 1;
+    if (!(p > (u128)M * (m / 2) * umax * umax)) return DKSS_EPARAM;
+    const uint64_t zeta = dkss_host::proth_generator(h, n);
+    if (zeta == 0) return DKSS_EPARAM;
+    return plan_ring(pl, n_bits, M, m, u, p, 1, p, zeta, zeta);
+}
+
+// Everything of a plan that needs no device, once the ring Z/qZ (q = p^z) and
+// a (p-1)-th root of unity zeta_z mod q are fixed: limb layout, roots
+// (Section 3.2.3) and the constants of the lazy arithmetic.
+static dkss_status plan_ring(dkss_plan_s* pl, uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, u128 p, uint32_t z,
+                             u128 q, uint64_t zeta, u128 zeta_z) {
+    const uint64_t h = m / 2;
+    const uint64_t P2 = 2 * M;
     if ((u128)m * q >= ((u128)1 << 127)) return DKSS_EUNSUPPORTED;  // host sums of m products; 4 m q < 2^130
     // limbs: one spare bit for sums, and m q^2 + R q < 2^(64L) for the REDC of m-term sums
     uint32_t L = (uint32_t)((bitlen(q) + 1 + 31) / 32);
@@ -162,13 +203,15 @@ dkss_status plan_host(dkss_plan_s* pl, uint64_t n_bits, uint64_t M, uint32_t m, 
         for (int i = 0; i < 5; ++i) inv *= 2 - q0 * inv;
         pl->nprime26 = (0u - inv) & ((1u << 26) - 1);
     }
+    pl->q_sparse = LR >= 3 && pl->q_rr[0] == 1;
+    for (uint32_t i = 1; i + 1 < LR; ++i) pl->q_sparse = pl->q_sparse && pl->q_rr[i] == 0;
 
     // roots (Section 3.2.3)
     MontCtx c(q);
     u128 phi = q / p * (p - 1);
     dkss_host::Roots& r = pl->roots;
-    r.zeta = dkss_host::smallest_generator(p);
-    r.zeta_z = dkss_host::hensel_lift(r.zeta, p, z);
+    r.zeta = zeta;
+    r.zeta_z = zeta_z;
     u128 omega_m = c.pow(c.to(r.zeta_z), (p - 1) / P2);
     u128 gamma_m = c.pow(omega_m, pl->mu_top);
     r.omega = c.from(omega_m);
@@ -404,14 +447,201 @@ void fill_consts(const dkss_plan_s* pl, uint64_t* consts, size_t n) {
                           : ((pl->flags & DKSS_RMUL_DIRECT) || !pl->ntt_ok)         ? 1
                           : pl->eval_levels                                          ? 3
                                                                                      : 0;
-    uint64_t v[16] = {pl->P2, pl->mu_top, pl->L, (uint64_t)pl->col_levels + 1, (uint64_t)pl->q,
+    uint64_t v[24] = {pl->P2, pl->mu_top, pl->L, (uint64_t)pl->col_levels + 1, (uint64_t)pl->q,
                       (uint64_t)(pl->q >> 64), pl->roots.zeta, (uint64_t)pl->roots.omega,
                       (uint64_t)(pl->roots.omega >> 64), (uint64_t)pl->roots.gamma,
                       (uint64_t)(pl->roots.gamma >> 64), pl->LR, form,
                       (uint64_t)(pl->ntt_ok && pl->ntt_bias.prescale),
-                      (uint64_t)(pl->ntt_ok && pl->ntt_bias.eval_ok && pl->m <= 32), pl->ntt_bias.eval_skip};
-    for (size_t i = 0; i < n && i < 16; ++i) consts[i] = v[i];
+                      (uint64_t)(pl->ntt_ok && pl->ntt_bias.eval_ok && pl->m <= 32), pl->ntt_bias.eval_skip,
+                      pl->M, pl->m, pl->u, (uint64_t)pl->p, pl->z, (uint64_t)(pl->p >> 64), pl->q_sparse ? 1u : 0u,
+                      pl->dev_bytes};
+    for (size_t i = 0; i < n && i < 24; ++i) consts[i] = v[i];
 }
+
+}  // namespace
+
+namespace {
+using namespace dkss_planning;
+
+// One valid parameter set with its limb and level structure.
+struct Cand {
+    uint64_t M, p;
+    uint32_t m, u, z, L, LR, levels;
+    uint64_t r_last, P2;
+    uint32_t S;   // bytes of p^z (INT8 form)
+};
+
+const uint64_t kCandPrimes[] = {12289, 40961, 65537, 786433, 7340033, 23068673, 104857601, 167772161,
+                                469762049, 998244353};
+
+// Every (M, m, u, p, z) for N-bit operands that dkss_plan accepts and this
+// build has kernels for: m in {16, 32, 64}, u in {8, 16, 24, 32}, the smallest
+// M with M (m/2) u >= N and 2M > 2m, each listed prime with 2M | p-1 and the
+// smallest z above the coefficient bound (Section 3.2.2).
+std::vector<Cand> enumerate_candidates(uint64_t n_bits) {
+    static const uint32_t ms[] = {16, 32, 64};
+    static const uint32_t us[] = {8, 16, 24, 32};
+    std::vector<Cand> out;
+    for (uint32_t m : ms)
+        for (uint32_t u : us) {
+            const uint64_t per = (uint64_t)(m / 2) * u;
+            uint64_t M = 1;
+            while (M * per < n_bits || M <= m) M <<= 1;
+            for (uint64_t p : kCandPrimes) {
+                if ((p - 1) % (2 * M) != 0) continue;
+                for (uint32_t z = 1; z <= 8; ++z) {
+                    dkss_plan_s pl;
+                    const dkss_status s = plan_host(&pl, n_bits, M, m, u, p, z);
+                    if (s == DKSS_EPARAM) continue;     // p^z below the bound: try the next z
+                    Kernels k;
+                    if (s == DKSS_OK && lookup(pl.m, pl.L, pl.LR, &k))
+                        out.push_back(Cand{M, p, m, u, z, pl.L, pl.LR, pl.col_levels + 1, pl.r_last, pl.P2, pl.i8_S});
+                    break;   // the smallest z that passes the bound (or an unsupported one) ends the search
+                }
+            }
+        }
+    return out;
+}
+
+// The thesis's rule (Section 4.1): the largest u, then the smallest M m,
+// then M/m closest to N / log2(N)^3; then the fewest limbs and p^z just
+// above the coefficient bound (the smallest p^z of those left).
+bool rule_less(const Cand& a, const Cand& b, uint64_t n_bits) {
+    const double lg = std::log2((double)n_bits);
+    const double target = std::log2((double)n_bits / (lg * lg * lg));
+    auto key = [&](const Cand& c) {
+        u128 q = 1;
+        for (uint32_t i = 0; i < c.z; ++i) q *= c.p;
+        return std::make_tuple(-(int)c.u, c.M * c.m, std::fabs(std::log2((double)c.M / c.m) - target), c.L, c.LR,
+                               q);
+    };
+    return key(a) < key(b);
+}
+
+// Arithmetic work of a product with candidate c, for picking which
+// candidates to time: R-multiplications ((3 levels' worth of twiddles + the
+// componentwise products) of m log m Montgomery products of LR^2 limb
+// products each) and the bytes of one pass per level over three polynomials.
+double work_estimate(const Cand& c) {
+    const double rmuls = (3.0 * (c.levels - 1) + 1.0) * (double)c.P2;
+    const double lgm = std::log2((double)c.m);
+    const double ops = rmuls * c.m * lgm * c.LR * c.LR;
+    const double bytes = (double)c.P2 * c.m * c.L * 4.0 * (2.0 * c.levels + 1.0);
+    return ops / 20.0 + bytes / 6.0;    // about 20 T multiply-adds/s against 6 TB/s
+}
+
+bool form_ok(const Cand& c, uint32_t flags) {
+    if (flags & DKSS_FORM_INT8TC) return c.m >= 32 && c.S <= 16;   // a warp per element, at most 16 bytes
+    return true;
+}
+
+// Measured operands are bounded so that timing a candidate stays cheap.
+constexpr uint64_t kTuneMaxBits = (uint64_t)1 << 26;
+constexpr int kTuneCandidates = 4;
+
+std::mutex g_tune_mu;
+std::map<std::tuple<int, uint64_t, uint32_t>, Cand> g_tune_cache;   // (device, N, flags) -> choice
+
+// Median device time (ms) of one product with candidate c on the current
+// device, operands of N bits with every limb 0x5a5a... (the top limb masked).
+double time_candidate(uint64_t n_bits, const Cand& c, uint32_t flags, bool* ok) {
+    *ok = false;
+    dkss_plan_t pl = nullptr;
+    if (dkss_plan(&pl, n_bits, c.M, c.m, c.u, c.p, c.z, flags & ~(uint32_t)DKSS_PROFILE) != DKSS_OK) return 0;
+    const size_t nw = (n_bits + 63) / 64;
+    uint64_t* buf = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    std::vector<float> ts;
+    if (cudaMalloc(&buf, 4 * nw * sizeof(uint64_t)) == cudaSuccess &&
+        cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
+        cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess &&
+        cudaMemsetAsync(buf, 0x5a, 2 * nw * sizeof(uint64_t), st) == cudaSuccess) {
+        const int top = (int)(n_bits - 64 * (nw - 1));
+        const uint64_t last = top < 64 ? (0x5a5a5a5a5a5a5a5aull & ((1ull << top) - 1)) : 0x5a5a5a5a5a5a5a5aull;
+        bool good = cudaMemcpyAsync(buf + nw - 1, &last, 8, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+                    cudaMemcpyAsync(buf + 2 * nw - 1, &last, 8, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+                    cudaStreamSynchronize(st) == cudaSuccess;
+        for (int rep = 0; good && rep < 4; ++rep) {
+            good = cudaEventRecord(e0, st) == cudaSuccess &&
+                   dkss_mul(pl, buf, buf + nw, buf + 2 * nw, (dkss_stream_t)st) == DKSS_OK &&
+                   cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+            float t = 0;
+            if (good && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess && rep > 0) ts.push_back(t);
+        }
+        *ok = good && dkss_sync_status(pl, (dkss_stream_t)st) == DKSS_OK && !ts.empty();
+    }
+    cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    cudaFree(buf);
+    dkss_plan_destroy(pl);
+    if (!*ok) return 0;
+    std::sort(ts.begin(), ts.end());
+    return ts[ts.size() / 2];
+}
+
+// Parameters for dkss_plan(..., 0, 0, 0, 0, 0, flags): the thesis's rule
+// alone for large N or with DKSS_TUNE_RULE, else the fastest measured of the
+// rule's choice and the candidates with the least estimated work; cached per
+// (device, N, flags) for the life of the process.
+dkss_status choose_params(uint64_t n_bits, uint32_t flags, Cand* out) {
+    std::vector<Cand> all = enumerate_candidates(n_bits), cands;
+    for (const Cand& c : all)
+        if (form_ok(c, flags)) cands.push_back(c);
+    if (cands.empty()) return DKSS_EUNSUPPORTED;
+    const Cand rule = *std::min_element(cands.begin(), cands.end(),
+                                        [&](const Cand& a, const Cand& b) { return rule_less(a, b, n_bits); });
+    if ((flags & DKSS_TUNE_RULE) || n_bits > kTuneMaxBits) {
+        *out = rule;
+        return DKSS_OK;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return DKSS_ECUDA;
+    const auto key = std::make_tuple(dev, n_bits, flags & ~(uint32_t)DKSS_PROFILE);
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            *out = it->second;
+            return DKSS_OK;
+        }
+    }
+    // candidates with the same kernels and shapes cost the same: keep one of each
+    std::vector<Cand> uniq;
+    for (const Cand& c : cands) {
+        bool dup = false;
+        for (const Cand& d : uniq)
+            dup |= d.M == c.M && d.m == c.m && d.u == c.u && d.L == c.L && d.LR == c.LR && d.levels == c.levels &&
+                   d.r_last == c.r_last;
+        if (!dup) uniq.push_back(c);
+    }
+    std::sort(uniq.begin(), uniq.end(), [](const Cand& a, const Cand& b) { return work_estimate(a) < work_estimate(b); });
+    std::vector<Cand> timed{rule};
+    for (const Cand& c : uniq) {
+        if ((int)timed.size() >= kTuneCandidates + 1) break;
+        if (!(c.M == rule.M && c.m == rule.m && c.u == rule.u && c.L == rule.L && c.LR == rule.LR)) timed.push_back(c);
+    }
+    Cand best = rule;
+    double best_ms = 0;
+    bool any = false;
+    for (const Cand& c : timed) {
+        bool ok = false;
+        const double ms = time_candidate(n_bits, c, flags, &ok);
+        if (ok && (!any || ms < best_ms)) {
+            best = c;
+            best_ms = ms;
+            any = true;
+        }
+    }
+    *out = best;
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune_cache[key] = best;
+    return DKSS_OK;
+}
+
+dkss_status finish_plan(dkss_plan_s* pl, dkss_status s, dkss_plan_t* plan);
 
 }  // namespace
 
@@ -423,10 +653,37 @@ dkss_status dkss_plan(dkss_plan_t* plan, uint64_t n_bits, uint64_t M, uint32_t m
                       uint32_t flags) {
     if (!plan) return DKSS_EINVAL;
     *plan = nullptr;
+    if (M == 0 && m == 0 && u == 0 && p == 0 && z == 0) {   // parameters chosen by the library
+        if (n_bits == 0) return DKSS_EPARAM;
+        Cand c{};
+        const dkss_status cs = choose_params(n_bits, flags, &c);
+        if (cs != DKSS_OK) return cs;
+        M = c.M; m = c.m; u = c.u; p = c.p; z = c.z;
+    }
     dkss_plan_s* pl = (g_fault.load() & DKSS_FAULT_HOST_ALLOC) ? nullptr : new (std::nothrow) dkss_plan_s;
     if (!pl) return DKSS_ENOMEM;
     pl->flags = flags;
-    dkss_status s = plan_host(pl, n_bits, M, m, u, p, z);
+    return finish_plan(pl, plan_host(pl, n_bits, M, m, u, p, z), plan);
+}
+
+dkss_status dkss_plan_proth(dkss_plan_t* plan, uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, uint64_t h,
+                            uint32_t n, uint32_t flags) {
+    if (!plan) return DKSS_EINVAL;
+    *plan = nullptr;
+    dkss_plan_s* pl = (g_fault.load() & DKSS_FAULT_HOST_ALLOC) ? nullptr : new (std::nothrow) dkss_plan_s;
+    if (!pl) return DKSS_ENOMEM;
+    pl->flags = flags;
+    return finish_plan(pl, plan_host_proth(pl, n_bits, M, m, u, h, n), plan);
+}
+
+}  // extern "C"
+
+namespace {
+// Device half of a plan whose host half (pl, status s) is done: kernel
+// lookup, tables, workspace.  Takes ownership of pl.
+dkss_status finish_plan(dkss_plan_s* pl, dkss_status s, dkss_plan_t* plan) {
+    const uint32_t flags = pl->flags;
+    const uint64_t n_bits = pl->n_bits;
     Kernels k;
     if (s == DKSS_OK && !lookup(pl->m, pl->L, pl->LR, &k)) s = DKSS_EUNSUPPORTED;
     // the INT8 tensor-core form needs a warp per element and at most 16 bytes per residue
@@ -439,7 +696,8 @@ dkss_status dkss_plan(dkss_plan_t* plan, uint64_t n_bits, uint64_t M, uint32_t m
     if (!pl->ntt_ok && !(flags & (DKSS_RMUL_DIRECT | DKSS_FORM_INT8TC))) pl->flags |= DKSS_RMUL_DIRECT;
     // inner levels in evaluation coordinates: the NTT form, m <= 32, within their limits
     pl->eval_levels = pl->eval_levels && !(pl->flags & DKSS_RMUL_DIRECT);
-    if (cudaGetDevice(&pl->device) != cudaSuccess) {
+    if (cudaGetDevice(&pl->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&pl->sm_count, cudaDevAttrMultiProcessorCount, pl->device) != cudaSuccess) {
         delete pl;
         return DKSS_ECUDA;
     }
@@ -468,6 +726,8 @@ dkss_status dkss_plan(dkss_plan_t* plan, uint64_t n_bits, uint64_t M, uint32_t m
         delete pl;
         return DKSS_ENOMEM;
     }
+    pl->dev_bytes = 4 * (table.size() + 2 * pl->poly_words + pl->n_tiles + 1 + ntt.size() + evtw.size() +
+                         table_minv.size());
     if (cudaMemcpy(pl->d_table, table.data(), table.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(pl->d_ntt, ntt.data(), ntt.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
         (!evtw.empty() &&
@@ -488,6 +748,10 @@ dkss_status dkss_plan(dkss_plan_t* plan, uint64_t n_bits, uint64_t M, uint32_t m
     *plan = pl;
     return DKSS_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 dkss_status dkss_mul(dkss_plan_t pl, const uint64_t* a, const uint64_t* b, uint64_t* out, dkss_stream_t stream) {
     if (!pl || !a || !b || !out) return DKSS_EINVAL;
@@ -554,38 +818,59 @@ dkss_status dkss_plan_rho(uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, u
     return dkss_plan_info(&pl, consts, n_consts, rho_out);
 }
 
-dkss_status dkss_plan_candidates(uint64_t n_bits, uint64_t* rows, size_t max_rows, size_t* n_rows) {
-    static const uint64_t primes[] = {12289, 40961, 65537, 786433, 7340033, 23068673, 104857601, 167772161,
-                                      469762049, 998244353};
-    static const uint32_t ms[] = {16, 32, 64};
-    static const uint32_t us[] = {8, 16, 24, 32};
-    if (!n_rows || n_bits == 0) return DKSS_EINVAL;
-    size_t n = 0;
-    for (uint32_t m : ms)
-        for (uint32_t u : us) {
-            const uint64_t per = (uint64_t)(m / 2) * u;
-            uint64_t M = 1;
-            while (M * per < n_bits || M <= m) M <<= 1;
-            for (uint64_t p : primes) {
-                if ((p - 1) % (2 * M) != 0) continue;
-                for (uint32_t z = 1; z <= 8; ++z) {
-                    dkss_plan_s pl;
-                    const dkss_status s = plan_host(&pl, n_bits, M, m, u, p, z);
-                    if (s == DKSS_EPARAM) continue;     // p^z below the bound: try the next z
-                    Kernels k;
-                    if (s == DKSS_OK && lookup(pl.m, pl.L, pl.LR, &k)) {
-                        if (rows && n < max_rows) {
-                            const uint64_t v[10] = {M, m, u, p, z, pl.L, pl.LR, (uint64_t)pl.col_levels + 1,
-                                                    pl.r_last, pl.P2};
-                            for (int i = 0; i < 10; ++i) rows[10 * n + i] = v[i];
-                        }
-                        ++n;
-                    }
-                    break;   // the smallest z that passes the bound (or an unsupported one) ends the search
-                }
-            }
+dkss_status dkss_plan_proth_rho(uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, uint64_t h, uint32_t n,
+                                uint64_t* rho_out, uint64_t* consts, size_t n_consts) {
+    dkss_plan_s pl;
+    dkss_status s = plan_host_proth(&pl, n_bits, M, m, u, h, n);
+    if (s != DKSS_OK) return s;
+    return dkss_plan_info(&pl, consts, n_consts, rho_out);
+}
+
+dkss_status dkss_proth_ring(uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, uint64_t* h_out, uint32_t* n_out) {
+    if (!h_out || !n_out) return DKSS_EINVAL;
+    if (check_shape(n_bits, M, m, u) != DKSS_OK) return DKSS_EPARAM;
+    const u128 umax = ((u128)1 << u) - 1;
+    const u128 bound = (u128)M * (m / 2) * umax * umax;
+    const uint32_t lg2M = log2u(2 * M);
+    for (uint32_t LR = 3; LR <= 5; ++LR) {
+        const uint32_t n = std::max<uint32_t>(26 * (LR - 1), lg2M);
+        const int top = 26 * (int)LR - 2 - (int)log2u(m);       // m p < 2^(26 LR - 2)
+        if (top <= (int)n || top > 126) continue;
+        uint64_t h = (uint64_t)(bound >> n) + 1;
+        h |= 1;
+        for (int tries = 0; tries < 200000; ++tries, h += 2) {
+            if ((h >> 32) != 0 || (int)(n + bitlen(h)) > top) break;
+            if (!dkss_host::proth_is_prime(h, n)) continue;
+            dkss_plan_s pl;
+            if (plan_host_proth(&pl, n_bits, M, m, u, h, n) != DKSS_OK) continue;
+            Kernels k;
+            if (pl.LR != LR || !pl.q_sparse || !lookup(pl.m, pl.L, pl.LR, &k)) continue;
+            *h_out = h;
+            *n_out = n;
+            return DKSS_OK;
         }
-    *n_rows = n;
+    }
+    return DKSS_EUNSUPPORTED;
+}
+
+dkss_status dkss_plan_choose(uint64_t n_bits, uint32_t flags, uint64_t* params) {
+    if (!params || n_bits == 0) return DKSS_EINVAL;
+    Cand c{};
+    const dkss_status s = choose_params(n_bits, flags, &c);
+    if (s != DKSS_OK) return s;
+    params[0] = c.M; params[1] = c.m; params[2] = c.u; params[3] = c.p; params[4] = c.z;
+    return DKSS_OK;
+}
+
+dkss_status dkss_plan_candidates(uint64_t n_bits, uint64_t* rows, size_t max_rows, size_t* n_rows) {
+    if (!n_rows || n_bits == 0) return DKSS_EINVAL;
+    const std::vector<Cand> all = enumerate_candidates(n_bits);
+    for (size_t i = 0; rows && i < all.size() && i < max_rows; ++i) {
+        const Cand& c = all[i];
+        const uint64_t v[10] = {c.M, c.m, c.u, c.p, c.z, c.L, c.LR, c.levels, c.r_last, c.P2};
+        for (int k = 0; k < 10; ++k) rows[10 * i + k] = v[k];
+    }
+    *n_rows = all.size();
     return DKSS_OK;
 }
 

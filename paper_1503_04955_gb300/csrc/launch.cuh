@@ -1,6 +1,7 @@
 // Host launchers of the DKSS_MUL kernels for one (m, L) pair.
 #pragma once
 #include <algorithm>
+#include "debug_checks.cuh"
 #include "decode.cuh"
 #include "dkss_kernels.cuh"
 #include "eval_levels.cuh"
@@ -17,9 +18,9 @@ static Mod<L> make_mod(const dkss_plan_s* pl) {
     return md;
 }
 
-template <int LR>
-static ModRR<LR> make_modrr(const dkss_plan_s* pl) {
-    ModRR<LR> md;
+template <int LR, class MR = ModRR<LR>>
+static MR make_modrr(const dkss_plan_s* pl) {
+    MR md;
     for (int i = 0; i < LR; ++i) md.q[i] = pl->q_rr[i];
     md.nprime = pl->nprime26;
     return md;
@@ -103,6 +104,41 @@ __global__ void k_unpermute(const uint32_t* src, uint64_t* dst, uint64_t P2, uin
         if (cudaGetLastError() != cudaSuccess) return DKSS_ECUDA; \
     } while (0)
 
+// DKSS_DEBUG_CHECKS: every residue of n_res residues at poly is below p^z
+// (debug_checks.cuh); a failure sets kStatusRange in the plan's status word.
+template <int L>
+static dkss_status range_check(dkss_plan_s* pl, const uint32_t* poly, uint64_t n_res, cudaStream_t st) {
+    if (!(pl->flags & DKSS_DEBUG_CHECKS)) return DKSS_OK;
+    RangeParams rp{};
+    rp.poly = poly;
+    rp.n_res = n_res;
+    for (int i = 0; i < 4; ++i) rp.q[i] = pl->q_limbs[i];
+    rp.status = pl->d_status;
+    const uint64_t blocks = std::min<uint64_t>((n_res + 255) / 256, (uint64_t)pl->sm_count * 8);
+    k_check_range<L><<<(unsigned)std::max<uint64_t>(1, blocks), 256, 0, st>>>(rp);
+    DKSS_CHECK_LAUNCH();
+    return DKSS_OK;
+}
+
+// Test hook (DKSS_FAULT_RANGE, host side): overwrite residue 0 of the first
+// polynomial with 2^(32L) - 1, which is above p^z, by a host-to-device copy
+// queued on the stream.  The range check that follows must report it.
+template <int L>
+static dkss_status inject_range_fault(dkss_plan_s* pl, cudaStream_t st) {
+    if (!(dkss_planning::fault_mask() & DKSS_FAULT_RANGE)) return DKSS_OK;
+    static const uint32_t bad[4] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu};
+    if (cudaMemcpyAsync(pl->d_work, bad, L * sizeof(uint32_t), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return DKSS_ECUDA;
+    return DKSS_OK;
+}
+
+// The NTT form's kernels take the sparse-modulus Montgomery product when the
+// plan's p^z allows it (Proth primes, dkss_plan_proth; ntt_rmul.cuh).
+template <int LR>
+static bool sparse_ntt(const dkss_plan_s* pl) {
+    return LR >= 3 && pl->q_sparse && !(pl->flags & (DKSS_RMUL_DIRECT | DKSS_FORM_INT8TC));
+}
+
 // The NTT form runs each radix-2m level as one fused kernel (column DFT and
 // its R-multiplications) when a column and the exchange buffers fit three or
 // more CTAs per SM; bigger columns (m = 64 with 4-word residues) keep the
@@ -163,6 +199,18 @@ dkss_status prepare(dkss_plan_s* pl) {
         cudaFuncSetAttribute(k_twiddle_ntt<m, L, LR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, twn) ||
         cudaFuncSetAttribute(k_final_dft<m, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, fdft_max))
         return DKSS_ECUDA;
+    if constexpr (LR >= 3) {
+        using MS = ModRRSparse<LR>;
+        if (sparse_ntt<LR>(pl) &&
+            (cudaFuncSetAttribute(k_final_pointwise<m, L, LR, kFormNtt, MS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  fin_ntt_max) ||
+             cudaFuncSetAttribute(k_level_fwd_ntt<m, L, LR, true, MS>, cudaFuncAttributeMaxDynamicSharedMemorySize, lvl) ||
+             cudaFuncSetAttribute(k_level_fwd_ntt<m, L, LR, false, MS>, cudaFuncAttributeMaxDynamicSharedMemorySize, lvl) ||
+             cudaFuncSetAttribute(k_level_inv_ntt<m, L, LR, MS>, cudaFuncAttributeMaxDynamicSharedMemorySize, lvl) ||
+             cudaFuncSetAttribute(k_twiddle_ntt<m, L, LR, false, MS>, cudaFuncAttributeMaxDynamicSharedMemorySize, twn) ||
+             cudaFuncSetAttribute(k_twiddle_ntt<m, L, LR, true, MS>, cudaFuncAttributeMaxDynamicSharedMemorySize, twn)))
+            return DKSS_ECUDA;
+    }
     if constexpr (m <= 32) {
         if (pl->eval_levels) {
             const int fe = (int)std::min<size_t>(final_eval_smem_bytes<m, L, LR>(G::TWO_M), (size_t)optin);
@@ -176,7 +224,10 @@ dkss_status prepare(dkss_plan_s* pl) {
     // launches per dkss_mul: per radix-2m level a DFT and a twiddle launch forward
     // and backwards, the fused last level, three decode kernels
     // (the NTT form fuses each level's DFT and R-multiplications into one launch)
-    pl->launches = (fused_levels<m, L, LR>(pl) ? 2 : 4) * pl->col_levels + 1 + 3;
+    // (DKSS_DEBUG_CHECKS adds three range checks, one before decoding with
+    // the levels in evaluation coordinates)
+    pl->launches = (fused_levels<m, L, LR>(pl) ? 2 : 4) * pl->col_levels + 1 + 3 +
+                   ((pl->flags & DKSS_DEBUG_CHECKS) ? (pl->eval_levels ? 1 : 3) : 0);
     return DKSS_OK;
 }
 
@@ -188,10 +239,10 @@ static inline void level_geometry(const dkss_plan_s* pl, uint32_t d, uint64_t* l
     *len = pl->P2 / b;
 }
 
-template <int m, int L, int LR, bool INV>
+template <int m, int L, int LR, bool INV, class MR = ModRR<LR>>
 static dkss_status launch_twiddle(dkss_plan_s* pl, LevelParams lp, int operands, cudaStream_t st) {
     using G = Geo<m, L>;
-    const ModRR<LR> mr = make_modrr<LR>(pl);
+    const MR mr = make_modrr<LR, MR>(pl);
     const uint64_t mu_d = lp.len / G::TWO_M;
     const uint64_t total = (uint64_t)(G::TWO_M - 1) * (mu_d - 1) * (pl->P2 / lp.len);
     if (total == 0) return DKSS_OK;
@@ -206,13 +257,13 @@ static dkss_status launch_twiddle(dkss_plan_s* pl, LevelParams lp, int operands,
     else {
         // one team per element of the level (those with twiddle 1 return at once)
         dim3 gn((unsigned)((pl->P2 + NttTeam<m>::NTEAMS - 1) / NttTeam<m>::NTEAMS), operands);
-        k_twiddle_ntt<m, L, LR, INV><<<gn, kThreads, twiddle_ntt_smem_bytes<m, L, LR>(), st>>>(lp, mr);
+        k_twiddle_ntt<m, L, LR, INV, MR><<<gn, kThreads, twiddle_ntt_smem_bytes<m, L, LR>(), st>>>(lp, mr);
     }
     DKSS_CHECK_LAUNCH();
     return DKSS_OK;
 }
 
-template <int m, int L, int LR>
+template <int m, int L, int LR, class MR = ModRR<LR>>
 static dkss_status launch_forward_levels(dkss_plan_s* pl, LevelParams lp, int operands, cudaStream_t st) {
     using G = Geo<m, L>;
     const Mod<L> md = make_mod<L>(pl);
@@ -222,11 +273,11 @@ static dkss_status launch_forward_levels(dkss_plan_s* pl, LevelParams lp, int op
         level_geometry(pl, d, &lp.len, &lp.bp);
         if (fused) {   // inner DFT and R-multiplications of a column in one kernel (NTT form)
             ProfScope ps(pl, st, kProfFwdTwiddle);
-            const ModRR<LR> mr = make_modrr<LR>(pl);
+            const MR mr = make_modrr<LR, MR>(pl);
             if (d == 0)
-                k_level_fwd_ntt<m, L, LR, true><<<grid, kThreads, level_ntt_smem_bytes<m, L, LR>(), st>>>(lp, md, mr);
+                k_level_fwd_ntt<m, L, LR, true, MR><<<grid, kThreads, level_ntt_smem_bytes<m, L, LR>(), st>>>(lp, md, mr);
             else
-                k_level_fwd_ntt<m, L, LR, false><<<grid, kThreads, level_ntt_smem_bytes<m, L, LR>(), st>>>(lp, md, mr);
+                k_level_fwd_ntt<m, L, LR, false, MR><<<grid, kThreads, level_ntt_smem_bytes<m, L, LR>(), st>>>(lp, md, mr);
             DKSS_CHECK_LAUNCH();
             continue;
         }
@@ -237,7 +288,7 @@ static dkss_status launch_forward_levels(dkss_plan_s* pl, LevelParams lp, int op
             DKSS_CHECK_LAUNCH();
         }
         ProfScope ps(pl, st, kProfFwdTwiddle);
-        dkss_status s = launch_twiddle<m, L, LR, false>(pl, lp, operands, st);
+        dkss_status s = launch_twiddle<m, L, LR, false, MR>(pl, lp, operands, st);
         if (s != DKSS_OK) return s;
     }
     return DKSS_OK;
@@ -319,26 +370,26 @@ static dkss_status run_eval_levels(dkss_plan_s* pl, LevelParams lp, cudaStream_t
     return DKSS_OK;
 }
 
-template <int m, int L, int LR>
-dkss_status run_mul(dkss_plan_s* pl, const uint64_t* a, const uint64_t* b, uint64_t* out, cudaStream_t st) {
+// A product with every radix-2m level on coefficients (the thesis's
+// structure); MR is the modulus type of the NTT-form kernels (ModRRSparse for
+// a sparse Proth modulus, ntt_rmul.cuh).
+template <int m, int L, int LR, class MR>
+static dkss_status run_mul_coef(dkss_plan_s* pl, const uint64_t* a, const uint64_t* b, uint64_t* out, cudaStream_t st) {
     using G = Geo<m, L>;
     const Mod<L> md = make_mod<L>(pl);
-    const ModRR<LR> mr = make_modrr<LR>(pl);
+    const MR mr = make_modrr<LR, MR>(pl);
+    const ModRR<LR> mr0 = make_modrr<LR>(pl);
     LevelParams lp = make_level(pl);
     lp.raw_a = a;
     lp.raw_b = b;
     dkss_status s = DKSS_OK;
-    if constexpr (m <= 32) {
-        if (pl->eval_levels) {
-            s = run_eval_levels<m, L, LR>(pl, lp, st);
-            if (s != DKSS_OK) return s;
-            return launch_decode<m, L, LR>(pl, out, st);
-        }
-    }
     // a square (a == b) transforms one polynomial; the last level reads it as both factors
     const bool square = a == b;
-    s = launch_forward_levels<m, L, LR>(pl, lp, square ? 1 : 2, st);
+    s = launch_forward_levels<m, L, LR, MR>(pl, lp, square ? 1 : 2, st);
     if (s != DKSS_OK) return s;
+    if ((s = inject_range_fault<L>(pl, st)) != DKSS_OK) return s;
+    // both transformed operands (b directly follows a)
+    if ((s = range_check<L>(pl, pl->d_work, (square ? 1 : 2) * pl->P2 * m, st)) != DKSS_OK) return s;
     lp.len = pl->r_last;
     if (square) {
         lp.poly_words = 0;
@@ -351,39 +402,62 @@ dkss_status run_mul(dkss_plan_s* pl, const uint64_t* a, const uint64_t* b, uint6
             if constexpr (m >= 32)
                 k_final_pointwise<m, L, LR, kFormI8>
                     <<<blocks, kThreads, final_smem_bytes<m, L, LR>((int)pl->r_last, kFormI8, (int)pl->i8_S), st>>>(
-                        lp, md, mr);
+                        lp, md, mr0);
         } else if (pl->flags & DKSS_RMUL_DIRECT) {
             k_final_pointwise<m, L, LR, kFormDirect><<<blocks, kThreads, final_smem_bytes<m, L, LR>((int)pl->r_last), st>>>(
-                lp, md, mr);
+                lp, md, mr0);
         } else {
             const unsigned nblocks = blocks / (unsigned)final_blocks_per_cta<m>((int)pl->r_last);
-            k_final_pointwise<m, L, LR, kFormNtt>
+            k_final_pointwise<m, L, LR, kFormNtt, MR>
                 <<<nblocks, kThreads, final_smem_bytes<m, L, LR>((int)pl->r_last, kFormNtt), st>>>(lp, md, mr);
         }
         DKSS_CHECK_LAUNCH();
     }
     lp.poly_words = pl->poly_words;
     lp.square = 0;
+    if ((s = range_check<L>(pl, pl->d_work, pl->P2 * m, st)) != DKSS_OK) return s;
     const bool fused = fused_levels<m, L, LR>(pl);
     for (int d = (int)pl->col_levels - 1; d >= 0; --d) {
         level_geometry(pl, (uint32_t)d, &lp.len, &lp.bp);
         if (fused) {   // R-multiplications and inner DFT of a column in one kernel (NTT form)
             ProfScope ps(pl, st, kProfInvTwiddle);
-            k_level_inv_ntt<m, L, LR><<<(unsigned)(pl->P2 / G::TWO_M), kThreads, level_ntt_smem_bytes<m, L, LR>(), st>>>(
-                lp, md, mr);
+            k_level_inv_ntt<m, L, LR, MR><<<(unsigned)(pl->P2 / G::TWO_M), kThreads, level_ntt_smem_bytes<m, L, LR>(),
+                                           st>>>(lp, md, mr);
             DKSS_CHECK_LAUNCH();
             continue;
         }
         {
             ProfScope ps(pl, st, kProfInvTwiddle);
-            s = launch_twiddle<m, L, LR, true>(pl, lp, 1, st);
+            s = launch_twiddle<m, L, LR, true, MR>(pl, lp, 1, st);
             if (s != DKSS_OK) return s;
         }
         ProfScope ps(pl, st, kProfInvDft);
         k_dft_inv<m, L><<<(unsigned)(pl->P2 / G::TWO_M), kThreads, column_smem_bytes<m, L>(), st>>>(lp, md);
         DKSS_CHECK_LAUNCH();
     }
+    // the product polynomial's coefficients, before decoding
+    if ((s = range_check<L>(pl, pl->d_work, pl->P2 * m, st)) != DKSS_OK) return s;
     return launch_decode<m, L, LR>(pl, out, st);
+}
+
+template <int m, int L, int LR>
+dkss_status run_mul(dkss_plan_s* pl, const uint64_t* a, const uint64_t* b, uint64_t* out, cudaStream_t st) {
+    if constexpr (m <= 32) {
+        if (pl->eval_levels) {
+            LevelParams lp = make_level(pl);
+            lp.raw_a = a;
+            lp.raw_b = b;
+            dkss_status s = run_eval_levels<m, L, LR>(pl, lp, st);
+            if (s != DKSS_OK) return s;
+            s = range_check<L>(pl, pl->d_work, pl->P2 * m, st);
+            if (s != DKSS_OK) return s;
+            return launch_decode<m, L, LR>(pl, out, st);
+        }
+    }
+    if constexpr (LR >= 3) {
+        if (sparse_ntt<LR>(pl)) return run_mul_coef<m, L, LR, ModRRSparse<LR>>(pl, a, b, out, st);
+    }
+    return run_mul_coef<m, L, LR, ModRR<LR>>(pl, a, b, out, st);
 }
 
 template <int m, int L, int LR>

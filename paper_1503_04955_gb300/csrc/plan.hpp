@@ -12,7 +12,8 @@
 
 struct dkss_plan_s {
     // parameters (thesis Section 3.2 steps 1-2)
-    uint64_t n_bits = 0, M = 0, P2 = 0, mu_top = 0, p = 0;
+    uint64_t n_bits = 0, M = 0, P2 = 0, mu_top = 0;
+    dkss_host::u128 p = 0;        // the prime (above 2^64 only for Proth primes, dkss_plan_proth)
     uint32_t m = 0, u = 0, z = 0, flags = 0;
     uint32_t L = 0;               // 32-bit limbs per residue
     uint32_t log2_mu_top = 0;
@@ -25,12 +26,16 @@ struct dkss_plan_s {
     uint32_t i8_S = 0;            // bytes per residue for the INT8 tensor-core form
     uint32_t q_rr[5] = {0, 0, 0, 0, 0};
     uint32_t nprime26 = 0;        // -(p^z)^-1 mod 2^26
+    bool q_sparse = false;        // p^z = 1 mod 2^26 and its 26-bit limbs 1 .. LR-2 are zero (Proth
+                                  // primes h 2^n + 1, n >= 26 (LR-1)): Montgomery reduction without the
+                                  // digit product and with one limb product per digit (rr_arith.cuh)
     uint32_t kscale[5] = {0, 0, 0, 0, 0};  // (2M)^-1 R'^2 mod p^z, 26-bit limbs
     dkss_host::Roots roots;
     bool ntt_ok = false;                  // the lazy NTT form's limits hold for this ring
     dkss_planning::NttBiases ntt_bias{};  // its bias constants
     // device memory owned by the plan
     int device = 0;
+    int sm_count = 1;
     uint32_t* d_table = nullptr;  // rho^s (s < mu_top): coefficients, or evaluations (default)
     uint32_t* d_ntt = nullptr;    // constants of the transform in R
     bool eval_levels = false;     // inner levels in evaluation coordinates (eval_levels.cuh)
@@ -44,6 +49,7 @@ struct dkss_plan_s {
     uint32_t* d_status = nullptr;
     uint64_t* d_stage = nullptr;  // dkss_mul_host staging: a, b, out
     uint32_t launches = 0;
+    uint64_t dev_bytes = 0;       // device memory the plan holds (workspace, tables, scratch)
     // DKSS_PROFILE: CUDA events around each kernel group, summed by kind on read
     struct ProfRec {
         cudaEvent_t start, stop;
@@ -55,8 +61,12 @@ struct dkss_plan_s {
 };
 
 namespace dkss_planning {
+// Process-wide host fault-injection mask (dkss_fault_inject; 0 in normal use).
+uint32_t fault_mask();
 // Host parts of a plan, shared by single plans and batches (capi.cu).
 dkss_status plan_host(dkss_plan_s* pl, uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, uint64_t p, uint32_t z);
+dkss_status plan_host_proth(dkss_plan_s* pl, uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, uint64_t h,
+                            uint32_t n);
 void build_table(const dkss_plan_s* pl, std::vector<uint32_t>& out);
 void build_eval_table(const dkss_plan_s* pl, std::vector<uint32_t>& out, bool with_minv);
 void build_ntt_consts(const dkss_plan_s* pl, std::vector<uint32_t>& out);

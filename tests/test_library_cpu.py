@@ -169,3 +169,114 @@ def test_fault_injection_host_allocation(dk):
     finally:
         lib.dkss_fault_inject(old)
     assert lib.dkss_fault_inject(0) == 0
+
+
+@pytest.mark.parametrize("n_bits", [4096, 65536, 100000, 1 << 20, 3 << 20, 1 << 24, 1 << 28, 1 << 32])
+def test_plan_choose_follows_the_thesis_rule(dk, n_bits):
+    """dkss_plan_choose with the rule flag (host only): among the valid sets
+    (dkss_plan_candidates), u is the largest, M m the smallest, M/m the
+    closest to N / log2(N)^3, and p^z the smallest of that kernel shape
+    (Section 4.1) -- checked by enumeration; the shape equals the Python
+    restatement's."""
+    import math
+    from paper_1503_04955_gb300 import autotune
+    M, m, u, p, z = dk.plan_choose(n_bits, dk.TUNE_RULE)
+    cands = dk.plan_candidates(n_bits)
+    assert any((c["M"], c["m"], c["u"], c["p"], c["z"]) == (M, m, u, p, z) for c in cands)
+    umax = max(c["u"] for c in cands)
+    assert u == umax
+    best_mm = min(c["M"] * c["m"] for c in cands if c["u"] == umax)
+    assert M * m == best_mm
+    target = math.log2(n_bits / math.log2(n_bits) ** 3)
+    dist = abs(math.log2(M / m) - target)
+    assert all(abs(math.log2(c["M"] / c["m"]) - target) >= dist - 1e-12
+               for c in cands if c["u"] == umax and c["M"] * c["m"] == best_mm)
+    # the same kernel shape as the Python restatement (which keeps one ring per shape)
+    r = autotune.rule_choice(n_bits, autotune.candidates(n_bits))
+    mine = [c for c in cands if (c["M"], c["m"], c["u"], c["p"], c["z"]) == (M, m, u, p, z)][0]
+    assert tuple(r[k] for k in autotune.KEY) == tuple(mine[k] for k in autotune.KEY)
+    # and p^z just above the bound: the smallest p^z of that shape
+    same = [c for c in cands if all(c[k] == mine[k] for k in autotune.KEY)]
+    assert p ** z == min(c["p"] ** c["z"] for c in same)
+    o.Params(n_bits, M, m, u, p, z).check()
+
+
+def test_plan_choose_rule_for_int8_needs_m32(dk):
+    for n_bits in (65536, 1 << 24):
+        M, m, u, p, z = dk.plan_choose(n_bits, dk.TUNE_RULE | dk.FORM_INT8TC)
+        assert m >= 32
+    with pytest.raises(dk.DkssError):
+        dk.plan_choose(0, dk.TUNE_RULE)
+
+
+# Proth rings (z = 1, p = h 2^n + 1): the thesis's primes (Section 4.1)
+PROTH_SHAPES = [(1 << 16, 512, 16, 16), (1 << 20, 1 << 13, 16, 16), (1 << 24, 1 << 15, 32, 32),
+                (1 << 28, 1 << 18, 64, 32), (1 << 32, 1 << 22, 64, 32)]
+
+
+def test_proth_primality_matches_sympy(dk):
+    """dkss_plan_proth_rho rejects exactly the composite h 2^n + 1 (Proth's
+    theorem on the host) -- compared with sympy on every odd h below 200 for
+    a few n."""
+    sympy = pytest.importorskip("sympy")
+    M, m, u = 32, 16, 8
+    for n in (30, 61, 64, 78, 100):
+        for h in range(1, 200, 2):
+            p = (h << n) + 1
+            try:
+                dk.plan_proth_rho(2000, M, m, u, h, n)
+                ok = True
+            except dk.DkssError as e:
+                assert e.code == 2
+                ok = False
+            assert ok == sympy.isprime(p), (h, n)
+
+
+@pytest.mark.parametrize("shape", PROTH_SHAPES)
+def test_proth_ring_is_the_smallest_valid_prime(dk, shape):
+    """dkss_proth_ring: p = h 2^n + 1 prime, 2M | p - 1, above the coefficient
+    bound, m p < 2^(26 LR - 2) with the fewest limbs, and no smaller odd h at
+    that n gives such a prime (p just above the bound, Section 4.1)."""
+    n_bits, M, m, u = shape
+    h, n = dk.proth_ring(*shape)
+    p = (h << n) + 1
+    bound = M * (m // 2) * ((1 << u) - 1) ** 2
+    assert o.lucas_is_prime(p) and (p - 1) % (2 * M) == 0 and p > bound
+    lr = (n + 25) // 26 + (1 if n % 26 == 0 else 0)
+    assert n == max(26 * (lr - 1), (2 * M).bit_length() - 1)
+    assert m * p < 1 << (26 * lr - 2)
+    for hh in range(max(1, (bound >> n) + 1) | 1, h, 2):
+        assert not o.lucas_is_prime((hh << n) + 1) or ((hh << n) + 1) <= bound
+    rho, consts = dk.plan_proth_rho(n_bits, M, m, u, h, n)
+    assert consts["sparse"] == 1 and consts["LR"] == lr and consts["p"] == p and consts["z"] == 1
+    par = o.Params(n_bits, M, m, u, p, 1).check()
+    roots = o.compute_roots(par)
+    assert rho == roots.rho
+    assert (consts["zeta"], consts["omega"], consts["gamma"]) == (roots.zeta, roots.omega, roots.gamma)
+
+
+def test_proth_plan_argument_checks(dk):
+    with pytest.raises(dk.DkssError):
+        dk.plan_proth_rho(1 << 24, 1 << 15, 32, 32, 4, 78)      # h even
+    with pytest.raises(dk.DkssError):
+        dk.plan_proth_rho(1 << 24, 1 << 15, 32, 32, 3, 10)      # 2M does not divide 2^n
+    with pytest.raises(dk.DkssError):
+        dk.plan_proth_rho(1 << 24, 1 << 15, 32, 32, 1, 20)      # below the coefficient bound
+
+
+def test_decode_static_size_limit_on_host(dk):
+    """The allocation-free decode refuses products beyond its static scratch
+    (ceil(N/64) <= 2^27, N <= 2^33) before any device work: N = 2^33 + 64 gives
+    DKSS_EUNSUPPORTED, N = 2^33 passes the size check and then needs a device
+    (DKSS_ECUDA on this host).  Host only: with a GPU present the accepted
+    call would launch kernels on the placeholder pointers, so it is skipped."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("host-only check")
+    except ImportError:
+        pass
+    lib = dk.load()
+    c, out = 4096, 8192          # placeholders, never dereferenced on this host
+    assert lib.dkss_decode_static(c, (1 << 33) + 64, 1 << 28, 64, 32, 4, out, None) == 4
+    assert lib.dkss_decode_static(c, 1 << 33, 1 << 28, 64, 32, 4, out, None) == 5
