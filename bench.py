@@ -412,6 +412,8 @@ def run_ours(args):
     forms = compare_forms(args.workload, args.form, dev, flush, a, b, out, ms_per_step, args.form_budget_ms, A, B,
                           rab) \
         if (rank == 0 and not args.no_forms) else None
+    proth = proth_ring_time(args.workload, dev, flush, a, b, out, ms_per_step, args.form_budget_ms, A, B, rab) \
+        if (rank == 0 and not args.no_forms) else None
     del a, b, out
     others = other_workloads(args, dev, flush) if (rank == 0 and not args.no_others) else None
     batched = run_batched(args, dev, flush) if (rank == 0 and not args.no_batched) else None
@@ -440,6 +442,7 @@ def run_ours(args):
             "roofline": roofline,
             "cpu_baseline": cpu,
             "forms": forms,
+            "proth_ring": proth,
             "square": square,
             "workloads": others,
             "batched": batched,
@@ -528,6 +531,8 @@ def other_workloads(args, dev, flush):
                  "products_per_s": round(1 / (ms * 1e-3), 2), "bit_exact": bool(ok)}
         if not args.no_forms:
             entry["forms"] = compare_forms(name, "ntt", dev, flush, a, b, out, ms, args.form_budget_ms, A, B, rab)
+        if cfg[0] >= 1 << 24:
+            entry["proth_ring"] = proth_ring_time(name, dev, flush, a, b, out, ms, args.form_budget_ms, A, B, rab)
         res[name] = entry
         del a, b, out
     return res
@@ -570,6 +575,37 @@ def compare_forms(workload, main_form, dev, flush, a, b, out, ms_main, budget_ms
         res["tc_vs_imad_direct"] = round(res["direct"]["ms_per_step"] / res["int8tc"]["ms_per_step"], 3)
         res["tc_vs_imad_ntt"] = round(res["ntt"]["ms_per_step"] / res["int8tc"]["ms_per_step"], 3)
     return res
+
+
+def proth_ring_time(workload, dev, flush, a, b, out, ms_config, budget_ms, A, B, rab):
+    """The same product (same N, M, m, u) over the Proth ring Z/pZ, p = h 2^n + 1
+    of dkss_proth_ring (z = 1, the form of the thesis's primes), whose
+    Montgomery reductions need no digit products: device ms per product in the
+    default form, against the workload's own ring (p^z)."""
+    import torch
+
+    import paper_1503_04955_gb300 as dk
+
+    n_bits, M, m, u = syn.workload_params(workload)[:4]
+    try:
+        h, n = dk.proth_ring(n_bits, M, m, u)
+        plan = dk.Plan.proth(n_bits, M, m, u, h, n)
+    except dk.DkssError as e:
+        return {"unsupported": str(e)}
+    info = plan.info()
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(2):
+        plan.mul(a, b, out)
+    torch.cuda.synchronize(dev)
+    t = time_steps(lambda: plan.mul(a, b, out), 1, flush, stream)
+    steps = steps_for(t[0], budget_ms, lo=1, hi=50)
+    ms = sum(time_steps(lambda: plan.mul(a, b, out), steps, flush, stream)) / steps
+    ok = check_product(out.cpu().numpy().view(np.uint64), A, B, *rab)
+    plan.close()
+    return {"h": h, "n": n, "p_bits": ((h << n) + 1).bit_length(), "L": info["L"], "LR": info["LR"],
+            "sparse_reduction": bool(info["sparse"]), "ms_per_step": round(ms, 5), "steps": steps,
+            "gbit_s": round(2 * n_bits / (ms * 1e-3) / 1e9, 4),
+            "speedup_vs_config_ring": round(ms_config / ms, 3), "bit_exact": bool(ok)}
 
 
 def run_batched(args, dev, flush):

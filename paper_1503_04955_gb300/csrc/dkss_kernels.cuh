@@ -520,8 +520,8 @@ __device__ __forceinline__ void load_shifted_rr(uint32_t (&out)[LR], const uint3
 // element, xbuf = the CTA's exchange buffers (NttTeam<m>::NTEAMS of m
 // residues of LR words).
 // ---------------------------------------------------------------------------
-template <int m, int L, int LR, bool INV>
-__device__ __forceinline__ void twiddle_ntt_group(const LevelParams& prm, const ModRR<LR>& mr, uint64_t group, int op,
+template <int m, int L, int LR, bool INV, class MR>
+__device__ __forceinline__ void twiddle_ntt_group(const LevelParams& prm, const MR& mr, uint64_t group, int op,
                                                   uint32_t* xbuf) {
     using G = Geo<m, L>;
     using NT = NttTeam<m>;
@@ -571,10 +571,10 @@ __device__ __forceinline__ void twiddle_ntt_group(const LevelParams& prm, const 
     }
 }
 
-template <int m, int L, int LR, bool INV>
-__global__ void __launch_bounds__(kThreads, (LR >= 5 || m >= 64) ? 3 : 4) k_twiddle_ntt(LevelParams prm, ModRR<LR> mr) {
+template <int m, int L, int LR, bool INV, class MR = ModRR<LR>>
+__global__ void __launch_bounds__(kThreads, (LR >= 5 || m >= 64) ? 3 : 4) k_twiddle_ntt(LevelParams prm, MR mr) {
     extern __shared__ __align__(16) uint32_t smem[];
-    twiddle_ntt_group<m, L, LR, INV>(prm, mr, blockIdx.x, blockIdx.y, smem);
+    twiddle_ntt_group<m, L, LR, INV, MR>(prm, mr, blockIdx.x, blockIdx.y, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -586,8 +586,8 @@ __global__ void __launch_bounds__(kThreads, (LR >= 5 || m >= 64) ? 3 : 4) k_twid
 // level reads and writes the polynomial once.  smem: the column (2m elements)
 // and the teams' exchange buffers.
 // ---------------------------------------------------------------------------
-template <int m, int L, int LR>
-__device__ __forceinline__ void level_rmul_element(const LevelParams& prm, const ModRR<LR>& mr, const uint32_t* src,
+template <int m, int L, int LR, class MR>
+__device__ __forceinline__ void level_rmul_element(const LevelParams& prm, const MR& mr, const uint32_t* src,
                                                    uint32_t* dst, uint64_t e, uint32_t* buf, int lane, unsigned mask,
                                                    const uint32_t (&bn)[LR]) {
     using NT = NttTeam<m>;
@@ -617,8 +617,8 @@ __device__ __forceinline__ void level_rmul_element(const LevelParams& prm, const
     }
 }
 
-template <int m, int L, int LR, bool FIRST>
-__device__ __forceinline__ void level_fwd_ntt(const LevelParams& prm, const Mod<L>& md, const ModRR<LR>& mr,
+template <int m, int L, int LR, bool FIRST, class MR>
+__device__ __forceinline__ void level_fwd_ntt(const LevelParams& prm, const Mod<L>& md, const MR& mr,
                                               uint32_t* smem, uint64_t column, int op) {
     using G = Geo<m, L>;
     using NT = NttTeam<m>;
@@ -648,19 +648,19 @@ __device__ __forceinline__ void level_fwd_ntt(const LevelParams& prm, const Mod<
             }
             continue;
         }
-        level_rmul_element<m, L, LR>(prm, mr, src, dst, (uint64_t)v * l * prm.bp, buf, nt.lane, nt.mask, bn);
+        level_rmul_element<m, L, LR, MR>(prm, mr, src, dst, (uint64_t)v * l * prm.bp, buf, nt.lane, nt.mask, bn);
     }
 }
 
-template <int m, int L, int LR, bool FIRST>
+template <int m, int L, int LR, bool FIRST, class MR = ModRR<LR>>
 __global__ void __launch_bounds__(kThreads, m >= 64 ? 1 : 4)
-    k_level_fwd_ntt(LevelParams prm, Mod<L> md, ModRR<LR> mr) {
+    k_level_fwd_ntt(LevelParams prm, Mod<L> md, MR mr) {
     extern __shared__ __align__(16) uint32_t smem[];
-    level_fwd_ntt<m, L, LR, FIRST>(prm, md, mr, smem, blockIdx.x, blockIdx.y);
+    level_fwd_ntt<m, L, LR, FIRST, MR>(prm, md, mr, smem, blockIdx.x, blockIdx.y);
 }
 
-template <int m, int L, int LR>
-__device__ __forceinline__ void level_inv_ntt(const LevelParams& prm, const Mod<L>& md, const ModRR<LR>& mr,
+template <int m, int L, int LR, class MR>
+__device__ __forceinline__ void level_inv_ntt(const LevelParams& prm, const Mod<L>& md, const MR& mr,
                                               uint32_t* smem, uint64_t column) {
     using G = Geo<m, L>;
     using NT = NttTeam<m>;
@@ -689,7 +689,7 @@ __device__ __forceinline__ void level_inv_ntt(const LevelParams& prm, const Mod<
             }
             continue;
         }
-        level_rmul_element<m, L, LR>(prm, mr, src, dst, prm.P2 - (uint64_t)v * l * prm.bp, buf, nt.lane, nt.mask,
+        level_rmul_element<m, L, LR, MR>(prm, mr, src, dst, prm.P2 - (uint64_t)v * l * prm.bp, buf, nt.lane, nt.mask,
                                      bn);
     }
     __syncthreads();
@@ -702,11 +702,11 @@ __device__ __forceinline__ void level_inv_ntt(const LevelParams& prm, const Mod<
     }
 }
 
-template <int m, int L, int LR>
+template <int m, int L, int LR, class MR = ModRR<LR>>
 __global__ void __launch_bounds__(kThreads, m >= 64 ? 1 : 4)
-    k_level_inv_ntt(LevelParams prm, Mod<L> md, ModRR<LR> mr) {
+    k_level_inv_ntt(LevelParams prm, Mod<L> md, MR mr) {
     extern __shared__ __align__(16) uint32_t smem[];
-    level_inv_ntt<m, L, LR>(prm, md, mr, smem, blockIdx.x);
+    level_inv_ntt<m, L, LR, MR>(prm, md, mr, smem, blockIdx.x);
 }
 
 template <int m, int L, int LR>
@@ -721,8 +721,8 @@ constexpr size_t level_ntt_smem_bytes() {
 // alpha^(2m/len)).  For a square the caller passes poly_words = 0 (b is a) and
 // square = 1: the NTT form then reuses a's evaluations for both factors.
 // ---------------------------------------------------------------------------
-template <int m, int L, int LR, int FORM>
-__device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>& md, const ModRR<LR>& mr,
+template <int m, int L, int LR, int FORM, class MR>
+__device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>& md, const MR& mr,
                                             uint32_t* smem, uint64_t block) {
     using G = Geo<m, L>;
     const int n = (int)prm.len;
@@ -864,10 +864,10 @@ __device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>
     }
 }
 
-template <int m, int L, int LR, int FORM>
-__global__ void __launch_bounds__(kThreads, FORM == kFormNtt ? (LR >= 5 ? 2 : 3) : 1) k_final_pointwise(LevelParams prm, Mod<L> md, ModRR<LR> mr) {
+template <int m, int L, int LR, int FORM, class MR = ModRR<LR>>
+__global__ void __launch_bounds__(kThreads, FORM == kFormNtt ? (LR >= 5 ? 2 : 3) : 1) k_final_pointwise(LevelParams prm, Mod<L> md, MR mr) {
     extern __shared__ __align__(16) uint32_t smem[];
-    final_block<m, L, LR, FORM>(prm, md, mr, smem, blockIdx.x);
+    final_block<m, L, LR, FORM, MR>(prm, md, mr, smem, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------

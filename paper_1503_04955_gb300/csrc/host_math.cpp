@@ -131,6 +131,59 @@ uint64_t smallest_generator(uint64_t p) {
     return 0;
 }
 
+int jacobi(u128 a, u128 n) {
+    a %= n;
+    int t = 1;
+    while (a != 0) {
+        while ((a & 1) == 0) {
+            a >>= 1;
+            const unsigned r = (unsigned)(n & 7);
+            if (r == 3 || r == 5) t = -t;
+        }
+        u128 tmp = a;
+        a = n;
+        n = tmp;
+        if ((a & 3) == 3 && (n & 3) == 3) t = -t;
+        a %= n;
+    }
+    return n == 1 ? t : 0;
+}
+
+// Proth's theorem: p = h 2^n + 1 with h < 2^n is prime iff a^((p-1)/2) = -1
+// (mod p) for some a.  With a quadratic non-residue a ((a/p) = -1, Jacobi
+// symbol) the test is decisive: for prime p Euler's criterion gives -1.  A
+// composite p with no such a below 2^16 (a perfect square, for example) is
+// rejected as well.
+bool proth_is_prime(uint64_t h, uint32_t n) {
+    if (h == 0 || (h & 1) == 0 || n == 0 || n >= 126) return false;
+    if (n < 64 && h >= ((uint64_t)1 << n)) return false;
+    const u128 p = ((u128)h << n) + 1;
+    if ((p >> 126) != 0) return false;
+    if (p < 4) return p == 2 || p == 3;
+    MontCtx c(p);
+    for (uint64_t a = 3; a < 65536; ++a) {
+        const int j = jacobi(a, p);
+        if (j == 0) return (u128)a == p;     // a shares a factor with p
+        if (j == 1) continue;
+        return c.pow(c.to(a), (p - 1) / 2) == c.sub(0, c.r1);   // a^((p-1)/2) = -1
+    }
+    return false;
+}
+
+uint64_t proth_generator(uint64_t h, uint32_t n) {
+    const u128 p = ((u128)h << n) + 1;
+    std::vector<uint64_t> f = prime_factors_u64(h);   // odd prime factors of p - 1
+    f.push_back(2);
+    MontCtx c(p);
+    for (uint64_t g = 2; g < 65536; ++g) {
+        bool ok = true;
+        for (uint64_t q : f)
+            if (c.pow(c.to(g), (p - 1) / q) == c.r1) { ok = false; break; }
+        if (ok) return g;
+    }
+    return 0;
+}
+
 u128 inverse_mod(u128 x, u128 q, u128 phi_minus_one) {
     MontCtx c(q);
     return c.from(c.pow(c.to(x), phi_minus_one));

@@ -37,6 +37,12 @@ uint64_t smallest_generator(uint64_t p);
 u128 hensel_lift(uint64_t zeta, uint64_t p, uint32_t z);  // (p-1)-th root of unity mod p^z
 u128 inverse_mod(u128 x, u128 q, u128 phi_minus_one);     // x^(phi-1) mod q
 
+// Proth numbers p = h 2^n + 1 (h odd, h < 2^n, p < 2^126): the thesis's
+// primes (Section 4.1, its table of primes of that form).
+int jacobi(u128 a, u128 n);                          // Jacobi symbol (a/n), n odd
+bool proth_is_prime(uint64_t h, uint32_t n);         // Proth's theorem with a non-residue witness
+uint64_t proth_generator(uint64_t h, uint32_t n);    // smallest generator of F_p^*, p - 1 = h 2^n
+
 // Element of R: m residues in Montgomery form.
 typedef std::vector<u128> Relem;
 Relem r_mul(const MontCtx& c, const Relem& x, const Relem& y);     // negacyclic product

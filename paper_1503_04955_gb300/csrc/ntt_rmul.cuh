@@ -103,6 +103,41 @@ DKSS_HD void mmul(uint32_t (&r)[LR], const uint32_t (&a)[LR], const uint32_t (&b
     }
 }
 
+// A modulus p^z = 1 (mod 2^26) whose 26-bit limbs 1 .. LR-2 are zero: a Proth
+// prime p = h 2^n + 1 with z = 1 and 26 (LR-1) <= n (the thesis's primes,
+// Section 4.1; its outlook proposes exploiting their form in the modular
+// reductions).  Then -(p^z)^-1 = -1 (mod 2^26): the Montgomery digit of a
+// column is its negated low 26 bits (no product), and adding digit * p^z
+// touches the column itself and the top limb only (one limb product per
+// digit instead of LR + 1).  The digits and the result are those of mmul with
+// the same modulus; only products by zero limbs are left out.
+template <int LR>
+struct ModRRSparse : ModRR<LR> {};
+
+template <int LR>
+DKSS_HD void mmul(uint32_t (&r)[LR], const uint32_t (&a)[LR], const uint32_t (&b)[LR],
+                                     const ModRRSparse<LR>& md) {
+    uint64_t col[2 * LR];
+#pragma unroll
+    for (int i = 0; i < 2 * LR; ++i) col[i] = 0;
+    mac_cols<LR>(col, a, b);
+    const uint32_t qtop = md.q[LR - 1];
+#pragma unroll
+    for (int i = 0; i < LR; ++i) {
+        const uint32_t qi = (0u - (uint32_t)col[i]) & kM26;
+        const uint64_t c = col[i] + qi;                       // low 26 bits become 0
+        col[i + 1] += c >> 26;
+        col[i + LR - 1] += (uint64_t)qi * qtop;
+    }
+    uint64_t carry = 0;
+#pragma unroll
+    for (int i = 0; i < LR; ++i) {
+        const uint64_t v = col[LR + i] + carry;
+        r[i] = i + 1 < LR ? ((uint32_t)v & kM26) : (uint32_t)v;
+        carry = v >> 26;
+    }
+}
+
 // canonical residue of normalised limbs of a value below 2q
 template <int LR>
 DKSS_HD void canon(uint32_t (&r)[LR], const uint32_t (&x)[LR], const ModRR<LR>& md) {
@@ -193,9 +228,9 @@ __device__ __forceinline__ void ntt_exchange(uint32_t (&v)[4][LR], uint32_t* buf
 // Forward negacyclic transform (lazy).  On entry slot j of lane l holds
 // coefficient l + j m/4; on exit the evaluations at bit-reversed positions
 // 4l + j.
-template <int m, int LR>
+template <int m, int LR, class MD>
 __device__ __forceinline__ void ntt_forward(uint32_t (&v)[4][LR], uint32_t* buf, int lane, unsigned mask,
-                                            const uint32_t* cst, const ModRR<LR>& md) {
+                                            const uint32_t* cst, const MD& md) {
     using NL = NttLayout<m>;
     constexpr int LG = NL::LG;
     uint32_t bf[LR];
@@ -229,9 +264,9 @@ __device__ __forceinline__ void ntt_forward(uint32_t (&v)[4][LR], uint32_t* buf,
 // times R').  With RAW_LO (c = 1, already folded into the inputs) the last
 // stage leaves slots 0 and 1 as the plain sums, unreduced (reduce_raw), and
 // multiplies only slots 2 and 3 by cst[hi_c].
-template <int m, int LR, bool RAW_LO = false>
+template <int m, int LR, bool RAW_LO = false, class MD = ModRR<LR>>
 __device__ __forceinline__ void ntt_backward(uint32_t (&v)[4][LR], uint32_t* buf, int lane, unsigned mask,
-                                             const uint32_t* cst, int lo_c, int hi_c, const ModRR<LR>& md) {
+                                             const uint32_t* cst, int lo_c, int hi_c, const MD& md) {
     using NL = NttLayout<m>;
     constexpr int LG = NL::LG;
     int h = 1;
