@@ -1,15 +1,17 @@
 // Decoding and carry propagation without any allocation (dkss_decode_static).
 //
-// Callers that must not allocate device memory at the time of the call -- code
-// running while a CUDA stream is being captured into a graph (where
-// cudaMalloc/cudaFree are not allowed), or a real-time loop whose memory is
-// fixed up front -- can still turn a product polynomial into the product's
-// words.  The carry scan's scratch (one word per tile of 2048 output windows
+// Callers that must not allocate device memory at the time of the call can
+// still turn a product polynomial into the product's words: a latency-bound
+// loop whose device memory is fixed before it starts (cudaMalloc and cudaFree
+// may synchronize the device and stall its other streams), or code running
+// inside a framework that owns the device's memory pool and gives its plugins
+// no allocator.  The carry scan's scratch (one word per tile of 2048 output windows
 // plus one status word) lives in a file-scope device array instead of
 // caller- or plan-owned memory.  Every GPU that loads the library holds this
 // array (1 MiB) until the process exits.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 
 #include "../../include/dkss.h"
@@ -25,8 +27,9 @@ static __device__ __align__(256) uint32_t g_decode_scratch[kStaticTiles + 1];
 
 // Device address of g_decode_scratch per device, looked up once per device
 // with that device current (a host-side reference to the symbol is not a
-// device address and must never reach a kernel).
-uint32_t* g_scratch_ptr[kMaxDevices] = {nullptr};
+// device address and must never reach a kernel).  Atomic: two host threads
+// may make their first calls on a device at once (both store the same value).
+std::atomic<uint32_t*> g_scratch_ptr[kMaxDevices] = {};
 
 template <int L>
 void launch(const dkss::DecodeParams& dp, uint32_t u, cudaStream_t st) {
@@ -50,12 +53,13 @@ extern "C" dkss_status dkss_decode_static(const uint32_t* c, uint64_t n_bits, ui
     if (n_tiles > kStaticTiles) return DKSS_EUNSUPPORTED;   // product longer than the static scratch covers
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || (uint64_t)dev >= kMaxDevices) return DKSS_ECUDA;
-    if (!g_scratch_ptr[dev]) {
+    uint32_t* scratch = g_scratch_ptr[dev].load(std::memory_order_acquire);
+    if (!scratch) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_decode_scratch) != cudaSuccess || !p) return DKSS_ECUDA;
-        g_scratch_ptr[dev] = static_cast<uint32_t*>(p);
+        scratch = static_cast<uint32_t*>(p);
+        g_scratch_ptr[dev].store(scratch, std::memory_order_release);
     }
-    uint32_t* scratch = g_scratch_ptr[dev];
     cudaStream_t st = (cudaStream_t)stream;
     // tile aggregates are written before they are read; only the status word must start at zero
     if (cudaMemsetAsync(scratch + kStaticTiles, 0, sizeof(uint32_t), st) != cudaSuccess) return DKSS_ECUDA;

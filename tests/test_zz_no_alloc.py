@@ -1,9 +1,9 @@
 """dkss_decode_static, the entry point that allocates nothing (needs a GPU).
 
-Callers that cannot allocate device memory when they call -- code running while
-a stream is captured into a CUDA graph, or a real-time loop with memory fixed up
-front -- decode a product polynomial with scratch held in a file-scope device
-array.  Its output must equal what dkss_mul produces for the same product, on
+Callers that cannot allocate device memory when they call -- a latency-bound
+loop whose device memory is fixed before it starts, or code inside a framework
+that owns the device's memory pool -- decode a product polynomial with scratch
+held in a file-scope device array.  Its output must equal what dkss_mul produces for the same product, on
 two calls in a row (the scratch keeps the previous call's contents).  The file
 sorts last so that a failure here comes after every other test has run.
 """
