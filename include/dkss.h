@@ -215,21 +215,31 @@ typedef struct {
 typedef struct dkss_batch_s* dkss_batch_t;
 
 enum {
-    DKSS_BATCH_RULE = 32,     /* size-class parameters by rule instead of measurement */
-    DKSS_BATCH_NO_GRAPH = 64  /* launch the persistent kernel directly, not from a graph */
+    DKSS_BATCH_RULE = 32,      /* size-class parameters by rule instead of measurement */
+    DKSS_BATCH_NO_GRAPH = 64,  /* launch the persistent kernel directly, not from a graph */
+    DKSS_BATCH_PROTH = 128,    /* every class over its own Proth prime (dkss_plan_proth) */
+    DKSS_BATCH_NO_PROTH = 256  /* every class over the configured primes */
 };
 
 /*
  * Plan a batch of `count` independent products whose operands have the given
  * bit lengths (each job is Section 3.2 on its own).  Jobs are grouped into
- * size classes (operands up to the next power of two, at least 2^12 bits)
- * that share the ring m = 32, p = 65537, z = 5 and differ in M and u; each
- * class's (M, u) comes from an autotuner that times one product of the class
- * with u = 32 and with u = 16 on the current device (cached per device and
- * class; DKSS_BATCH_RULE takes the largest valid u instead, the thesis's own
- * rule of Section 4.1).  The plan owns every job's workspace and the class
- * tables, and records one cooperative persistent-kernel launch in a CUDA
- * graph.  Operands up to 2^21 bits; count <= 2^20.
+ * size classes (operands up to the next power of two, at least 2^12 bits).
+ * All classes share the limb layout of one kernel (m = 32, residues of three
+ * 32-bit words, products in four 26-bit limbs); each class has its own M, u
+ * and ring Z/p^zZ in that layout: either the smallest p^z above its
+ * coefficient bound from the primes dkss_plan_candidates draws from, or its
+ * own Proth prime p = h 2^n + 1 (z = 1, dkss_proth_ring), whose reductions
+ * are cheaper (Section 4.1 and the outlook of Section 5.1).  Per class the
+ * autotuner times one product with u = 32 and with u = 16 on the current
+ * device (cached per device, class and ring family) and keeps the faster;
+ * the ring family of the batch is the one with the smaller sum over classes
+ * of jobs x time (DKSS_BATCH_PROTH, DKSS_BATCH_NO_PROTH force one;
+ * DKSS_BATCH_RULE takes the configured primes and the largest valid u, the
+ * thesis's own rule of Section 4.1, without timing).  The plan owns every
+ * job's workspace and the class tables, and records one cooperative
+ * persistent-kernel launch in a CUDA graph.  Operands up to 2^21 bits;
+ * count <= 2^20.
  * Errors: DKSS_EINVAL, DKSS_EUNSUPPORTED (operand too long), DKSS_ENOMEM,
  * DKSS_ECUDA.  On error *batch is NULL.
  */
@@ -245,9 +255,10 @@ dkss_status dkss_batch_plan(dkss_batch_t* batch, const uint64_t* n_bits, size_t 
 dkss_status dkss_batch_run(dkss_batch_t batch, const dkss_job* jobs, dkss_stream_t stream);
 
 /*
- * Parameters chosen for job `job`: params[0..8] = M, m, u, p, z, the class's
- * largest operand bits, transform levels, persistent grid size, 1 if the
- * launch is a graph.  n is the length of params.
+ * Parameters chosen for job `job`: params[0..12] = M, m, u, p (low word), z,
+ * the class's largest operand bits, transform levels, persistent grid size,
+ * 1 if the launch is a graph, p's high word, 1 for a Proth ring, and its h
+ * and n (p = h 2^n + 1; 0 otherwise).  n is the length of params.
  */
 dkss_status dkss_batch_job_params(dkss_batch_t batch, size_t job, uint64_t* params, size_t n);
 

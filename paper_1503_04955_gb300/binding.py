@@ -311,6 +311,8 @@ def ll_step(c, s, p, stream=None):
 
 BATCH_RULE = 32
 BATCH_NO_GRAPH = 64
+BATCH_PROTH = 128
+BATCH_NO_PROTH = 256
 
 
 class _Job(ctypes.Structure):
@@ -343,7 +345,7 @@ def _jobs_array(a_list, b_list, out_list, n_bits):
 class Batch:
     """A planned batch of products of uneven sizes (dkss_batch_plan)."""
 
-    PARAM_NAMES = ["M", "m", "u", "p", "z", "class_bits", "levels", "grid", "graph"]
+    PARAM_NAMES = ["M", "m", "u", "p_lo", "z", "class_bits", "levels", "grid", "graph", "p_hi", "proth", "h", "n"]
 
     def __init__(self, n_bits, flags=0):
         lib = _load_batch()
@@ -355,9 +357,19 @@ class Batch:
         self._h = h
 
     def job_params(self, j):
-        v = np.zeros(9, dtype=np.uint64)
-        _check(_load_batch().dkss_batch_job_params(self._h, j, v.ctypes.data, 9), "dkss_batch_job_params")
-        return dict(zip(self.PARAM_NAMES, [int(x) for x in v]))
+        v = np.zeros(13, dtype=np.uint64)
+        _check(_load_batch().dkss_batch_job_params(self._h, j, v.ctypes.data, 13), "dkss_batch_job_params")
+        d = dict(zip(self.PARAM_NAMES, [int(x) for x in v]))
+        d["p"] = d.pop("p_lo") | (d.pop("p_hi") << 64)
+        return d
+
+    def class_plan(self, j, n_bits=None):
+        """A single-product plan with job j's class parameters (for comparison)."""
+        d = self.job_params(j)
+        n_bits = n_bits or self.n_bits[j]
+        if d["proth"]:
+            return Plan.proth(n_bits, d["M"], d["m"], d["u"], d["h"], d["n"])
+        return Plan(n_bits, d["M"], d["m"], d["u"], d["p"], d["z"])
 
     def run(self, a_list, b_list, out_list, stream=None):
         """out_list[j] = a_list[j] * b_list[j] (CUDA tensors of 64-bit words)."""

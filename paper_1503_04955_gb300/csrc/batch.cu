@@ -13,6 +13,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "batch.cuh"
@@ -22,16 +23,24 @@ using dkss_host::u128;
 
 namespace {
 
-// The residue ring shared by all classes of a batch: m = 32, p = 65537 = 2^16 + 1
-// (2M | p - 1 for every 2M <= 2^16), z = 5, so p^z ~ 2^80 exceeds the largest
-// coefficient M (m/2) (2^u - 1)^2 for M <= 4096 with u = 32; L = 3, LR = 4.
-constexpr uint32_t kBm = 32, kBL = 3, kBLR = 4, kBz = 5;
-constexpr uint64_t kBp = 65537;
+// The limb layout shared by all classes of a batch (one kernel instantiation):
+// m = 32, residues of L = 3 32-bit words, products in LR = 4 26-bit limbs.
+// Each class has its own M, u and ring Z/p^zZ with that layout.
+constexpr uint32_t kBm = 32, kBL = 3, kBLR = 4;
+
+// A class's ring: (p, z) with p from the candidate primes, or a Proth prime
+// p = h 2^n + 1 with z = 1 (dkss_plan_proth).
+struct Ring {
+    uint64_t p = 0, h = 0;
+    uint32_t z = 0, n = 0;
+    bool proth = false;
+};
 
 struct ClassParams {
     uint64_t M = 0;
     uint32_t u = 0;
-    double ms[2] = {-1.0, -1.0};   // measured time per product for u = 32, 16 (autotuned)
+    Ring ring;
+    double ms = -1.0;   // measured device time of one product of the class (autotuned)
 };
 
 struct ClassTables {
@@ -46,30 +55,67 @@ uint64_t next_pow2(uint64_t x) {
     return r;
 }
 
-u128 ring_q() {
-    u128 q = 1;
-    for (uint32_t i = 0; i < kBz; ++i) q *= kBp;
-    return q;
+dkss_status class_host(dkss_plan_s* pl, uint64_t N, uint64_t M, uint32_t u, const Ring& r) {
+    return r.proth ? dkss_planning::plan_host_proth(pl, N, M, kBm, u, r.h, r.n)
+                   : dkss_planning::plan_host(pl, N, M, kBm, u, r.p, r.z);
 }
 
-// Smallest valid M for u, or 0: M (m/2) u >= N, 2M > 2m (one radix-2m level at
-// least), and the coefficient bound below p^z.
+bool in_layout(const dkss_plan_s& h) { return h.L == kBL && h.LR == kBLR && h.ntt_ok; }
+
+// Smallest M for u: M (m/2) u >= N and 2M > 2m (one radix-2m level at least).
 uint64_t class_M(uint64_t N, uint32_t u) {
     uint64_t M = next_pow2((N + (kBm / 2) * u - 1) / ((kBm / 2) * u));
-    if (M < 2 * kBm) M = 2 * kBm;
-    const u128 umax = ((u128)1 << u) - 1;
-    if ((u128)M * (kBm / 2) * umax * umax >= ring_q() || 2 * M > (1u << 16)) return 0;
-    return M;
+    return M < 2 * kBm ? 2 * kBm : M;
+}
+
+// The class's ring in the batch layout: with proth, the Proth prime of
+// dkss_proth_ring at LR = 4; otherwise, of the candidate primes with 2M | p-1,
+// the smallest p^z above the coefficient bound whose plan has the layout
+// (p^z just above the bound, the thesis's choice of Section 4.1).
+bool class_ring(uint64_t N, uint64_t M, uint32_t u, bool proth, Ring* out) {
+    if (proth) {
+        Ring r;
+        r.proth = true;
+        r.z = 1;
+        if (!dkss_planning::proth_ring_lr(N, M, kBm, u, kBLR, &r.h, &r.n)) return false;
+        dkss_plan_s pl;
+        if (class_host(&pl, N, M, u, r) != DKSS_OK || !in_layout(pl)) return false;
+        r.p = (uint64_t)pl.p;
+        *out = r;
+        return true;
+    }
+    bool found = false;
+    u128 best = 0;
+    for (size_t i = 0; i < dkss_planning::kNumCandidatePrimes; ++i) {
+        const uint64_t p = dkss_planning::kCandidatePrimes[i];
+        if ((p - 1) % (2 * M) != 0) continue;
+        for (uint32_t z = 1; z <= 8; ++z) {
+            dkss_plan_s pl;
+            const dkss_status s = dkss_planning::plan_host(&pl, N, M, kBm, u, p, z);
+            if (s != DKSS_OK || !in_layout(pl)) continue;
+            if (!found || pl.q < best) {
+                best = pl.q;
+                out->p = p;
+                out->z = z;
+                out->proth = false;
+                found = true;
+            }
+            break;
+        }
+    }
+    return found;
 }
 
 std::mutex g_tune_mu;
-std::map<std::pair<int, uint64_t>, ClassParams> g_tune_cache;   // (device, class N) -> choice
+std::map<std::tuple<int, uint64_t, bool>, ClassParams> g_tune_cache;   // (device, class N, proth) -> choice
 
-// Device time of one product of the class with (M, u): plan, 2 warm-up calls,
-// median of 5 timed calls.
-double time_candidate(uint64_t N, uint64_t M, uint32_t u) {
+// Device time of one product of the class with (M, u, ring): plan, 2 warm-up
+// calls, median of 5 timed calls.
+double time_candidate(uint64_t N, uint64_t M, uint32_t u, const Ring& r) {
     dkss_plan_t pl = nullptr;
-    if (dkss_plan(&pl, N, M, kBm, u, kBp, kBz, 0) != DKSS_OK) return -1.0;
+    const dkss_status ps = r.proth ? dkss_plan_proth(&pl, N, M, kBm, u, r.h, r.n, 0)
+                                   : dkss_plan(&pl, N, M, kBm, u, r.p, r.z, 0);
+    if (ps != DKSS_OK) return -1.0;
     const size_t nw = (N + 63) / 64;
     uint64_t* buf = nullptr;
     double result = -1.0;
@@ -111,40 +157,53 @@ double time_candidate(uint64_t N, uint64_t M, uint32_t u) {
     return result;
 }
 
-// Parameters of the class of operands up to N bits: by the rule (largest valid
-// u, the thesis's "maximise u" heuristic of Section 4.1) or by measurement.
-ClassParams choose_class(int device, uint64_t N, bool autotune) {
+// Parameters of the class of operands up to N bits, over the configured
+// primes or over Proth primes: by the rule (the largest u with a ring in the
+// layout, the thesis's "maximise u" of Section 4.1) or by timing u = 32 and
+// u = 16, each with its ring.
+ClassParams choose_class(int device, uint64_t N, bool proth, bool autotune) {
     ClassParams c;
     const uint32_t us[2] = {32, 16};
     if (!autotune) {
-        for (uint32_t u : us)
-            if ((c.M = class_M(N, u))) {
+        for (uint32_t u : us) {
+            const uint64_t M = class_M(N, u);
+            Ring r;
+            if (2 * M <= (1u << 16) && class_ring(N, M, u, proth, &r)) {
+                c.M = M;
                 c.u = u;
+                c.ring = r;
                 return c;
             }
+        }
         return c;
     }
+    const auto key = std::make_tuple(device, N, proth);
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
-        auto it = g_tune_cache.find({device, N});
+        auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) return it->second;
     }
-    double best = -1.0;
-    for (int i = 0; i < 2; ++i) {
-        const uint64_t M = class_M(N, us[i]);
-        if (!M) continue;
-        const double t = time_candidate(N, M, us[i]);
-        c.ms[i] = t;
-        if (t > 0 && (best < 0 || t < best)) {
-            best = t;
+    for (uint32_t u : us) {
+        const uint64_t M = class_M(N, u);
+        Ring r;
+        if (2 * M > (1u << 16) || !class_ring(N, M, u, proth, &r)) continue;
+        const double t = time_candidate(N, M, u, r);
+        if (t > 0 && (c.ms < 0 || t < c.ms)) {
+            c.ms = t;
             c.M = M;
-            c.u = us[i];
+            c.u = u;
+            c.ring = r;
         }
     }
-    if (!c.M) return choose_class(device, N, false);
+    if (!c.M) return choose_class(device, N, proth, false);
     std::lock_guard<std::mutex> g(g_tune_mu);
-    g_tune_cache[{device, N}] = c;
+    g_tune_cache[key] = c;
     return c;
+}
+
+const void* batch_kernel(bool proth) {
+    if (proth) return (const void*)dkss::k_batch<kBm, kBL, kBLR, dkss::ModRRSparse<kBLR>>;
+    return (const void*)dkss::k_batch<kBm, kBL, kBLR, dkss::ModRR<kBLR>>;
 }
 
 }  // namespace
@@ -166,8 +225,7 @@ struct dkss_batch_s {
     uint32_t* d_work = nullptr;
     uint32_t* d_agg = nullptr;
     uint32_t* d_status = nullptr;
-    dkss::Mod<kBL> md{};
-    dkss::ModRR<kBLR> mr{};
+    bool proth = false;                            // every class over a Proth prime (sparse reduction)
     int grid = 0;
     size_t smem = 0;
     cudaGraph_t graph = nullptr;
@@ -198,9 +256,9 @@ void batch_free(dkss_batch_s* b) {
 
 dkss_status launch_batch(dkss_batch_s* b, cudaStream_t st) {
     uint32_t count = (uint32_t)b->n_bits.size();
-    void* args[] = {&b->d_jobs, &b->d_stages, &b->n_stages, &count, &b->md, &b->mr};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void*)dkss::k_batch<kBm, kBL, kBLR>, dim3(b->grid),
-                                                dim3(dkss::kThreads), args, b->smem, st);
+    void* args[] = {&b->d_jobs, &b->d_stages, &b->n_stages, &count};
+    cudaError_t e = cudaLaunchCooperativeKernel(batch_kernel(b->proth), dim3(b->grid), dim3(dkss::kThreads), args,
+                                                b->smem, st);
     return e == cudaSuccess ? DKSS_OK : DKSS_ECUDA;
 }
 
@@ -229,10 +287,27 @@ dkss_status dkss_batch_plan(dkss_batch_t* out, const uint64_t* n_bits, size_t co
         }
         cls.emplace(std::max<uint64_t>(4096, next_pow2(n)), 0);
     }
+    std::map<uint64_t, uint64_t> jobs_per_class;
+    for (uint64_t n : b->n_bits) ++jobs_per_class[std::max<uint64_t>(4096, next_pow2(n))];
+    // rings: the configured primes or Proth primes for every class (one kernel
+    // instantiation per batch); by flag, by the rule (configured primes), or
+    // the set with the smaller sum over classes of jobs x measured time
+    const bool autotune = !(flags & DKSS_BATCH_RULE);
+    bool proth = (flags & DKSS_BATCH_PROTH) != 0;
+    if (autotune && !(flags & (DKSS_BATCH_PROTH | DKSS_BATCH_NO_PROTH))) {
+        double cost[2] = {0, 0};
+        for (int mode = 0; mode < 2; ++mode)
+            for (auto& kv : cls) {
+                const ClassParams c = choose_class(b->device, kv.first, mode == 1, true);
+                cost[mode] += (c.M && c.ms > 0) ? c.ms * (double)jobs_per_class[kv.first] : 1e30;
+            }
+        proth = cost[1] < cost[0];
+    }
+    b->proth = proth;
     for (auto& kv : cls) {
         kv.second = (uint32_t)b->class_N.size();
         b->class_N.push_back(kv.first);
-        ClassParams c = choose_class(b->device, kv.first, !(flags & DKSS_BATCH_RULE));
+        ClassParams c = choose_class(b->device, kv.first, proth, autotune);
         if (!c.M) {
             delete b;
             return DKSS_EUNSUPPORTED;
@@ -245,9 +320,8 @@ dkss_status dkss_batch_plan(dkss_batch_t* out, const uint64_t* n_bits, size_t co
     dkss_status s = DKSS_OK;
     for (size_t c = 0; c < b->class_N.size() && s == DKSS_OK; ++c) {
         auto t = std::make_unique<ClassTables>();
-        s = dkss_planning::plan_host(&t->host, b->class_N[c], b->class_params[c].M, kBm, b->class_params[c].u, kBp,
-                                     kBz);
-        if (s == DKSS_OK && (t->host.L != kBL || t->host.LR != kBLR || !t->host.ntt_ok)) s = DKSS_EUNSUPPORTED;
+        s = class_host(&t->host, b->class_N[c], b->class_params[c].M, b->class_params[c].u, b->class_params[c].ring);
+        if (s == DKSS_OK && (!in_layout(t->host) || t->host.q_sparse != b->proth)) s = DKSS_EUNSUPPORTED;
         if (s == DKSS_OK) {
             std::vector<uint32_t> ev, nt;
             dkss_planning::build_eval_table(&t->host, ev, true);
@@ -264,12 +338,6 @@ dkss_status dkss_batch_plan(dkss_batch_t* out, const uint64_t* n_bits, size_t co
         batch_free(b);
         return s;
     }
-    const dkss_plan_s& h0 = b->tables[0]->host;
-    for (int i = 0; i < (int)kBL; ++i) b->md.q[i] = h0.q_limbs[i];
-    b->md.nprime = h0.nprime;
-    b->md.nsub = h0.nsub;
-    for (int i = 0; i < (int)kBLR; ++i) b->mr.q[i] = h0.q_rr[i];
-    b->mr.nprime = h0.nprime26;
 
     // workspaces, carry scratch, job table
     uint64_t work_words = 0, agg_words = 0;
@@ -328,6 +396,11 @@ dkss_status dkss_batch_plan(dkss_batch_t* out, const uint64_t* n_bits, size_t co
         dp.db += 1;
         jb.col_levels = h.col_levels;
         jb.r_last = (uint32_t)h.r_last;
+        for (int i = 0; i < 4; ++i) jb.q32[i] = h.q_limbs[i];
+        jb.nprime32 = h.nprime;
+        jb.nsub = h.nsub;
+        for (int i = 0; i < 5; ++i) jb.q26[i] = h.q_rr[i];
+        jb.nprime26 = h.nprime26;
         max_levels = std::max(max_levels, h.col_levels);
     }
 
@@ -389,9 +462,9 @@ dkss_status dkss_batch_plan(dkss_batch_t* out, const uint64_t* n_bits, size_t co
     int per_sm = 0, sms = 0, optin = 0;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device) != cudaSuccess ||
         (int)b->smem > optin ||
-        cudaFuncSetAttribute(dkss::k_batch<kBm, kBL, kBLR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem) !=
+        cudaFuncSetAttribute(batch_kernel(b->proth), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem) !=
             cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dkss::k_batch<kBm, kBL, kBLR>, dkss::kThreads, b->smem) !=
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel(b->proth), dkss::kThreads, b->smem) !=
             cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess || per_sm < 1) {
         cudaGetLastError();
@@ -446,9 +519,10 @@ dkss_status dkss_batch_job_params(dkss_batch_t b, size_t job, uint64_t* params, 
     if (!b || job >= b->n_bits.size() || !params) return DKSS_EINVAL;
     const ClassParams& c = b->class_params[b->job_class[job]];
     const ClassTables& t = *b->tables[b->job_class[job]];
-    const uint64_t v[9] = {c.M, kBm, c.u, kBp, kBz, b->class_N[b->job_class[job]], (uint64_t)(t.host.col_levels + 1),
-                           (uint64_t)b->grid, (uint64_t)(b->exec != nullptr)};
-    for (size_t i = 0; i < n && i < 9; ++i) params[i] = v[i];
+    const uint64_t v[13] = {c.M, kBm, c.u, (uint64_t)t.host.p, c.ring.z, b->class_N[b->job_class[job]],
+                            (uint64_t)(t.host.col_levels + 1), (uint64_t)b->grid, (uint64_t)(b->exec != nullptr),
+                            (uint64_t)(t.host.p >> 64), (uint64_t)c.ring.proth, c.ring.h, c.ring.n};
+    for (size_t i = 0; i < n && i < 13; ++i) params[i] = v[i];
     return DKSS_OK;
 }
 

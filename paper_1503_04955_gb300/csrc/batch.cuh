@@ -1,7 +1,8 @@
 // Many products of uneven sizes in one persistent kernel launch.
 //
-// A batch groups its jobs into size classes that share the residue ring (m,
-// p, z, hence L and LR) and differ in M and u.  The persistent kernel walks a
+// A batch groups its jobs into size classes that share the limb layout (m,
+// L, LR) and each have their own ring (p, z), M and u; the ring's constants
+// travel with every job.  The persistent kernel walks a
 // host-built list of stages (per level the fused column DFT and its
 // R-multiplications, forward; the fused last level with the componentwise
 // products; per level backwards the fused R-multiplications and column DFT;
@@ -40,6 +41,11 @@ struct BatchJob {
     DecodeParams dp;
     uint32_t col_levels;
     uint32_t r_last;
+    // the job's ring Z/p^zZ: p^z in 32-bit limbs (Mod) and 26-bit limbs (ModRR)
+    uint32_t q32[4];
+    uint32_t nprime32, nsub;
+    uint32_t q26[5];
+    uint32_t nprime26;
 };
 
 struct BatchStage {
@@ -74,9 +80,9 @@ __host__ __device__ inline uint64_t batch_items(uint32_t type, uint32_t level, u
     return 0;
 }
 
-template <int m, int L, int LR>
+template <int m, int L, int LR, class MR>
 __global__ void __launch_bounds__(kThreads, 2) k_batch(const BatchJob* __restrict__ jobs, const BatchStage* __restrict__ stages,
-                                                    uint32_t n_stages, uint32_t count, Mod<L> md, ModRR<LR> mr) {
+                                                    uint32_t n_stages, uint32_t count) {
     using G = Geo<m, L>;
     namespace cg = cooperative_groups;
     extern __shared__ __align__(16) uint32_t smem[];
@@ -92,6 +98,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(const BatchJob* __restric
             }
             const BatchJob& jb = jobs[lo];
             const uint64_t local = item - st.offs[lo];
+            Mod<L> md;
+#pragma unroll
+            for (int i = 0; i < L; ++i) md.q[i] = jb.q32[i];
+            md.nprime = jb.nprime32;
+            md.nsub = jb.nsub;
+            MR mr;
+#pragma unroll
+            for (int i = 0; i < LR; ++i) mr.q[i] = jb.q26[i];
+            mr.nprime = jb.nprime26;
             LevelParams lp = jb.lp;
             uint64_t bp = 1;
             for (uint32_t i = 0; i < st.level; ++i) bp *= G::TWO_M;
@@ -100,11 +115,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(const BatchJob* __restric
             const uint64_t cols = lp.P2 / G::TWO_M;
             switch (st.type) {
                 case kStFwdLevel:
-                    if (st.level == 0) level_fwd_ntt<m, L, LR, true>(lp, md, mr, smem, local % cols, (int)(local / cols));
-                    else level_fwd_ntt<m, L, LR, false>(lp, md, mr, smem, local % cols, (int)(local / cols));
+                    if (st.level == 0) level_fwd_ntt<m, L, LR, true, MR>(lp, md, mr, smem, local % cols, (int)(local / cols));
+                    else level_fwd_ntt<m, L, LR, false, MR>(lp, md, mr, smem, local % cols, (int)(local / cols));
                     break;
                 case kStInvLevel:
-                    level_inv_ntt<m, L, LR>(lp, md, mr, smem, local);
+                    level_inv_ntt<m, L, LR, MR>(lp, md, mr, smem, local);
                     break;
                 case kStFwdDft:
                     if (st.level == 0) dft_fwd_column<m, L, true>(lp, md, smem, local % cols, (int)(local / cols));
@@ -114,14 +129,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(const BatchJob* __restric
                 case kStInvTwiddle: {
                     const uint64_t groups = (lp.P2 + NttTeam<m>::NTEAMS - 1) / NttTeam<m>::NTEAMS;
                     if (st.type == kStFwdTwiddle)
-                        twiddle_ntt_group<m, L, LR, false>(lp, mr, local % groups, (int)(local / groups), smem);
+                        twiddle_ntt_group<m, L, LR, false, MR>(lp, mr, local % groups, (int)(local / groups), smem);
                     else
-                        twiddle_ntt_group<m, L, LR, true>(lp, mr, local, 0, smem);
+                        twiddle_ntt_group<m, L, LR, true, MR>(lp, mr, local, 0, smem);
                     break;
                 }
                 case kStFinal:
                     lp.len = jb.r_last;
-                    final_block<m, L, LR, kFormNtt>(lp, md, mr, smem, local);
+                    final_block<m, L, LR, kFormNtt, MR>(lp, md, mr, smem, local);
                     break;
                 case kStInvDft:
                     dft_inv_column<m, L>(lp, md, smem, local);

@@ -25,6 +25,9 @@ static std::atomic<uint32_t> g_fault{0};
 
 namespace dkss_planning {
 
+const uint64_t kCandidatePrimes[kNumCandidatePrimes] = {12289, 40961, 65537, 786433, 7340033, 23068673,
+                                                        104857601, 167772161, 469762049, 998244353};
+
 uint32_t fault_mask() { return g_fault.load(); }
 
 bool is_pow2(uint64_t x) { return x && !(x & (x - 1)); }
@@ -138,6 +141,32 @@ dkss_status plan_host_proth(dkss_plan_s* pl, uint64_t n_bits, uint64_t M, uint32
     const uint64_t zeta = dkss_host::proth_generator(h, n);
     if (zeta == 0) return DKSS_EPARAM;
     return plan_ring(pl, n_bits, M, m, u, p, 1, p, zeta, zeta);
+}
+
+// The Proth ring with the sparse reduction at a given LR: n = max(26 (LR-1),
+// log2 2M) and the smallest odd h with p = h 2^n + 1 prime, above the
+// coefficient bound, m p < 2^(26 LR - 2), and a plan with that LR.
+bool proth_ring_lr(uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, uint32_t LR, uint64_t* h_out,
+                   uint32_t* n_out) {
+    if (check_shape(n_bits, M, m, u) != DKSS_OK || LR < 3 || LR > 5) return false;
+    const u128 umax = ((u128)1 << u) - 1;
+    const u128 bound = (u128)M * (m / 2) * umax * umax;
+    const uint32_t n = std::max<uint32_t>(26 * (LR - 1), log2u(2 * M));
+    const int top = 26 * (int)LR - 2 - (int)log2u(m);       // m p < 2^(26 LR - 2)
+    if (top <= (int)n || top > 126) return false;
+    uint64_t h = (uint64_t)(bound >> n) + 1;
+    h |= 1;
+    for (int tries = 0; tries < 200000; ++tries, h += 2) {
+        if ((h >> 32) != 0 || (int)(n + bitlen(h)) > top) break;
+        if (!dkss_host::proth_is_prime(h, n)) continue;
+        dkss_plan_s pl;
+        if (plan_host_proth(&pl, n_bits, M, m, u, h, n) != DKSS_OK) continue;
+        if (pl.LR != LR || !pl.q_sparse) continue;
+        *h_out = h;
+        *n_out = n;
+        return true;
+    }
+    return false;
 }
 
 // Everything of a plan that needs no device, once the ring Z/qZ (q = p^z) and
@@ -471,8 +500,7 @@ struct Cand {
     uint32_t S;   // bytes of p^z (INT8 form)
 };
 
-const uint64_t kCandPrimes[] = {12289, 40961, 65537, 786433, 7340033, 23068673, 104857601, 167772161,
-                                469762049, 998244353};
+const uint64_t* kCandPrimes = dkss_planning::kCandidatePrimes;
 
 // Every (M, m, u, p, z) for N-bit operands that dkss_plan accepts and this
 // build has kernels for: m in {16, 32, 64}, u in {8, 16, 24, 32}, the smallest
@@ -487,7 +515,8 @@ std::vector<Cand> enumerate_candidates(uint64_t n_bits) {
             const uint64_t per = (uint64_t)(m / 2) * u;
             uint64_t M = 1;
             while (M * per < n_bits || M <= m) M <<= 1;
-            for (uint64_t p : kCandPrimes) {
+            for (size_t ip = 0; ip < kNumCandidatePrimes; ++ip) {
+                const uint64_t p = kCandPrimes[ip];
                 if ((p - 1) % (2 * M) != 0) continue;
                 for (uint32_t z = 1; z <= 8; ++z) {
                     dkss_plan_s pl;
@@ -829,27 +858,8 @@ dkss_status dkss_plan_proth_rho(uint64_t n_bits, uint64_t M, uint32_t m, uint32_
 dkss_status dkss_proth_ring(uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, uint64_t* h_out, uint32_t* n_out) {
     if (!h_out || !n_out) return DKSS_EINVAL;
     if (check_shape(n_bits, M, m, u) != DKSS_OK) return DKSS_EPARAM;
-    const u128 umax = ((u128)1 << u) - 1;
-    const u128 bound = (u128)M * (m / 2) * umax * umax;
-    const uint32_t lg2M = log2u(2 * M);
-    for (uint32_t LR = 3; LR <= 5; ++LR) {
-        const uint32_t n = std::max<uint32_t>(26 * (LR - 1), lg2M);
-        const int top = 26 * (int)LR - 2 - (int)log2u(m);       // m p < 2^(26 LR - 2)
-        if (top <= (int)n || top > 126) continue;
-        uint64_t h = (uint64_t)(bound >> n) + 1;
-        h |= 1;
-        for (int tries = 0; tries < 200000; ++tries, h += 2) {
-            if ((h >> 32) != 0 || (int)(n + bitlen(h)) > top) break;
-            if (!dkss_host::proth_is_prime(h, n)) continue;
-            dkss_plan_s pl;
-            if (plan_host_proth(&pl, n_bits, M, m, u, h, n) != DKSS_OK) continue;
-            Kernels k;
-            if (pl.LR != LR || !pl.q_sparse || !lookup(pl.m, pl.L, pl.LR, &k)) continue;
-            *h_out = h;
-            *n_out = n;
-            return DKSS_OK;
-        }
-    }
+    for (uint32_t LR = 3; LR <= 5; ++LR)
+        if (proth_ring_lr(n_bits, M, m, u, LR, h_out, n_out)) return DKSS_OK;
     return DKSS_EUNSUPPORTED;
 }
 

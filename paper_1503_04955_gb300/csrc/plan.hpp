@@ -67,6 +67,10 @@ uint32_t fault_mask();
 dkss_status plan_host(dkss_plan_s* pl, uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, uint64_t p, uint32_t z);
 dkss_status plan_host_proth(dkss_plan_s* pl, uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, uint64_t h,
                             uint32_t n);
+bool proth_ring_lr(uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, uint32_t LR, uint64_t* h, uint32_t* n);
+// The primes the parameter search draws from (dkss_plan_candidates).
+constexpr size_t kNumCandidatePrimes = 10;
+extern const uint64_t kCandidatePrimes[kNumCandidatePrimes];
 void build_table(const dkss_plan_s* pl, std::vector<uint32_t>& out);
 void build_eval_table(const dkss_plan_s* pl, std::vector<uint32_t>& out, bool with_minv);
 void build_ntt_consts(const dkss_plan_s* pl, std::vector<uint32_t>& out);
