@@ -460,6 +460,8 @@ void free_device(dkss_plan_s* pl) {
     cudaFree(pl->d_ntt);
     cudaFree(pl->d_evtw);
     cudaFree(pl->d_table_minv);
+    cudaFree(pl->d_half);
+    pl->d_half = nullptr;
     pl->d_ntt = nullptr;
     pl->d_evtw = nullptr;
     pl->d_table_minv = nullptr;

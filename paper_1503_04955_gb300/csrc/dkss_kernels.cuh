@@ -783,8 +783,12 @@ __device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>
         using NT = NttTeam<m>;
         NT nt;
         uint32_t* buf = tbuf + nt.id * 2 * m * LR;
-        uint32_t* park = buf + m * LR + nt.lane * LR;     // residue j at park + j * TEAM * LR
         const int lane = nt.lane;
+        // b's evaluations: residue j of the lane at park + j * TEAM * LR, or with
+        // limb planes (3 or 5 limbs, m = 64) limb w at pbase + w * m + (j * TEAM + lane) ^ flip
+        uint32_t* park = buf + m * LR + nt.lane * LR;
+        uint32_t* pbase = buf + m * LR;
+        constexpr bool PLANES = XchgPlanes<m, LR>::value;
 #pragma unroll 1
         for (int v = nt.id; v < nn; v += NT::NTEAMS) {
             uint32_t x[4][LR], w[L];
@@ -802,7 +806,14 @@ __device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>
                 for (int j = 0; j < 4; ++j) mmul<LR>(x[j], x[j], c, mr);
             }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) st_rr<LR>(park + j * NT::TEAM * LR, x[j]);
+            for (int j = 0; j < 4; ++j) {
+                if constexpr (PLANES) {
+#pragma unroll
+                    for (int w = 0; w < LR; ++w) pbase[w * m + ((j * NT::TEAM + lane) ^ xteam_flip())] = x[j][w];
+                } else {
+                    st_rr<LR>(park + j * NT::TEAM * LR, x[j]);
+                }
+            }
             // a square keeps the unscaled evaluations of a = b in registers
             if (!prm.square || prm.ntt_prescale) {
 #pragma unroll
@@ -815,7 +826,12 @@ __device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 uint32_t y[LR];
-                ld_rr<LR>(y, park + j * NT::TEAM * LR);
+                if constexpr (PLANES) {
+#pragma unroll
+                    for (int w = 0; w < LR; ++w) y[w] = pbase[w * m + ((j * NT::TEAM + lane) ^ xteam_flip())];
+                } else {
+                    ld_rr<LR>(y, park + j * NT::TEAM * LR);
+                }
                 mmul<LR>(x[j], x[j], y, mr);
             }
             if (prm.ntt_prescale)
@@ -946,6 +962,172 @@ template <int m, int L>
 __global__ void __launch_bounds__(kThreads) k_dft_inv(LevelParams prm, Mod<L> md) {
     extern __shared__ __align__(16) uint32_t smem[];
     dft_inv_column<m, L>(prm, md, smem, blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// Column DFTs in halves, for columns too large for several CTAs per SM (m = 64:
+// 2m elements of 64 residues of 3 or 4 words are 96 or 128 KiB).  The 2m-point
+// DFT with root alpha^r splits into two m-point DFTs with root alpha^(2r):
+// forward (decimation in time) over the even and the odd elements, then
+// X_v = E_v + alpha^(r v) O_v and X_(v+m) = E_v - alpha^(r v) O_v; backwards
+// (decimation in frequency) first s_k = x_k + x_(k+m) and
+// d_k = alpha^(r k) (x_k - x_(k+m)), whose m-point DFTs give the even and the
+// odd outputs.  One half sits in shared memory while the other waits in the
+// CTA's slice of a plan-owned scratch buffer (m elements; L2-resident, since
+// only the resident CTAs own slices), so a CTA needs m elements of shared
+// memory and three or four CTAs fit per SM.  Persistent grid: CTA b owns
+// scratch slice b and takes columns b, b + gridDim.x, ...
+// ---------------------------------------------------------------------------
+template <int m, int L>
+__device__ __forceinline__ void copy_words_block(uint32_t* dst, const uint32_t* src, int words) {
+    for (int i = 4 * threadIdx.x; i < words; i += 4 * kThreads)
+        *reinterpret_cast<uint4*>(dst + i) = *reinterpret_cast<const uint4*>(src + i);
+}
+
+// Elements j = 2i + parity (i < m) of the column into slot bitrev(i) (log2 m bits).
+template <int m, int L, bool FIRST>
+__device__ __forceinline__ void half_load_fwd(const LevelParams& prm, uint32_t* half, uint64_t base, uint64_t l,
+                                              uint64_t mu_d, int op, int parity) {
+    using G = Geo<m, L>;
+    constexpr int LOG2_M = ilog2<m>();
+    const uint32_t* poly = prm.data + (op ? prm.poly_words : 0);
+    const uint64_t* raw = op ? prm.raw_b : prm.raw_a;
+    const int h = m / 2;
+    for (int idx = threadIdx.x; idx < m * m; idx += kThreads) {
+        const int i = idx / m, t = idx % m;
+        const uint64_t j = 2 * (uint64_t)i + parity;
+        uint32_t* dst = half + bitrev(i, LOG2_M) * G::EW + t * L;
+        if constexpr (FIRST) {
+            const uint64_t io = j * mu_d + l;           // outer coefficient index
+            uint32_t v = 0;
+            if (io < prm.M && t < h) v = get_field(raw, prm.raw_words, prm.n_bits, (uint64_t)prm.u * (io * h + t), prm.u);
+            dst[0] = v;
+#pragma unroll
+            for (int w = 1; w < L; ++w) dst[w] = 0;
+        } else {
+            uint32_t x[L];
+            ld_res<L>(x, poly + ((base + j * mu_d + l) * m + t) * L);
+            st_res<L>(dst, x);
+        }
+    }
+}
+
+template <int m, int L, bool FIRST>
+__global__ void __launch_bounds__(kThreads) k_dft_fwd_half(LevelParams prm, Mod<L> md, uint32_t* scratch,
+                                                           uint32_t operands) {
+    using G = Geo<m, L>;
+    extern __shared__ __align__(16) uint32_t smem[];
+    uint32_t* E = scratch + (uint64_t)blockIdx.x * m * G::EW;
+    const int lg_mu = (__ffsll((long long)prm.len) - 1) - ilog2<G::TWO_M>();
+    const uint64_t mu_d = 1ull << lg_mu;
+    const uint64_t cols = prm.P2 / G::TWO_M;
+    Team<m, L> tm;
+    for (uint64_t item = blockIdx.x; item < cols * operands; item += gridDim.x) {
+        const int op = (int)(item / cols);
+        const uint64_t column = item % cols;
+        const uint64_t blk = column >> lg_mu, l = column & (mu_d - 1);
+        const uint64_t base = blk * prm.len;
+        uint32_t* poly = prm.data + (op ? prm.poly_words : 0);
+        // even elements: E_v, v < m, to the scratch slice
+        half_load_fwd<m, L, FIRST>(prm, smem, base, l, mu_d, op, 0);
+        __syncthreads();
+        dft_dit<m, L>(smem, 1, m, 2, md);
+        copy_words_block<m, L>(E, smem, m * G::EW);
+        __syncthreads();
+        // odd elements: O_v in shared memory
+        half_load_fwd<m, L, FIRST>(prm, smem, base, l, mu_d, op, 1);
+        __syncthreads();
+        dft_dit<m, L>(smem, 1, m, 2, md);
+        // X_v = E_v + alpha^v O_v, X_(v+m) = E_v - alpha^v O_v
+        for (int v = tm.id; v < m; v += G::NTEAMS) {
+#pragma unroll
+            for (int c = 0; c < G::CPL; ++c) {
+                const int t = tm.lane + c * G::TEAM;
+                uint32_t a[L], y[L], pl[L], mi[L];
+                bool ng;
+                ld_res<L>(a, E + v * G::EW + t * L);
+                shifted<m, L>(y, ng, smem + v * G::EW, t, v);
+                add_mod<L>(pl, a, y, md);
+                sub_mod<L>(mi, a, y, md);
+                // where the shifted coefficient carries a minus sign the two results trade places
+                uint32_t* d0 = poly + ((base + (uint64_t)v * mu_d + l) * m + t) * L;
+                uint32_t* d1 = poly + ((base + (uint64_t)(v + m) * mu_d + l) * m + t) * L;
+                st_res<L>(ng ? d1 : d0, pl);
+                st_res<L>(ng ? d0 : d1, mi);
+            }
+        }
+        __syncthreads();   // shared memory and the scratch slice are reused by the next column
+    }
+}
+
+template <int m, int L>
+__global__ void __launch_bounds__(kThreads) k_dft_inv_half(LevelParams prm, Mod<L> md, uint32_t* scratch) {
+    using G = Geo<m, L>;
+    constexpr int LOG2_M = ilog2<m>();
+    constexpr int ROOT = G::TWO_M - 1;                 // alpha^-1
+    constexpr int SUB_ROOT = (2 * ROOT) % G::TWO_M;    // alpha^-2 for the half DFTs
+    extern __shared__ __align__(16) uint32_t smem[];
+    uint32_t* D = scratch + (uint64_t)blockIdx.x * m * G::EW;
+    const uint64_t mu_d = prm.len / G::TWO_M;
+    const uint64_t cols = prm.P2 / G::TWO_M;
+    uint32_t* poly = prm.data;
+    for (uint64_t column = blockIdx.x; column < cols; column += gridDim.x) {
+        const uint64_t blk = column / mu_d, l = column % mu_d;
+        const uint64_t base = blk * prm.len;
+        // s_k = x_k + x_(k+m) to shared memory, d_k = alpha^(ROOT k) (x_k - x_(k+m)) to the scratch slice
+        for (int idx = threadIdx.x; idx < m * m; idx += kThreads) {
+            const int k = idx / m, t = idx % m;
+            const uint32_t* pa = poly + (base + (uint64_t)k * mu_d + l) * G::EW;
+            const uint32_t* pb = poly + (base + (uint64_t)(k + m) * mu_d + l) * G::EW;
+            uint32_t a[L], b[L], r[L];
+            ld_res<L>(a, pa + t * L);
+            ld_res<L>(b, pb + t * L);
+            add_mod<L>(r, a, b, md);
+            st_res<L>(smem + k * G::EW + t * L, r);
+            // coefficient t of alpha^sh (a - b): +-(a - b)[t - sh]; b - a where the sign is negative
+            const int sh = (ROOT * k) & (G::TWO_M - 1);
+            int src = t - sh;
+            bool neg = false;
+            if (src < 0) {
+                src += m;
+                neg = true;
+                if (src < 0) {
+                    src += m;
+                    neg = false;
+                }
+            }
+            ld_res<L>(a, (neg ? pb : pa) + src * L);
+            ld_res<L>(b, (neg ? pa : pb) + src * L);
+            sub_mod<L>(r, a, b, md);
+            st_res<L>(D + k * G::EW + t * L, r);
+        }
+        __syncthreads();
+        // even outputs X_(2v), from slot bitrev(v)
+        dft_dif<m, L>(smem, 1, m, SUB_ROOT, md);
+        for (int idx = threadIdx.x; idx < m * m; idx += kThreads) {
+            const int v = idx / m, t = idx % m;
+            uint32_t x[L];
+            ld_res<L>(x, smem + bitrev(v, LOG2_M) * G::EW + t * L);
+            st_res<L>(poly + ((base + (uint64_t)(2 * v) * mu_d + l) * m + t) * L, x);
+        }
+        __syncthreads();
+        // odd outputs X_(2v+1)
+        copy_words_block<m, L>(smem, D, m * G::EW);
+        __syncthreads();
+        dft_dif<m, L>(smem, 1, m, SUB_ROOT, md);
+        for (int idx = threadIdx.x; idx < m * m; idx += kThreads) {
+            const int v = idx / m, t = idx % m;
+            uint32_t x[L];
+            ld_res<L>(x, smem + bitrev(v, LOG2_M) * G::EW + t * L);
+            st_res<L>(poly + ((base + (uint64_t)(2 * v + 1) * mu_d + l) * m + t) * L, x);
+        }
+        __syncthreads();
+    }
+}
+
+template <int m, int L>
+constexpr size_t half_column_smem_bytes() {
+    return sizeof(uint32_t) * (size_t)m * Geo<m, L>::EW;
 }
 
 template <int m, int L>

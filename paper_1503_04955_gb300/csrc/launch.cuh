@@ -132,6 +132,14 @@ static dkss_status inject_range_fault(dkss_plan_s* pl, cudaStream_t st) {
     return DKSS_OK;
 }
 
+// Columns of more than 64 KiB (m = 64, L >= 3) run their DFTs in halves
+// (k_dft_fwd_half, k_dft_inv_half): three or four CTAs per SM instead of one
+// or two.
+template <int m, int L>
+constexpr bool half_columns() {
+    return column_smem_bytes<m, L>() > 64 * 1024;
+}
+
 // The NTT form's kernels take the sparse-modulus Montgomery product when the
 // plan's p^z allows it (Proth primes, dkss_plan_proth; ntt_rmul.cuh).
 template <int LR>
@@ -199,6 +207,28 @@ dkss_status prepare(dkss_plan_s* pl) {
         cudaFuncSetAttribute(k_twiddle_ntt<m, L, LR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, twn) ||
         cudaFuncSetAttribute(k_final_dft<m, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, fdft_max))
         return DKSS_ECUDA;
+    if constexpr (half_columns<m, L>()) {
+        // persistent grids of the half-column DFTs and one scratch slice per CTA
+        const int hb = (int)half_column_smem_bytes<m, L>();
+        int occ_f = 0, occ_i = 0;
+        if (cudaFuncSetAttribute(k_dft_fwd_half<m, L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, hb) ||
+            cudaFuncSetAttribute(k_dft_fwd_half<m, L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, hb) ||
+            cudaFuncSetAttribute(k_dft_inv_half<m, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, hb) ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, k_dft_fwd_half<m, L, true>, kThreads, hb) ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_i, k_dft_inv_half<m, L>, kThreads, hb) || occ_f < 1 ||
+            occ_i < 1)
+            return DKSS_ECUDA;
+        pl->half_grid_fwd = occ_f * pl->sm_count;
+        pl->half_grid_inv = occ_i * pl->sm_count;
+        if (!pl->d_half) {
+            const size_t words = (size_t)std::max(pl->half_grid_fwd, pl->half_grid_inv) * m * G::EW;
+            if (cudaMalloc(&pl->d_half, words * sizeof(uint32_t)) != cudaSuccess) {
+                cudaGetLastError();
+                return DKSS_ENOMEM;
+            }
+            pl->dev_bytes += words * sizeof(uint32_t);
+        }
+    }
     if constexpr (LR >= 3) {
         using MS = ModRRSparse<LR>;
         if (sparse_ntt<LR>(pl) &&
@@ -283,8 +313,15 @@ static dkss_status launch_forward_levels(dkss_plan_s* pl, LevelParams lp, int op
         }
         {
             ProfScope ps(pl, st, kProfFwdDft);
-            if (d == 0) k_dft_fwd<m, L, true><<<grid, kThreads, column_smem_bytes<m, L>(), st>>>(lp, md);
-            else k_dft_fwd<m, L, false><<<grid, kThreads, column_smem_bytes<m, L>(), st>>>(lp, md);
+            if constexpr (half_columns<m, L>()) {
+                const size_t hb = half_column_smem_bytes<m, L>();
+                const unsigned hg = (unsigned)std::min<uint64_t>(pl->half_grid_fwd, (pl->P2 / G::TWO_M) * operands);
+                if (d == 0) k_dft_fwd_half<m, L, true><<<hg, kThreads, hb, st>>>(lp, md, pl->d_half, operands);
+                else k_dft_fwd_half<m, L, false><<<hg, kThreads, hb, st>>>(lp, md, pl->d_half, operands);
+            } else {
+                if (d == 0) k_dft_fwd<m, L, true><<<grid, kThreads, column_smem_bytes<m, L>(), st>>>(lp, md);
+                else k_dft_fwd<m, L, false><<<grid, kThreads, column_smem_bytes<m, L>(), st>>>(lp, md);
+            }
             DKSS_CHECK_LAUNCH();
         }
         ProfScope ps(pl, st, kProfFwdTwiddle);
@@ -432,7 +469,12 @@ static dkss_status run_mul_coef(dkss_plan_s* pl, const uint64_t* a, const uint64
             if (s != DKSS_OK) return s;
         }
         ProfScope ps(pl, st, kProfInvDft);
-        k_dft_inv<m, L><<<(unsigned)(pl->P2 / G::TWO_M), kThreads, column_smem_bytes<m, L>(), st>>>(lp, md);
+        if constexpr (half_columns<m, L>()) {
+            const unsigned hg = (unsigned)std::min<uint64_t>(pl->half_grid_inv, pl->P2 / G::TWO_M);
+            k_dft_inv_half<m, L><<<hg, kThreads, half_column_smem_bytes<m, L>(), st>>>(lp, md, pl->d_half);
+        } else {
+            k_dft_inv<m, L><<<(unsigned)(pl->P2 / G::TWO_M), kThreads, column_smem_bytes<m, L>(), st>>>(lp, md);
+        }
         DKSS_CHECK_LAUNCH();
     }
     // the product polynomial's coefficients, before decoding

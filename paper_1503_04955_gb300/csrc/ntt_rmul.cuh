@@ -206,6 +206,26 @@ __device__ __forceinline__ int xpos(int i) {
     else return i;
 }
 
+// Residues of 3 or 5 limbs (m = 64) do not fit the 16-byte layout above: the
+// exchange buffer then holds one plane of m words per limb (limb w of index
+// i at w m + xplane(i)).  With i = (A, B, C) in 2-bit fields, xplane keeps A
+// and replaces the low four bits by (A ^ C, B ^ C): in each of the three
+// exchange patterns the 16 lanes of a team vary two of the fields, and the
+// map is one-to-one on them, so the lanes hit 16 different banks modulo 16;
+// the warp's second team flips bit 4 and takes the other 16 banks.
+template <int m, int LR>
+struct XchgPlanes {
+    static constexpr bool value = m == 64 && (LR == 3 || LR == 5);
+};
+
+__device__ __forceinline__ int xplane(int i) {
+    const int a = i >> 4, b = (i >> 2) & 3, c = i & 3;
+    return (a << 4) | ((a ^ c) << 2) | (b ^ c);
+}
+
+// Bit 4 for the second team of a warp (teams of 16 lanes, m = 64).
+__device__ __forceinline__ int xteam_flip() { return (threadIdx.x & 16); }
+
 // Index held in slot j (0..3) by lane l when the local index bits are (h, h-1).
 __device__ __forceinline__ int lidx(int l, int j, int h) {
     const int low = (1 << (h - 1)) - 1;
@@ -218,11 +238,28 @@ template <int m, int LR>
 __device__ __forceinline__ void ntt_exchange(uint32_t (&v)[4][LR], uint32_t* buf, int lane, int h_from, int h_to,
                                              unsigned mask) {
     __syncwarp(mask);   // the team's last reads of buf are done
+    if constexpr (XchgPlanes<m, LR>::value) {
+        const int f = xteam_flip();
 #pragma unroll
-    for (int j = 0; j < 4; ++j) st_rr<LR>(buf + xpos<m>(lidx(lane, j, h_from)) * LR, v[j]);
-    __syncwarp(mask);
+        for (int j = 0; j < 4; ++j) {
+            const int q = xplane(lidx(lane, j, h_from)) ^ f;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) ld_rr<LR>(v[j], buf + xpos<m>(lidx(lane, j, h_to)) * LR);
+            for (int w = 0; w < LR; ++w) buf[w * m + q] = v[j][w];
+        }
+        __syncwarp(mask);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int q = xplane(lidx(lane, j, h_to)) ^ f;
+#pragma unroll
+            for (int w = 0; w < LR; ++w) v[j][w] = buf[w * m + q];
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) st_rr<LR>(buf + xpos<m>(lidx(lane, j, h_from)) * LR, v[j]);
+        __syncwarp(mask);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ld_rr<LR>(v[j], buf + xpos<m>(lidx(lane, j, h_to)) * LR);
+    }
 }
 
 // Forward negacyclic transform (lazy).  On entry slot j of lane l holds

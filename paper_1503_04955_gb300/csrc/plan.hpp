@@ -45,6 +45,8 @@ struct dkss_plan_s {
     uint32_t* d_work = nullptr;   // two transformed polynomials
     uint64_t poly_words = 0;
     uint32_t* d_agg = nullptr;    // carry-scan tile aggregates
+    uint32_t* d_half = nullptr;   // m = 64 column DFTs in halves: one half column per resident CTA
+    int half_grid_fwd = 0, half_grid_inv = 0;   // their persistent grids
     uint64_t n_tiles = 0;
     uint32_t* d_status = nullptr;
     uint64_t* d_stage = nullptr;  // dkss_mul_host staging: a, b, out
