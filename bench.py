@@ -22,6 +22,8 @@ workloads  the other single-product workloads (65,536, 2^24 and 2^28 bits),
            each with its own form comparison.
 batched    the 4096-product batch (one persistent kernel from a CUDA graph)
            against plain per-product launches.
+thesis_points  the thesis's own operand lengths (its execution-time table)
+           over z = 1 Proth rings, against its printed CPU times.
 cpu_baseline  the CPU oracle (oracle/dkss_oracle.c) on all host cores and on
            one, on a bounded sample of the workload (oracle_sample).
 
@@ -78,6 +80,9 @@ def parse_args():
                     help="device time per form and workload in the form comparison")
     ap.add_argument("--no-others", action="store_true", help="skip the other single-product workloads")
     ap.add_argument("--other-budget-ms", type=float, default=1000.0)
+    ap.add_argument("--no-thesis-points", action="store_true",
+                    help="skip the thesis's operand lengths over Proth rings")
+    ap.add_argument("--thesis-budget-ms", type=float, default=600.0)
     ap.add_argument("--form", default="ntt", choices=["ntt", "eval", "direct", "int8tc"],
                     help="alpha-shift inner DFTs with R-multiplications through the evaluation map of R (ntt, the "
                          "default), inner levels in evaluation coordinates (eval), the direct convolution, or "
@@ -417,6 +422,7 @@ def run_ours(args):
     del a, b, out
     others = other_workloads(args, dev, flush) if (rank == 0 and not args.no_others) else None
     batched = run_batched(args, dev, flush) if (rank == 0 and not args.no_batched) else None
+    thesis = thesis_points(args, dev, flush) if (rank == 0 and not args.no_thesis_points) else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -446,6 +452,7 @@ def run_ours(args):
             "square": square,
             "workloads": others,
             "batched": batched,
+            "thesis_points": thesis,
             "clocks": clocks,
             "wall_s": round(wall, 3),
         }
@@ -608,6 +615,60 @@ def proth_ring_time(workload, dev, flush, a, b, out, ms_config, budget_ms, A, B,
             "speedup_vs_config_ring": round(ms_config / ms, 3), "bit_exact": bool(ok)}
 
 
+# The thesis's execution times of DKSS_MUL at its most favourable lengths (its
+# Section 4.4 table "Execution times of DKSS_MUL and SMUL"): operand length in
+# 64-bit words and CPU cycles on one core of a 3.4 GHz Core i7-3770.
+THESIS_TIMES = [(3648, 133948102), (7168, 288821718), (14336, 636214972), (28160, 1373645624),
+                (56320, 2908271180), (110592, 6013189608), (221184, 13430829526), (434176, 29461464342),
+                (868352, 62917787338), (1703936, 122680187946), (2752512, 199424397176),
+                (5505024, 410390455672), (10878976, 892949727060), (21757952, 1917703330120),
+                (42991616, 3965210546518), (85983232, 8145120758260)]
+THESIS_HZ = 3.4e9
+
+
+def thesis_points(args, dev, flush):
+    """The thesis's operand lengths with its kind of ring: z = 1 and a Proth
+    prime p = h 2^n + 1 (dkss_proth_ring) under the parameters its rule picks
+    (largest u, smallest M m, M/m near N / log^3 N: dkss_plan_choose with the
+    rule flag).  The thesis itself used u of 54 to 83 bits and 128- or 192-bit
+    primes, which this build's limbs (u <= 32, p^z < 2^126) do not hold, so
+    u is 32 here.  Device ms per product against the thesis's CPU time."""
+    import torch
+
+    import paper_1503_04955_gb300 as dk
+
+    stream = torch.cuda.current_stream(dev)
+    out_rows = []
+    for words, cycles in THESIS_TIMES:
+        n_bits = 64 * words
+        M, m, u, _, _ = dk.plan_choose(n_bits, dk.TUNE_RULE)
+        try:
+            h, n = dk.proth_ring(n_bits, M, m, u)
+            plan = dk.Plan.proth(n_bits, M, m, u, h, n)
+        except dk.DkssError as e:
+            out_rows.append({"words": words, "unsupported": str(e)})
+            continue
+        A, B = syn.operand_pair(n_bits, syn.config_seed(100), product=words)
+        a = torch.from_numpy(A.view(np.int64)).to(dev)
+        b = torch.from_numpy(B.view(np.int64)).to(dev)
+        out = torch.empty(2 * A.size, dtype=torch.int64, device=dev)
+        for _ in range(2):
+            plan.mul(a, b, out)
+        torch.cuda.synchronize(dev)
+        t = time_steps(lambda: plan.mul(a, b, out), 1, flush, stream)
+        steps = steps_for(t[0], args.thesis_budget_ms, lo=1, hi=20)
+        ms = sum(time_steps(lambda: plan.mul(a, b, out), steps, flush, stream)) / steps
+        ok = check_product(out.cpu().numpy().view(np.uint64), A, B)
+        plan.close()
+        thesis_s = cycles / THESIS_HZ
+        out_rows.append({"words": words, "n_bits": n_bits, "M": M, "m": m, "u": u, "p": "%d*2^%d+1" % (h, n),
+                         "ms_per_step": round(ms, 4), "gbit_s": round(2 * n_bits / (ms * 1e-3) / 1e9, 3),
+                         "thesis_s": round(thesis_s, 4), "speedup_vs_thesis": round(thesis_s / (ms * 1e-3), 1),
+                         "bit_exact": bool(ok)})
+        del a, b, out
+    return out_rows
+
+
 def run_batched(args, dev, flush):
     """4096 products, operand lengths 2^x with x uniform in [14, 20] rounded to
     64-bit limbs: one persistent-kernel launch under a CUDA graph per step,
@@ -652,28 +713,25 @@ def run_batched(args, dev, flush):
     torch.cuda.synchronize(dev)
     ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / steps
     ok = all(check_product(o.cpu().numpy().view(np.uint64), A, B)
-             for o, (A, B) in zip(o_l[::64], ops[::64]))
+             for o, (A, B) in zip(o_l[::16], ops[::16]))
     classes = {}
     for j in range(len(lengths)):
         prm = bt.job_params(j)
         key = prm["class_bits"]
         if key not in classes:
-            classes[key] = {"M": prm["M"], "u": prm["u"], "levels": prm["levels"], "jobs": 0}
+            classes[key] = {"M": prm["M"], "u": prm["u"], "levels": prm["levels"], "jobs": 0,
+                            "p_bits": prm["p"].bit_length(), "z": prm["z"], "proth": bool(prm["proth"])}
         classes[key]["jobs"] += 1
     graph = bool(bt.job_params(0)["graph"])
     grid = bt.job_params(0)["grid"]
-    # plain per-product launches with each class's parameters
-    plans = {}
-    for key, c in classes.items():
-        plans[key] = dk.Plan(key, c["M"], 32, c["u"], 65537, 5)
-    job_plan = [plans[bt.job_params(j)["class_bits"]] for j in range(len(lengths))]
-    bt.close()
-    # a plan is fixed to one N: one plan per distinct length for the plain loop
+    proth = bool(bt.job_params(0)["proth"])
+    # plain per-product launches with each class's parameters (one plan per
+    # distinct length: a plan is fixed to one N)
     plain_plans = {}
     for j, n in enumerate(lengths):
         if n not in plain_plans:
-            jp = job_plan[j]
-            plain_plans[n] = dk.Plan(n, jp.M, jp.m, jp.u, jp.p, jp.z)
+            plain_plans[n] = bt.class_plan(j)
+    bt.close()
     for _ in range(2):
         for j, n in enumerate(lengths):
             plain_plans[n].mul(a_l[j], b_l[j], o_l[j])
@@ -686,7 +744,7 @@ def run_batched(args, dev, flush):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     plain_ms = e0.elapsed_time(e1)
-    for p in list(plans.values()) + list(plain_plans.values()):
+    for p in plain_plans.values():
         p.close()
     bits = 2 * sum(lengths)
     return {"workload": "dkss_batch_4096_log_uniform_2p14_2p20", "products": len(lengths),
@@ -696,6 +754,7 @@ def run_batched(args, dev, flush):
             "plain_launches_ms": round(plain_ms, 4),
             "speedup_vs_plain_launches": round(plain_ms / ms, 3),
             "graph": graph, "persistent_grid": grid, "plan_s": round(plan_s, 3), "bit_exact_sampled": bool(ok),
+            "rings": "Proth primes (z = 1, sparse reduction)" if proth else "configured primes (smallest p^z per class)",
             "classes": {str(k): v for k, v in sorted(classes.items())}}
 
 
