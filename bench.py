@@ -62,6 +62,12 @@ FORM_FLAGS = {"ntt": 0, "eval": 128, "direct": 16, "int8tc": 2}   # binding.LEVE
 I8_TOPS = 150.0                   # mma.sync.m16n8k32 u8 throughput measured on a GB300 (2 ops per MAC)
 NCU_TRAFFIC_BYTES = {("dkss_2p24b", "ntt", "fwd_twiddle"): 46.6e6,
                      ("dkss_2p24b", "eval", "fwd_twiddle"): 44.3e6}
+# DRAM bytes (read + write) per element a bad-multiplication launch transforms,
+# from one ncu capture of the same kernel on the 2^26-bit product with the same
+# ring (profiles/stage_kernels_dkss_2p32b.md: 478 MB for 259,842 elements and
+# 408 MB for 227,584); a full launch's traffic is this times its elements.
+NCU_BYTES_PER_ELEMENT = {("dkss_2p32b", "ntt", "config", "fwd_twiddle"): 1817.0,
+                         ("dkss_2p26b_ring2p32", "ntt", "config", "fwd_twiddle"): 1817.0}
 
 
 def parse_args():
@@ -71,6 +77,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(syn.WORKLOADS))
+    ap.add_argument("--ring", default="config", choices=["config", "proth"],
+                    help="the workload's ring p^z (config) or z = 1 with its Proth prime (dkss_proth_ring)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--no-batched", action="store_true", help="skip the 4096-product batched workload")
@@ -239,6 +247,17 @@ def stage_work_i8(info, m):
             "inv_twiddle": (sum(nontrivial) * r, col_levels)}
 
 
+def transformed_elements(info, m):
+    """Elements each radix-2m level's bad multiplications transform (twiddle
+    not 1), per operand."""
+    out, length = [], info["P2"]
+    for _ in range(info["levels"] - 1):
+        mu_d = length // (2 * m)
+        out.append((info["P2"] // length) * (mu_d - 1) * (2 * m - 1))
+        length //= 2 * m
+    return out
+
+
 def stage_work(info, m, form):
     """Per kernel group: (algorithmic 32-bit multiply-adds per step, launches
     per step).  Twiddles rho^0 = 1 are not work; every other twiddle and every
@@ -348,8 +367,13 @@ def run_ours(args):
     n_bits = cfg[0]
     A, B = syn.operand_pair(n_bits, syn.config_seed(syn.WORKLOADS[args.workload]["index"]), product=rank)
     flags = binding.FORM_PROFILE | FORM_FLAGS[args.form]
-    plan = dk.Plan(*cfg, flags=flags)
+    if args.ring == "proth":      # the same N, M, m, u over the Proth ring of dkss_proth_ring
+        h, n = dk.proth_ring(*cfg[:4])
+        plan = dk.Plan.proth(*cfg[:4], h, n, flags=flags)
+    else:
+        plan = dk.Plan(*cfg, flags=flags)
     info = plan.info()
+    plan_p = info["p"]
     a = torch.from_numpy(A.view(np.int64)).to(dev)
     b = torch.from_numpy(B.view(np.int64)).to(dev)
     out = torch.empty(2 * A.size, dtype=torch.int64, device=dev)
@@ -436,12 +460,15 @@ def run_ours(args):
             "dtype": "u8" if args.form == "int8tc" else "u32",
             "data": "synthetic: SplitMix64 uniform operands in [0, 2^N)",
             "config": dict(workload_config(args.workload), form="int8tc" if args.form == "int8tc" else "imad",
+                           ring="workload's p^z" if args.ring == "config" else "Proth prime %s (z = 1)" % plan_p,
                            rmul=args.form,
                            l2="inputs larger than L2 at 2^28 bits and up; also flushed between steps "
                               "(256 MiB write outside the timed events)",
                            parallelism="replicas" if world > 1 else "single GPU"),
             "products_per_s": round(world / (ms_per_step * 1e-3), 3),
             "bit_exact": bool(ok),
+            "device_bytes": {"plan": info["dev_bytes"],
+                             "bits_per_operand_bit": round(8 * info["dev_bytes"] / n_bits, 2)},
             "gpu_launches": launches,
             "e2e": {"value": round(e2e_value, 4), "unit": "Gbit/s", "h2d_bytes_per_step": 2 * A.nbytes,
                     "d2h_bytes_per_step": 4 * A.nbytes, "steps": e2e_steps},
@@ -499,9 +526,14 @@ def main_roofline(args, info, cfg, A, prof):
             ach = mem_bytes[k] / (ms * 1e-3) / 1e9
             stages[k] = {"bound": "hbm", "ms": round(ms, 4), "achieved": round(ach, 1), "unit": "GB/s",
                          "frac": round(ach / HBM_GBS, 4)}
+    traffic = NCU_TRAFFIC_BYTES.get((args.workload, args.form, dom)) if args.ring == "config" else None
+    per_elem = NCU_BYTES_PER_ELEMENT.get((args.workload, args.form, args.ring, dom))
+    if per_elem is not None:
+        elements = sum(transformed_elements(info, cfg[2])) * (2 if dom == "fwd_twiddle" else 1)
+        traffic = round(per_elem * elements / max(1, launches_per_step))
     return {"bound": bound, "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 3),
             "unit": unit, "frac": round(achieved / peak, 4),
-            "traffic": NCU_TRAFFIC_BYTES.get((args.workload, args.form, dom)),
+            "traffic": traffic,
             "stages": stages,
             "avg_launch_ms": round(avg_launch_ms, 4), "ops_per_launch": int(ops_per_launch),
             "peak_basis": peak_basis}
@@ -611,6 +643,7 @@ def proth_ring_time(workload, dev, flush, a, b, out, ms_config, budget_ms, A, B,
     plan.close()
     return {"h": h, "n": n, "p_bits": ((h << n) + 1).bit_length(), "L": info["L"], "LR": info["LR"],
             "sparse_reduction": bool(info["sparse"]), "ms_per_step": round(ms, 5), "steps": steps,
+            "device_bytes": info["dev_bytes"], "bits_per_operand_bit": round(8 * info["dev_bytes"] / n_bits, 2),
             "gbit_s": round(2 * n_bits / (ms * 1e-3) / 1e9, 4),
             "speedup_vs_config_ring": round(ms_config / ms, 3), "bit_exact": bool(ok)}
 

@@ -113,6 +113,9 @@ WORKLOADS = {
     "dkss_2p24b": dict(index=1, n_bits=1 << 24, M=1 << 15, m=32, u=32, p=65537, z=6),
     "dkss_2p28b": dict(index=3, n_bits=1 << 28, M=1 << 18, m=64, u=32, p=7340033, z=4),
     "dkss_2p32b": dict(index=4, n_bits=1 << 32, M=1 << 22, m=64, u=32, p=998244353, z=4),
+    # the 2^32-bit workload's ring and encoding at 2^26 bits (ncu captures: a
+    # few hundred MB on the device, still larger than L2)
+    "dkss_2p26b_ring2p32": dict(index=5, n_bits=1 << 26, M=1 << 16, m=64, u=32, p=998244353, z=4),
 }
 BATCH_WORKLOAD = dict(index=2, count=4096, lo_exp=14, hi_exp=20)
 

@@ -103,3 +103,11 @@ def test_oracle_sample_is_a_valid_plan():
         assert cfg[2:] == list(full[2:])
         assert cfg[0] == min(full[0], bench.SAMPLE_MAX_BITS) and A.size == (cfg[0] + 63) // 64
         o.Params(*cfg).check()
+
+
+@pytest.mark.parametrize("P2,m,levels", [(1024, 16, 3), (4096, 16, 3), (8192, 32, 3), (1 << 15, 64, 3)])
+def test_transformed_elements_by_enumeration(P2, m, levels):
+    """Elements per level whose bad twiddle is not 1 (the unit the captured
+    per-element traffic is scaled by), against enumeration."""
+    got = bench.transformed_elements({"P2": P2, "levels": levels}, m)
+    assert got == enumerate_nontrivial(P2, m, levels)
