@@ -401,6 +401,7 @@ dkss_status dkss_batch_plan(dkss_batch_t* out, const uint64_t* n_bits, size_t co
         jb.nsub = h.nsub;
         for (int i = 0; i < 5; ++i) jb.q26[i] = h.q_rr[i];
         jb.nprime26 = h.nprime26;
+        jb.qtop_inv26 = dkss::qtop_reciprocal(h.q_rr[kBLR - 1], h.q_rr[kBLR - 2]);
         max_levels = std::max(max_levels, h.col_levels);
     }
 

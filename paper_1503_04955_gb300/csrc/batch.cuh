@@ -46,6 +46,7 @@ struct BatchJob {
     uint32_t nprime32, nsub;
     uint32_t q26[5];
     uint32_t nprime26;
+    uint64_t qtop_inv26;
 };
 
 struct BatchStage {
@@ -107,6 +108,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(const BatchJob* __restric
 #pragma unroll
             for (int i = 0; i < LR; ++i) mr.q[i] = jb.q26[i];
             mr.nprime = jb.nprime26;
+            mr.qtop_inv = jb.qtop_inv26;
             LevelParams lp = jb.lp;
             uint64_t bp = 1;
             for (uint32_t i = 0; i < st.level; ++i) bp *= G::TWO_M;

@@ -23,6 +23,7 @@ static MR make_modrr(const dkss_plan_s* pl) {
     MR md;
     for (int i = 0; i < LR; ++i) md.q[i] = pl->q_rr[i];
     md.nprime = pl->nprime26;
+    md.qtop_inv = qtop_reciprocal(pl->q_rr[LR - 1], pl->q_rr[LR - 2]);
     return md;
 }
 

@@ -166,21 +166,32 @@ DKSS_HD void lz_norm(uint32_t (&x)[LR]) {
 }
 
 // Canonical residue of a lazy value x (limbs below 2^32, value below 2^20 q):
-// quotient estimate k from the top two limbs in single precision, one
-// multi-limb subtraction of (k - 1) q, then two conditional subtractions.  The
-// estimate is within one of floor(x / q) because q's top two limbs (26 (LR-2)
-// bits down) hold at least 2^18 (the plan's limb choice), so x - (k - 1) q is
-// in [0, 3q).
+// quotient estimate k from the top two limbs, one multi-limb subtraction of
+// (k - 1) q, then two conditional subtractions.  With V the top two limbs of x
+// (after carrying to 26-bit limbs) and Q those of q, k = floor(V / Q) -- a
+// multiply-high by the plan's reciprocal floor((2^64 - 1) / Q), which is k or
+// k - 1, and one correction -- is within one of floor(x / q) because Q is at
+// least 2^18 and the quotient below 2^12 (the plan's limb choice and host
+// check), so x - (k - 1) q is in [0, 3q).  Integer arithmetic only.
+DKSS_HD uint64_t mulhi64(uint64_t a, uint64_t b) {
+#ifdef __CUDA_ARCH__
+    return __umul64hi(a, b);
+#else
+    return (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+
 template <int LR>
-__device__ __forceinline__ void reduce_raw(uint32_t (&r)[LR], const uint32_t (&x)[LR], const ModRR<LR>& md) {
+DKSS_HD void reduce_raw(uint32_t (&r)[LR], const uint32_t (&x)[LR], const ModRR<LR>& md) {
     uint32_t y[LR];
 #pragma unroll
     for (int i = 0; i < LR; ++i) y[i] = x[i];
     lz_norm<LR>(y);
-    const float vf = __uint2float_rz(y[LR - 1]) * 67108864.0f + __uint2float_rz(y[LR - 2]);
-    const float qf = __uint2float_rz(md.q[LR - 1]) * 67108864.0f + __uint2float_rz(md.q[LR - 2]);
-    const uint32_t ke = __float2uint_rz(__fdiv_rz(vf, qf));
-    const uint32_t k = ke > 0 ? ke - 1 : 0;
+    const uint64_t V = ((uint64_t)y[LR - 1] << 26) + y[LR - 2];          // below 2^58
+    const uint64_t Q = ((uint64_t)md.q[LR - 1] << 26) + md.q[LR - 2];
+    uint64_t ke = mulhi64(V, md.qtop_inv);                               // floor(V / Q) or one less
+    if (V - ke * Q >= Q) ++ke;
+    const uint32_t k = ke > 0 ? (uint32_t)ke - 1 : 0;
     int64_t carry = 0;
 #pragma unroll
     for (int i = 0; i < LR; ++i) {

@@ -19,12 +19,19 @@ constexpr uint32_t kM26 = (1u << 26) - 1;
 // the limb arithmetic below is plain integer code: also callable on the host,
 // where the CPU tests check it against exact integers
 #define DKSS_HD __host__ __device__ __forceinline__
+#define DKSS_HD_DECL __host__ __device__ inline
 
 template <int LR>
 struct ModRR {
-    uint32_t q[LR];    // p^z in 26-bit limbs
-    uint32_t nprime;   // -(p^z)^-1 mod 2^26
+    uint32_t q[LR];     // p^z in 26-bit limbs
+    uint32_t nprime;    // -(p^z)^-1 mod 2^26
+    uint64_t qtop_inv;  // floor((2^64 - 1) / Q), Q = q[LR-1] 2^26 + q[LR-2]: quotient estimates
 };
+
+// The reciprocal of ModRR::qtop_inv (host and device).
+DKSS_HD_DECL uint64_t qtop_reciprocal(uint32_t q_hi, uint32_t q_lo) {
+    return ~0ull / (((uint64_t)q_hi << 26) + q_lo);
+}
 
 // 32-bit limbs -> 26-bit limbs (x < 2^(26 LR))
 template <int L, int LR>

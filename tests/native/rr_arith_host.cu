@@ -5,7 +5,8 @@
 //
 // One request per input line, decimal 32-bit words:
 //   <op> <LR> <nprime> q[0..LR) x[0..LR) y[0..LR)
-// op: mont (mont_mul_rr), mmul (lazy Montgomery product), canon, norm
+// op: mont (mont_mul_rr), mmul (lazy Montgomery product), rraw (reduce_raw
+// of a lazy value), canon, norm
 // (lz_norm of x), neg (neg_rr of x), rt<L> (to_rr then from_rr of the L
 // words x[0..L), LR = limbs).  And the Lucas-Lehmer reduction of
 // csrc/mersenne.cuh:
@@ -27,6 +28,7 @@ void run(const char* op, uint32_t nprime, const uint32_t* q, const uint32_t* x, 
     dkss::ModRR<LR> md;
     for (int i = 0; i < LR; ++i) md.q[i] = q[i];
     md.nprime = nprime;
+    md.qtop_inv = dkss::qtop_reciprocal(q[LR - 1], q[LR - 2]);
     uint32_t a[LR], b[LR], r[LR];
     for (int i = 0; i < LR; ++i) {
         a[i] = x[i];
@@ -37,6 +39,8 @@ void run(const char* op, uint32_t nprime, const uint32_t* q, const uint32_t* x, 
         dkss::mont_mul_rr<LR>(r, a, b, md);
     } else if (!std::strcmp(op, "mmul")) {
         dkss::mmul<LR>(r, a, b, md);
+    } else if (!std::strcmp(op, "rraw")) {
+        dkss::reduce_raw<LR>(r, a, md);
     } else if (!std::strcmp(op, "canon")) {
         dkss::canon<LR>(r, a, md);
     } else if (!std::strcmp(op, "norm")) {

@@ -125,6 +125,34 @@ def test_canon_norm_neg(driver, rings):
         assert all(x <= M26 for x in g[:-1])
 
 
+def test_reduce_raw_of_lazy_values(driver, rings):
+    """reduce_raw: a lazy value (limbs up to 32 bits, quotient by q below
+    2^12, the plan's limits) to its canonical residue, with the integer
+    quotient estimate from q's two top limbs; rings whose top two limbs hold
+    at least 2^18 (the plan's condition for using it)."""
+    rng = random.Random(5)
+    reqs, want = [], []
+    for q, lr in rings:
+        ql = limbs(q, lr)
+        if (ql[-1] << 26) + ql[-2] < (1 << 18):
+            continue
+        for v in [0, q - 1, q, 2 * q - 1, 3 * q, (1 << 12) * q - 1] + \
+                 [rng.randrange((1 << 12) * q) for _ in range(60)]:
+            x = limbs(v, lr)
+            for i in range(lr - 1):            # move value into lower limbs (lazy form)
+                if x[i + 1] and rng.random() < 0.5:
+                    d = rng.randrange(1, min(x[i + 1], 32) + 1)
+                    x[i + 1] -= d
+                    x[i] += d << 26
+            assert value(x) == v and all(w < (1 << 32) for w in x)
+            reqs.append(("rraw", lr, nprime(q), ql, x, [0] * lr))
+            want.append(v % q)
+    assert reqs
+    got = call(driver, reqs)
+    for g, w in zip(got, want):
+        assert value(g) == w and all(x <= M26 for x in g[:-1])
+
+
 @pytest.mark.parametrize("L,LR", [(2, 2), (2, 3), (3, 4), (4, 4), (4, 5)])
 def test_word_limb_round_trip(driver, L, LR):
     """to_rr then from_rr of L 32-bit words (value below 2^(26 LR)); the
