@@ -572,6 +572,13 @@ def other_workloads(args, dev, flush):
             entry["forms"] = compare_forms(name, "ntt", dev, flush, a, b, out, ms, args.form_budget_ms, A, B, rab)
         if cfg[0] >= 1 << 24:
             entry["proth_ring"] = proth_ring_time(name, dev, flush, a, b, out, ms, args.form_budget_ms, A, B, rab)
+        if not args.no_cpu_baseline:
+            # the oracle (all host cores) on the whole workload: a few seconds up to 2^28 bits
+            dt, c, cores = oracle_product_seconds(list(cfg), A, B, os.cpu_count() or 1)
+            entry["cpu_oracle"] = {"seconds": round(dt, 3), "cores": cores,
+                                   "gbit_s": round(2 * cfg[0] / dt / 1e9, 6),
+                                   "bit_exact": bool(check_product(c, A, B, *rab)),
+                                   "gpu_speedup": round(dt / (ms * 1e-3), 1)}
         res[name] = entry
         del a, b, out
     return res
