@@ -11,7 +11,8 @@ tensor-core form.
 about half an hour and 32 GiB, so tests/golden/make_large_digests.py ran it
 once and stored SHA-256 digests of its product words and of its a_hat (the
 whole array and 16 equal slices); the GPU's full outputs are hashed the same
-way and must match every digest, in the default and the INT8 form.
+way and must match every digest, in the default, the direct and the INT8
+form.
 """
 import hashlib
 import os
@@ -105,7 +106,7 @@ def check_digests(got, want, what):
     assert got[0] == whole
 
 
-@pytest.mark.parametrize("flags", [FORM_DEFAULT, FORM_INT8])
+@pytest.mark.parametrize("flags", [FORM_DEFAULT, FORM_DIRECT, FORM_INT8])
 def test_2p32_bits_exact(dk, flags):
     name = "dkss_2p32b"
     want = golden.read_golden(name)
