@@ -458,7 +458,7 @@ dkss_status dkss_batch_plan(dkss_batch_t* out, const uint64_t* n_bits, size_t co
     size_t fin = 0;
     for (const auto& t : b->tables)
         fin = std::max(fin, dkss::final_smem_bytes<kBm, kBL, kBLR>((int)t->host.r_last, dkss::kFormNtt));
-    b->smem = std::max({sizeof(uint32_t) * (size_t)G::TWO_M * G::EW, fin, xbuf,
+    b->smem = std::max({sizeof(uint32_t) * (size_t)G::TWO_M * G::ES, fin, xbuf,
                         dkss::level_ntt_smem_bytes<kBm, kBL, kBLR>(), sizeof(uint32_t) * (size_t)dkss::kDecSmemWords});
     int per_sm = 0, sms = 0, optin = 0;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device) != cudaSuccess ||

@@ -33,6 +33,12 @@ template <int m, int L>
 struct Geo {
     static constexpr int TWO_M = 2 * m;
     static constexpr int EW = m * L;                     // words per element of R
+    // Shared-memory stride of an element: EW, padded for 3-word residues at
+    // m <= 32 so that the teams of a warp (2 of 16 lanes for m = 32, 4 of 8
+    // for m = 16), which work on different elements with scalar accesses,
+    // start in different banks (96 + 16 and 48 + 8 words).  The layout in HBM
+    // keeps EW.
+    static constexpr int ES = EW + ((L == 3 && m == 32) ? 16 : (L == 3 && m == 16) ? 8 : 0);
     static constexpr int TEAM = m / 2;                   // lanes per element in the DFTs and the direct
                                                          // form (2 coefficients each)
     static constexpr int TEAMS_PER_WARP = 32 / TEAM;
@@ -182,14 +188,14 @@ __device__ void dft_dit(uint32_t* base, int arrays, int n, int root, const Mod<L
         const int half = 1 << lh;
         const int scale = n >> (lh + 1);
         for (int bfa = tm.id; bfa < arrays * (n / 2); bfa += G::NTEAMS) {
-            uint32_t* s = base + (bfa >> (log2n - 1)) * n * G::EW;
+            uint32_t* s = base + (bfa >> (log2n - 1)) * n * G::ES;
             int bf = bfa & (n / 2 - 1);
             int k_in = bf & (half - 1);
             int ia = ((bf >> lh) << (lh + 1)) + k_in;
             int ib = ia + half;
             int sh = (root * scale * k_in) & (G::TWO_M - 1);
-            uint32_t* pa = s + ia * G::EW;
-            uint32_t* pb = s + ib * G::EW;
+            uint32_t* pa = s + ia * G::ES;
+            uint32_t* pb = s + ib * G::ES;
             uint32_t a[G::CPL][L], y[G::CPL][L];
             bool ng[G::CPL];
 #pragma unroll
@@ -230,7 +236,7 @@ __device__ void dft_dif(uint32_t* base, int arrays, int n, int root, const Mod<L
         const int half = 1 << lh;
         const int scale = n >> (lh + 1);
         for (int bfa = tm.id; bfa < arrays * (n / 2); bfa += G::NTEAMS) {
-            uint32_t* s = base + (bfa >> (log2n - 1)) * n * G::EW;
+            uint32_t* s = base + (bfa >> (log2n - 1)) * n * G::ES;
             const int bf = bfa & (n / 2 - 1);
             int k_in = bf & (half - 1);
             int ia = ((bf >> lh) << (lh + 1)) + k_in;
@@ -241,8 +247,8 @@ __device__ void dft_dif(uint32_t* base, int arrays, int n, int root, const Mod<L
             for (int c = 0; c < G::CPL; ++c) {
                 int t = tm.lane + c * G::TEAM;
                 uint32_t a[L], b[L];
-                ld_res<L>(a, s + ia * G::EW + t * L);
-                ld_res<L>(b, s + ib * G::EW + t * L);
+                ld_res<L>(a, s + ia * G::ES + t * L);
+                ld_res<L>(b, s + ib * G::ES + t * L);
                 add_mod<L>(sa[c], a, b, md);
                 // coefficient t of alpha^sh * (a - b)
                 int src = t - sh;
@@ -256,8 +262,8 @@ __device__ void dft_dif(uint32_t* base, int arrays, int n, int root, const Mod<L
                     }
                 }
                 // b - a instead of a - b where the coefficient carries a minus sign
-                const uint32_t* pa = s + (neg ? ib : ia) * G::EW + src * L;
-                const uint32_t* pb = s + (neg ? ia : ib) * G::EW + src * L;
+                const uint32_t* pa = s + (neg ? ib : ia) * G::ES + src * L;
+                const uint32_t* pb = s + (neg ? ia : ib) * G::ES + src * L;
                 ld_res<L>(a, pa);
                 ld_res<L>(b, pb);
                 sub_mod<L>(db[c], a, b, md);
@@ -266,8 +272,8 @@ __device__ void dft_dif(uint32_t* base, int arrays, int n, int root, const Mod<L
 #pragma unroll
             for (int c = 0; c < G::CPL; ++c) {
                 int t = tm.lane + c * G::TEAM;
-                st_res<L>(s + ia * G::EW + t * L, sa[c]);
-                st_res<L>(s + ib * G::EW + t * L, db[c]);
+                st_res<L>(s + ia * G::ES + t * L, sa[c]);
+                st_res<L>(s + ib * G::ES + t * L, db[c]);
             }
             __syncwarp(tm.mask);
         }
@@ -412,7 +418,7 @@ __device__ __forceinline__ void column_load_fwd(const LevelParams& prm, uint32_t
             uint64_t i = (uint64_t)j * mu_d + l;        // outer coefficient index
             uint32_t v = 0;
             if (i < prm.M && t < h) v = get_field(raw, prm.raw_words, prm.n_bits, (uint64_t)prm.u * (i * h + t), prm.u);
-            uint32_t* dst = col + bitrev(j, LOG2_TWO_M) * G::EW + t * L;
+            uint32_t* dst = col + bitrev(j, LOG2_TWO_M) * G::ES + t * L;
             dst[0] = v;
 #pragma unroll
             for (int w = 1; w < L; ++w) dst[w] = 0;
@@ -422,7 +428,7 @@ __device__ __forceinline__ void column_load_fwd(const LevelParams& prm, uint32_t
             int j = idx / m, t = idx % m;
             uint32_t x[L];
             ld_res<L>(x, poly + ((base + (uint64_t)j * mu_d + l) * m + t) * L);
-            st_res<L>(col + bitrev(j, LOG2_TWO_M) * G::EW + t * L, x);
+            st_res<L>(col + bitrev(j, LOG2_TWO_M) * G::ES + t * L, x);
         }
     }
 }
@@ -442,7 +448,7 @@ __device__ __forceinline__ void dft_fwd_column(const LevelParams& prm, const Mod
     for (int idx = threadIdx.x; idx < G::TWO_M * m; idx += kThreads) {
         int v = idx / m, t = idx % m;
         uint32_t x[L];
-        ld_res<L>(x, col + v * G::EW + t * L);
+        ld_res<L>(x, col + v * G::ES + t * L);
         st_res<L>(poly + ((base + (uint64_t)v * mu_d + l) * m + t) * L, x);
     }
 }
@@ -623,7 +629,7 @@ __device__ __forceinline__ void level_fwd_ntt(const LevelParams& prm, const Mod<
     using G = Geo<m, L>;
     using NT = NttTeam<m>;
     uint32_t* col = smem;
-    uint32_t* xbuf = smem + G::TWO_M * G::EW;
+    uint32_t* xbuf = smem + G::TWO_M * G::ES;
     uint32_t* poly = prm.data + (op ? prm.poly_words : 0);
     const int lg_mu = (__ffsll((long long)prm.len) - 1) - ilog2<G::TWO_M>();
     const uint64_t mu_d = 1ull << lg_mu;
@@ -637,7 +643,7 @@ __device__ __forceinline__ void level_fwd_ntt(const LevelParams& prm, const Mod<
     uint32_t bn[LR];
     ldg_rr<LR>(bn, prm.ntt_cst + NttLayout<m>::BN * LR);
     for (int v = nt.id; v < G::TWO_M; v += NT::NTEAMS) {
-        const uint32_t* src = col + v * G::EW;
+        const uint32_t* src = col + v * G::ES;
         uint32_t* dst = poly + (base + (uint64_t)v * mu_d + l) * G::EW;
         if (v == 0 || l == 0) {                  // twiddle 1
 #pragma unroll
@@ -666,7 +672,7 @@ __device__ __forceinline__ void level_inv_ntt(const LevelParams& prm, const Mod<
     using NT = NttTeam<m>;
     constexpr int LOG2_TWO_M = ilog2<G::TWO_M>();
     uint32_t* col = smem;
-    uint32_t* xbuf = smem + G::TWO_M * G::EW;
+    uint32_t* xbuf = smem + G::TWO_M * G::ES;
     uint32_t* poly = prm.data;
     const int lg_mu = (__ffsll((long long)prm.len) - 1) - LOG2_TWO_M;
     const uint64_t mu_d = 1ull << lg_mu;
@@ -679,7 +685,7 @@ __device__ __forceinline__ void level_inv_ntt(const LevelParams& prm, const Mod<
     // element v of the column times rho^(-v l bp), into slot v
     for (int v = nt.id; v < G::TWO_M; v += NT::NTEAMS) {
         const uint32_t* src = poly + (base + (uint64_t)v * mu_d + l) * G::EW;
-        uint32_t* dst = col + v * G::EW;
+        uint32_t* dst = col + v * G::ES;
         if (v == 0 || l == 0) {
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -697,7 +703,7 @@ __device__ __forceinline__ void level_inv_ntt(const LevelParams& prm, const Mod<
     for (int idx = threadIdx.x; idx < G::TWO_M * m; idx += kThreads) {
         int j = idx / m, t = idx % m;
         uint32_t x[L];
-        ld_res<L>(x, col + bitrev(j, LOG2_TWO_M) * G::EW + t * L);
+        ld_res<L>(x, col + bitrev(j, LOG2_TWO_M) * G::ES + t * L);
         st_res<L>(poly + ((base + (uint64_t)j * mu_d + l) * m + t) * L, x);
     }
 }
@@ -711,7 +717,7 @@ __global__ void __launch_bounds__(kThreads, m >= 64 ? 1 : 4)
 
 template <int m, int L, int LR>
 constexpr size_t level_ntt_smem_bytes() {
-    return sizeof(uint32_t) * ((size_t)Geo<m, L>::TWO_M * Geo<m, L>::EW + (size_t)NttTeam<m>::NTEAMS * m * LR);
+    return sizeof(uint32_t) * ((size_t)Geo<m, L>::TWO_M * Geo<m, L>::ES + (size_t)NttTeam<m>::NTEAMS * m * LR);
 }
 
 // ---------------------------------------------------------------------------
@@ -731,8 +737,8 @@ __device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>
     const int nb = FORM == kFormNtt ? final_blocks_per_cta<m>(n) : 1;
     const int nn = nb * n;
     uint32_t* sa = smem;
-    uint32_t* sb = smem + nn * G::EW;
-    uint32_t* tbuf = sb + nn * G::EW;
+    uint32_t* sb = smem + nn * G::ES;
+    uint32_t* tbuf = sb + nn * G::ES;
     const uint64_t base = block * nn;
     uint32_t* pa = prm.data;
     uint32_t* pb = prm.data + prm.poly_words;
@@ -741,9 +747,9 @@ __device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>
         uint32_t x[L];
         int slot = ((j >> log2n) << log2n) + bitrev(j & (n - 1), log2n);
         ld_res<L>(x, pa + ((base + j) * m + t) * L);
-        st_res<L>(sa + slot * G::EW + t * L, x);
+        st_res<L>(sa + slot * G::ES + t * L, x);
         ld_res<L>(x, pb + ((base + j) * m + t) * L);
-        st_res<L>(sb + slot * G::EW + t * L, x);
+        st_res<L>(sb + slot * G::ES + t * L, x);
     }
     __syncthreads();
     const int root = G::TWO_M / n;
@@ -761,8 +767,8 @@ __device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>
 #pragma unroll
         for (int w = 0; w < LR; ++w) ks[w] = prm.kscale[w];
         for (int v = warp; v < n; v += kWarps) {
-            i8_stage_x_from32<m, L, LR>(X, sa + v * G::EW, lane);
-            i8_stage_ext_from32<m, L, LR>(E, sb + v * G::EW, mr, lane);
+            i8_stage_x_from32<m, L, LR>(X, sa + v * G::ES, lane);
+            i8_stage_ext_from32<m, L, LR>(E, sb + v * G::ES, mr, lane);
             __syncwarp();
             i8_stage<m, LR>(xb, fb, (int)prm.i8_S, X, E, lane);
             __syncwarp();
@@ -773,7 +779,7 @@ __device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>
                 uint32_t scaled[LR], o32[L];
                 mont_mul_rr<LR>(scaled, out[c], ks, mr);
                 from_rr<L, LR>(o32, scaled);
-                st_res<L>(sa + v * G::EW + (lane + 32 * c) * L, o32);
+                st_res<L>(sa + v * G::ES + (lane + 32 * c) * L, o32);
             }
             __syncwarp();
         }
@@ -794,7 +800,7 @@ __device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>
             uint32_t x[4][LR], w[L];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                ld_res<L>(w, sb + v * G::EW + (lane + j * NT::TEAM) * L);
+                ld_res<L>(w, sb + v * G::ES + (lane + j * NT::TEAM) * L);
                 to_rr<L, LR>(x[j], w);
             }
             ntt_forward<m, LR>(x, buf, lane, nt.mask, prm.ntt_cst, mr);
@@ -818,7 +824,7 @@ __device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>
             if (!prm.square || prm.ntt_prescale) {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    ld_res<L>(w, sa + v * G::EW + (lane + j * NT::TEAM) * L);
+                    ld_res<L>(w, sa + v * G::ES + (lane + j * NT::TEAM) * L);
                     to_rr<L, LR>(x[j], w);
                 }
                 ntt_forward<m, LR>(x, buf, lane, nt.mask, prm.ntt_cst, mr);
@@ -843,7 +849,7 @@ __device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>
                 uint32_t c[LR];
                 canon<LR>(c, x[j], mr);
                 from_rr<L, LR>(w, c);
-                st_res<L>(sa + v * G::EW + (lane + j * NT::TEAM) * L, w);
+                st_res<L>(sa + v * G::ES + (lane + j * NT::TEAM) * L, w);
             }
         }
     } else {
@@ -853,8 +859,8 @@ __device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>
 #pragma unroll
         for (int w = 0; w < LR; ++w) ks[w] = prm.kscale[w];
         for (int v = tm.id; v < n; v += G::NTEAMS) {
-            stage_x_rr<m, L, LR>(X, sa + v * G::EW, tm.lane);
-            stage_ext_from32<m, L, LR>(E, sb + v * G::EW, mr, tm.lane);
+            stage_x_rr<m, L, LR>(X, sa + v * G::ES, tm.lane);
+            stage_ext_from32<m, L, LR>(E, sb + v * G::ES, mr, tm.lane);
             __syncwarp(tm.mask);
             uint32_t out[2][LR];
             negacyclic_mul_rr<m, LR>(out, X, E, 0, mr, tm.lane);
@@ -863,7 +869,7 @@ __device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>
                 uint32_t scaled[LR], o32[L];
                 mont_mul_rr<LR>(scaled, out[c], ks, mr);
                 from_rr<L, LR>(o32, scaled);
-                st_res<L>(sa + v * G::EW + (2 * tm.lane + c) * L, o32);
+                st_res<L>(sa + v * G::ES + (2 * tm.lane + c) * L, o32);
             }
             __syncwarp(tm.mask);
         }
@@ -875,7 +881,7 @@ __device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>
         int j = idx / m, t = idx % m;
         uint32_t x[L];
         const int slot = ((j >> log2n) << log2n) + bitrev(j & (n - 1), log2n);
-        ld_res<L>(x, sa + slot * G::EW + t * L);
+        ld_res<L>(x, sa + slot * G::ES + t * L);
         st_res<L>(pa + ((base + j) * m + t) * L, x);
     }
 }
@@ -946,14 +952,14 @@ __device__ __forceinline__ void dft_inv_column(const LevelParams& prm, const Mod
         int j = idx / m, t = idx % m;
         uint32_t x[L];
         ld_res<L>(x, poly + ((base + (uint64_t)j * mu_d + l) * m + t) * L);
-        st_res<L>(col + j * G::EW + t * L, x);
+        st_res<L>(col + j * G::ES + t * L, x);
     }
     __syncthreads();
     dft_dif<m, L>(col, 1, G::TWO_M, G::TWO_M - 1, md);
     for (int idx = threadIdx.x; idx < G::TWO_M * m; idx += kThreads) {
         int j = idx / m, t = idx % m;
         uint32_t x[L];
-        ld_res<L>(x, col + bitrev(j, LOG2_TWO_M) * G::EW + t * L);
+        ld_res<L>(x, col + bitrev(j, LOG2_TWO_M) * G::ES + t * L);
         st_res<L>(poly + ((base + (uint64_t)j * mu_d + l) * m + t) * L, x);
     }
 }
@@ -996,7 +1002,7 @@ __device__ __forceinline__ void half_load_fwd(const LevelParams& prm, uint32_t* 
     for (int idx = threadIdx.x; idx < m * m; idx += kThreads) {
         const int i = idx / m, t = idx % m;
         const uint64_t j = 2 * (uint64_t)i + parity;
-        uint32_t* dst = half + bitrev(i, LOG2_M) * G::EW + t * L;
+        uint32_t* dst = half + bitrev(i, LOG2_M) * G::ES + t * L;
         if constexpr (FIRST) {
             const uint64_t io = j * mu_d + l;           // outer coefficient index
             uint32_t v = 0;
@@ -1046,7 +1052,7 @@ __global__ void __launch_bounds__(kThreads) k_dft_fwd_half(LevelParams prm, Mod<
                 uint32_t a[L], y[L], pl[L], mi[L];
                 bool ng;
                 ld_res<L>(a, E + v * G::EW + t * L);
-                shifted<m, L>(y, ng, smem + v * G::EW, t, v);
+                shifted<m, L>(y, ng, smem + v * G::ES, t, v);
                 add_mod<L>(pl, a, y, md);
                 sub_mod<L>(mi, a, y, md);
                 // where the shifted coefficient carries a minus sign the two results trade places
@@ -1083,7 +1089,7 @@ __global__ void __launch_bounds__(kThreads) k_dft_inv_half(LevelParams prm, Mod<
             ld_res<L>(a, pa + t * L);
             ld_res<L>(b, pb + t * L);
             add_mod<L>(r, a, b, md);
-            st_res<L>(smem + k * G::EW + t * L, r);
+            st_res<L>(smem + k * G::ES + t * L, r);
             // coefficient t of alpha^sh (a - b): +-(a - b)[t - sh]; b - a where the sign is negative
             const int sh = (ROOT * k) & (G::TWO_M - 1);
             int src = t - sh;
@@ -1107,7 +1113,7 @@ __global__ void __launch_bounds__(kThreads) k_dft_inv_half(LevelParams prm, Mod<
         for (int idx = threadIdx.x; idx < m * m; idx += kThreads) {
             const int v = idx / m, t = idx % m;
             uint32_t x[L];
-            ld_res<L>(x, smem + bitrev(v, LOG2_M) * G::EW + t * L);
+            ld_res<L>(x, smem + bitrev(v, LOG2_M) * G::ES + t * L);
             st_res<L>(poly + ((base + (uint64_t)(2 * v) * mu_d + l) * m + t) * L, x);
         }
         __syncthreads();
@@ -1118,7 +1124,7 @@ __global__ void __launch_bounds__(kThreads) k_dft_inv_half(LevelParams prm, Mod<
         for (int idx = threadIdx.x; idx < m * m; idx += kThreads) {
             const int v = idx / m, t = idx % m;
             uint32_t x[L];
-            ld_res<L>(x, smem + bitrev(v, LOG2_M) * G::EW + t * L);
+            ld_res<L>(x, smem + bitrev(v, LOG2_M) * G::ES + t * L);
             st_res<L>(poly + ((base + (uint64_t)(2 * v + 1) * mu_d + l) * m + t) * L, x);
         }
         __syncthreads();
@@ -1127,12 +1133,13 @@ __global__ void __launch_bounds__(kThreads) k_dft_inv_half(LevelParams prm, Mod<
 
 template <int m, int L>
 constexpr size_t half_column_smem_bytes() {
-    return sizeof(uint32_t) * (size_t)m * Geo<m, L>::EW;
+    static_assert(Geo<m, L>::ES == Geo<m, L>::EW, "half columns are copied to and from their scratch word for word");
+    return sizeof(uint32_t) * (size_t)m * Geo<m, L>::ES;
 }
 
 template <int m, int L>
 constexpr size_t column_smem_bytes() {
-    return sizeof(uint32_t) * (size_t)Geo<m, L>::TWO_M * Geo<m, L>::EW;
+    return sizeof(uint32_t) * (size_t)Geo<m, L>::TWO_M * Geo<m, L>::ES;
 }
 
 template <int m, int L, int LR>
@@ -1147,7 +1154,7 @@ size_t final_smem_bytes(int n, int form = kFormDirect, int S = 0) {
                       : form == kFormNtt ? (size_t)NttTeam<m>::NTEAMS * 2 * m * LR
                                          : (size_t)G::NTEAMS * TeamBuf<m, LR>::WORDS;
     const size_t nn = (size_t)n * (form == kFormNtt ? final_blocks_per_cta<m>(n) : 1);
-    return sizeof(uint32_t) * (2 * nn * G::EW + tb);
+    return sizeof(uint32_t) * (2 * nn * G::ES + tb);
 }
 
 template <int m, int L, int LR>

@@ -105,7 +105,7 @@ __device__ __forceinline__ void level0_fwd_eval(const LevelParams& prm, const Mo
     using G = Geo<m, L>;
     using NT = NttTeam<m>;
     uint32_t* col = smem;
-    uint32_t* xbuf = smem + G::TWO_M * G::EW;
+    uint32_t* xbuf = smem + G::TWO_M * G::ES;
     uint32_t* poly = prm.data + (op ? prm.poly_words : 0);
     const int lg_mu = (__ffsll((long long)prm.len) - 1) - ilog2<G::TWO_M>();
     const uint64_t mu_d = 1ull << lg_mu;
@@ -120,7 +120,7 @@ __device__ __forceinline__ void level0_fwd_eval(const LevelParams& prm, const Mo
     uint32_t bn[LR];
     ldg_rr<LR>(bn, prm.ntt_cst + NttLayout<m>::BN * LR);
     for (int v = nt.id; v < G::TWO_M; v += NT::NTEAMS) {
-        const uint32_t* src = col + v * G::EW;
+        const uint32_t* src = col + v * G::ES;
         uint32_t* dst = poly + (base + (uint64_t)v * mu_d + l) * G::EW;
         const uint64_t e = (uint64_t)v * l * prm.bp;      // rho^e = alpha^r rho^s
         const int r = (int)(e >> prm.log2_mu_top);
@@ -315,7 +315,7 @@ __device__ __forceinline__ void level0_inv_eval(const LevelParams& prm, const Mo
     using NT = NttTeam<m>;
     constexpr int LOG2_TWO_M = ilog2<G::TWO_M>();
     uint32_t* col = smem;
-    uint32_t* xbuf = smem + G::TWO_M * G::EW;
+    uint32_t* xbuf = smem + G::TWO_M * G::ES;
     uint32_t* poly = prm.data;
     const int lg_mu = (__ffsll((long long)prm.len) - 1) - LOG2_TWO_M;
     const uint64_t mu_d = 1ull << lg_mu;
@@ -358,7 +358,7 @@ __device__ __forceinline__ void level0_inv_eval(const LevelParams& prm, const Mo
             canon<LR>(c, vv[j], mr);
             if (neg) neg_rr<LR>(c, c, mr);
             from_rr<L, LR>(o, c);
-            st_res<L>(col + v * G::EW + pos * L, o);
+            st_res<L>(col + v * G::ES + pos * L, o);
         }
     }
     __syncthreads();
@@ -366,7 +366,7 @@ __device__ __forceinline__ void level0_inv_eval(const LevelParams& prm, const Mo
     for (int idx = threadIdx.x; idx < G::TWO_M * m; idx += kThreads) {
         int j = idx / m, t = idx % m;
         uint32_t x[L];
-        ld_res<L>(x, col + bitrev(j, LOG2_TWO_M) * G::EW + t * L);
+        ld_res<L>(x, col + bitrev(j, LOG2_TWO_M) * G::ES + t * L);
         st_res<L>(poly + ((base + (uint64_t)j * mu_d + l) * m + t) * L, x);
     }
 }

@@ -65,14 +65,14 @@ __global__ void __launch_bounds__(kThreads) k_final_dft(LevelParams prm, Mod<L> 
         int j = idx / m, t = idx % m;
         uint32_t x[L];
         ld_res<L>(x, prm.data + ((base + j) * m + t) * L);
-        st_res<L>(smem + bitrev(j, log2n) * G::EW + t * L, x);
+        st_res<L>(smem + bitrev(j, log2n) * G::ES + t * L, x);
     }
     __syncthreads();
     dft_dit<m, L>(smem, 1, n, G::TWO_M / n, md);
     for (int idx = threadIdx.x; idx < n * m; idx += kThreads) {
         int j = idx / m, t = idx % m;
         uint32_t x[L];
-        ld_res<L>(x, smem + j * G::EW + t * L);
+        ld_res<L>(x, smem + j * G::ES + t * L);
         st_res<L>(prm.data + ((base + j) * m + t) * L, x);
     }
 }
@@ -191,7 +191,7 @@ dkss_status prepare(dkss_plan_s* pl) {
     // length 2m), capped by the device, so that no plan lowers another's.
     const int fin_max = (int)std::min<size_t>(final_smem_bytes<m, L, LR>(G::TWO_M), (size_t)optin);
     const int fin_ntt_max = (int)std::min<size_t>(final_smem_bytes<m, L, LR>(G::TWO_M, kFormNtt), (size_t)optin);
-    const int fdft_max = (int)std::min<size_t>(sizeof(uint32_t) * G::TWO_M * G::EW, (size_t)optin);
+    const int fdft_max = (int)std::min<size_t>(sizeof(uint32_t) * G::TWO_M * G::ES, (size_t)optin);
     if (cudaFuncSetAttribute(k_dft_fwd<m, L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, colb) ||
         cudaFuncSetAttribute(k_dft_fwd<m, L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, colb) ||
         cudaFuncSetAttribute(k_dft_inv<m, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, colb) ||
@@ -514,7 +514,7 @@ dkss_status run_forward(dkss_plan_s* pl, const uint64_t* a, uint64_t* out, cudaS
     dkss_status s = launch_forward_levels<m, L, LR>(pl, lp, 1, st);
     if (s != DKSS_OK) return s;
     lp.len = pl->r_last;
-    k_final_dft<m, L><<<(unsigned)(pl->P2 / pl->r_last), kThreads, sizeof(uint32_t) * pl->r_last * G::EW, st>>>(lp, md);
+    k_final_dft<m, L><<<(unsigned)(pl->P2 / pl->r_last), kThreads, sizeof(uint32_t) * pl->r_last * G::ES, st>>>(lp, md);
     DKSS_CHECK_LAUNCH();
     uint64_t total = pl->P2 * m;
     k_unpermute<m, L><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(pl->d_work, out, pl->P2, pl->col_levels);

@@ -26,6 +26,7 @@ SMALL = [
     (1 << 22, 1 << 12, 64, 32, 7340033, 4),  # m=64, L=3 (three REDC subtractions), last level 2m
     (1 << 21, 1 << 14, 64, 16, 998244353, 4),  # m=64, L=4, two radix-2m levels, last level 2
     (4096, 32, 16, 16, 40961, 3),           # m=16, L=2, LR=2: NTT form prescales the componentwise products
+    (65536, 256, 16, 32, 12289, 6),         # m=16, L=3: padded shared-memory element stride
 ]
 
 
