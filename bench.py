@@ -58,7 +58,7 @@ SM_MAX_MHZ = 2070.0
 HBM_GBS = 6782.1                  # STREAM-style copy bandwidth measured on a GB300 (HBM roofline denominator)
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture
 # (profiles/stage_kernels_dkss_2p24b*.md); valid only for the kernel version captured.
-FORM_FLAGS = {"ntt": 0, "eval": 128, "direct": 16, "int8tc": 2}   # binding.LEVELS_EVAL, RMUL_DIRECT, FORM_INT8TC
+FORM_FLAGS = {"ntt": 0, "mont": 512, "eval": 128, "direct": 16, "int8tc": 2}   # binding.ARITH_MONT, LEVELS_EVAL, ...
 I8_TOPS = 150.0                   # mma.sync.m16n8k32 u8 throughput measured on a GB300 (2 ops per MAC)
 NCU_TRAFFIC_BYTES = {("dkss_2p24b", "ntt", "fwd_twiddle"): 46.6e6,
                      ("dkss_2p24b", "eval", "fwd_twiddle"): 44.3e6}
@@ -66,8 +66,9 @@ NCU_TRAFFIC_BYTES = {("dkss_2p24b", "ntt", "fwd_twiddle"): 46.6e6,
 # from one ncu capture of the same kernel on the 2^26-bit product with the same
 # ring (profiles/stage_kernels_dkss_2p32b.md: 478 MB for 259,842 elements and
 # 408 MB for 227,584); a full launch's traffic is this times its elements.
-NCU_BYTES_PER_ELEMENT = {("dkss_2p32b", "ntt", "config", "fwd_twiddle"): 1817.0,
-                         ("dkss_2p26b_ring2p32", "ntt", "config", "fwd_twiddle"): 1817.0}
+# (Those captures ran the 26-bit-limb Montgomery kernels, now the "mont" form.)
+NCU_BYTES_PER_ELEMENT = {("dkss_2p32b", "mont", "config", "fwd_twiddle"): 1817.0,
+                         ("dkss_2p26b_ring2p32", "mont", "config", "fwd_twiddle"): 1817.0}
 
 
 def parse_args():
@@ -91,10 +92,11 @@ def parse_args():
     ap.add_argument("--no-thesis-points", action="store_true",
                     help="skip the thesis's operand lengths over Proth rings")
     ap.add_argument("--thesis-budget-ms", type=float, default=600.0)
-    ap.add_argument("--form", default="ntt", choices=["ntt", "eval", "direct", "int8tc"],
+    ap.add_argument("--form", default="ntt", choices=["ntt", "mont", "eval", "direct", "int8tc"],
                     help="alpha-shift inner DFTs with R-multiplications through the evaluation map of R (ntt, the "
-                         "default), inner levels in evaluation coordinates (eval), the direct convolution, or "
-                         "INT8 tensor-core byte-slice convolutions (int8tc)")
+                         "default; p-adic digits for m = 64 over p^4), the same with 26-bit-limb Montgomery "
+                         "products (mont), inner levels in evaluation coordinates (eval), the direct convolution, "
+                         "or INT8 tensor-core byte-slice convolutions (int8tc)")
     return ap.parse_args()
 
 
@@ -182,7 +184,15 @@ def modmul_imads(L):
     return 2 * L * L + L * (2 * L + 1)
 
 
-def rmul_imads(m, L, form, pointwise=False):
+def padic_mul_imads(z):
+    """32-bit multiply-adds of one product mod p^z in p-adic digits: the
+    z(z+1)/2 digit products of the truncated columns (lo and hi halves), and per
+    column a Barrett carry: the high half of a 64 x 64-bit product by the
+    reciprocal of p (seven multiply-adds) and one low product q p."""
+    return z * (z + 1) + 8 * z
+
+
+def rmul_imads(m, L, form, pointwise=False, padic_z=0):
     """Multiply-adds of one R-multiplication.
     direct: the negacyclic convolution (thesis eq. ncycconv), m^2 limb-level
       products and m reductions.
@@ -193,7 +203,8 @@ def rmul_imads(m, L, form, pointwise=False):
         return 2 * m * m * L * L + m * L * (2 * L + 1)
     lg = m.bit_length() - 1
     forwards = 2 if pointwise else 1
-    return (forwards * (m // 2) * lg + m + (m // 2) * (lg + 1)) * modmul_imads(L)
+    per = padic_mul_imads(padic_z) if padic_z else modmul_imads(L)
+    return (forwards * (m // 2) * lg + m + (m // 2) * (lg + 1)) * per
 
 
 def nontrivial_dft_products(n):
@@ -275,8 +286,10 @@ def stage_work(info, m, form):
         mu_d = length // (2 * m)
         nontrivial.append((P2 // length) * (mu_d - 1) * (2 * m - 1))
         length //= 2 * m
-    r = rmul_imads(m, L, form)
-    rp = rmul_imads(m, L, form, pointwise=True)
+    # m = 64 over p^4: the NTT form's products are p-adic (plan info "padic")
+    pz = info["z"] if info.get("padic") and form != "direct" else 0
+    r = rmul_imads(m, L, form, padic_z=pz)
+    rp = rmul_imads(m, L, form, pointwise=True, padic_z=pz)
     scale = P2 * m * modmul_imads(L) if form == "direct" else 0
     return {
         "fwd_twiddle": (2 * sum(nontrivial) * r, col_levels),
@@ -598,8 +611,8 @@ def compare_forms(workload, main_form, dev, flush, a, b, out, ms_main, budget_ms
     cfg = syn.workload_params(workload)
     res = {}
     stream = torch.cuda.current_stream(dev)
-    for name, flags in (("ntt", 0), ("eval", binding.LEVELS_EVAL), ("direct", binding.RMUL_DIRECT),
-                        ("int8tc", binding.FORM_INT8TC)):
+    for name, flags in (("ntt", 0), ("mont", binding.ARITH_MONT), ("eval", binding.LEVELS_EVAL),
+                        ("direct", binding.RMUL_DIRECT), ("int8tc", binding.FORM_INT8TC)):
         if name == main_form:
             res[name] = {"ms_per_step": round(ms_main, 5)}
             continue

@@ -59,6 +59,10 @@ enum {
                               DKSS_EDEVICE (the product itself is then not to be trusted) */
     DKSS_RMUL_DIRECT = 16, /* R-multiplications by the direct negacyclic convolution
                               (Section 2.9.2) instead of through the evaluation map of R */
+    DKSS_ARITH_MONT = 512, /* NTT form with m = 64 over p^4, p < 2^30: keep the 26-bit-limb Montgomery
+                              products instead of the default p-adic digits (each residue as
+                              four base-p digits, a product as ten digit products and a carry
+                              chain; Section 3.2.2's ring Z/p^zZ, no change of the transform) */
     DKSS_LEVELS_EVAL = 128 /* every radix-2m level but the first, and the last level, in the
                               evaluation coordinates of R (the CRT map of Section 3.2.3):
                               their inner DFTs become m independent DFTs over Z/p^zZ with
@@ -294,7 +298,8 @@ dkss_status dkss_mul_batch(const dkss_job* jobs, size_t count, uint32_t flags, d
  * the plan holds: its two transformed polynomials (the transform runs in
  * place, level by level, with no third polynomial for the thesis's
  * intermediate abar of Section 4.5), the twiddle tables and the carry-scan
- * scratch (0 for a host-only view).
+ * scratch (0 for a host-only view), and 1 when the m = 64 transforms in R
+ * compute in p-adic digits (see DKSS_ARITH_MONT) else 0.
  */
 dkss_status dkss_plan_info(dkss_plan_t plan, uint64_t* consts, size_t n_consts, uint64_t* rho_out);
 

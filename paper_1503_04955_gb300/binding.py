@@ -29,6 +29,7 @@ EXPORTS = ["dkss_plan", "dkss_mul", "dkss_sqr", "dkss_ll_step", "dkss_mul_host",
 FORM_PROFILE = 4
 RMUL_DIRECT = 16
 LEVELS_EVAL = 128
+ARITH_MONT = 512       # m = 64 over p^4: 26-bit-limb Montgomery products instead of p-adic digits
 DEBUG_CHECKS = 8
 TUNE_RULE = 32         # dkss_plan with M..z = 0: the thesis's rule without timing
 FAULT_RHO, FAULT_HOST_ALLOC, FAULT_RANGE = 1, 2, 4
@@ -118,9 +119,10 @@ def _words2_to_ints(arr):
     return [int(lo) | (int(hi) << 64) for lo, hi in zip(arr[0::2], arr[1::2])]
 
 
-N_CONSTS = 24
+N_CONSTS = 25
 CONST_NAMES = ["P2", "mu", "L", "levels", "pz_lo", "pz_hi", "zeta", "omega_lo", "omega_hi", "gamma_lo", "gamma_hi",
-               "LR", "rmul", "prescale", "eval_ok", "eval_skip", "M", "m", "u", "p_lo", "z", "p_hi", "sparse", "dev_bytes"]
+               "LR", "rmul", "prescale", "eval_ok", "eval_skip", "M", "m", "u", "p_lo", "z", "p_hi", "sparse", "dev_bytes",
+               "padic"]
 RMUL_FORMS = ("ntt", "direct", "int8tc", "eval")     # consts["rmul"] indexes this
 
 

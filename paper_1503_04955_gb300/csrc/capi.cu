@@ -305,6 +305,19 @@ void put_rr(uint32_t* dst, u128 v, uint32_t LR) {
     for (uint32_t w = 0; w < LR; ++w) dst[w] = (uint32_t)(v >> (26 * w)) & ((1u << 26) - 1);
 }
 
+// the four base-p digits of a canonical residue (p-adic digit form, padic.cuh)
+void put_pd(uint32_t* dst, u128 v, u128 p) {
+    for (uint32_t k = 0; k < 4; ++k) {
+        dst[k] = (uint32_t)(v % p);
+        v /= p;
+    }
+}
+
+// K (p, p-1, p-1, p-1): digits of K p^4, zero mod p^4
+void put_pd_bias(uint32_t* dst, uint32_t K, u128 p) {
+    for (uint32_t k = 0; k < 4; ++k) dst[k] = (uint32_t)(K * (k == 0 ? p : p - 1));
+}
+
 uint32_t brv(uint32_t x, uint32_t bits) {
     uint32_t r = 0;
     for (uint32_t i = 0; i < bits; ++i) r |= ((x >> i) & 1u) << (bits - 1 - i);
@@ -312,7 +325,49 @@ uint32_t brv(uint32_t x, uint32_t bits) {
 }
 
 // Constants of the transform in R (ntt_rmul.cuh, NttLayout): psi = gamma.
+// Constants of the transform in p-adic digits (padic.cuh, PdLayout): the
+// entries of NttLayout as plain residues, biases K (p, p-1, p-1, p-1), then the
+// digits of 2^(32j) mod p^4, j < 4.
+void build_ntt_consts_pd(const dkss_plan_s* pl, std::vector<uint32_t>& out) {
+    constexpr uint32_t Z = 4;
+    const uint32_t m = pl->m;
+    uint32_t lg = 0;
+    while ((1u << lg) < m) ++lg;
+    const uint32_t Q = 2 * m + lg + 2, PSI = Q + 7 + lg + 1, COUNT = PSI + 2 * m;
+    out.assign((size_t)(COUNT + 4) * Z, 0);
+    MontCtx c(pl->q);
+    const u128 phi = pl->q / pl->p * (pl->p - 1);
+    const u128 psi = c.to(pl->roots.gamma);
+    const u128 psi_inv = c.pow(psi, phi - 1);
+    auto put = [&](uint32_t idx, u128 v_m) { put_pd(&out[(size_t)idx * Z], c.from(v_m), pl->p); };
+    for (uint32_t k = 1; k < m; ++k) {
+        put(k, c.pow(psi, brv(k, lg)));
+        put(m + k, c.pow(psi_inv, brv(k, lg)));
+    }
+    for (uint32_t b = 0; b < lg; ++b) put_pd_bias(&out[(size_t)(2 * m + b) * Z], pl->pd_bias.kb[b], pl->p);
+    put_pd_bias(&out[(size_t)(2 * m + lg) * Z], pl->pd_bias.kf, pl->p);
+    put_pd_bias(&out[(size_t)(2 * m + lg + 1) * Z], pl->pd_bias.kf, pl->p);
+    const u128 minv = c.pow(c.to(m), phi - 1);
+    const u128 p2inv = c.pow(c.to(pl->P2 % pl->q), phi - 1);
+    const u128 zlast = c.pow(psi_inv, brv(1, lg));
+    put(Q + 1, minv);
+    put(Q + 2, c.mul(zlast, minv));
+    put(Q + 3, c.mul(minv, p2inv));
+    put(Q + 4, c.mul(c.mul(zlast, minv), p2inv));
+    put(Q + 5, c.to(1));
+    put(Q + 6, zlast);
+    u128 pw = 1;
+    for (uint32_t j = 0; j < 4; ++j) {
+        put_pd(&out[(size_t)(COUNT + j) * Z], pw, pl->p);
+        pw = c.from(c.mul(c.to(pw), c.to(((u128)1 << 32) % pl->q)));
+    }
+}
+
 void build_ntt_consts(const dkss_plan_s* pl, std::vector<uint32_t>& out) {
+    if (pl->padic) {
+        build_ntt_consts_pd(pl, out);
+        return;
+    }
     const uint32_t m = pl->m, LR = pl->LR;
     uint32_t lg = 0;
     while ((1u << lg) < m) ++lg;
@@ -413,7 +468,7 @@ void build_eval_level_tables(const dkss_plan_s* pl, std::vector<uint32_t>& out, 
 // backward transform's m^-1 (ntt_backward<RAW_LO>), for the levels in
 // evaluation coordinates not.
 void build_eval_table(const dkss_plan_s* pl, std::vector<uint32_t>& out, bool with_minv) {
-    const uint32_t m = pl->m, LR = pl->LR;
+    const uint32_t m = pl->m, LR = pl->padic ? 4u : pl->LR;
     uint32_t lg = 0;
     while ((1u << lg) < m) ++lg;
     const uint64_t mu = pl->mu_top;
@@ -437,8 +492,10 @@ void build_eval_table(const dkss_plan_s* pl, std::vector<uint32_t>& out, bool wi
                     val[j] = cur;
                     cur = c.mul(cur, w2);
                 }
-                for (uint32_t i = 0; i < m; ++i)
-                    put_rr(&out[(s * m + i) * LR], to_dev(c, c.mul(val[brv(i, lg)], scale), rdev), LR);
+                for (uint32_t i = 0; i < m; ++i) {
+                    if (pl->padic) put_pd(&out[(s * m + i) * LR], c.from(c.mul(val[brv(i, lg)], scale)), pl->p);
+                    else put_rr(&out[(s * m + i) * LR], to_dev(c, c.mul(val[brv(i, lg)], scale), rdev), LR);
+                }
                 ws = c.mul(ws, om);
             }
         });
@@ -478,15 +535,15 @@ void fill_consts(const dkss_plan_s* pl, uint64_t* consts, size_t n) {
                           : ((pl->flags & DKSS_RMUL_DIRECT) || !pl->ntt_ok)         ? 1
                           : pl->eval_levels                                          ? 3
                                                                                      : 0;
-    uint64_t v[24] = {pl->P2, pl->mu_top, pl->L, (uint64_t)pl->col_levels + 1, (uint64_t)pl->q,
+    uint64_t v[25] = {pl->P2, pl->mu_top, pl->L, (uint64_t)pl->col_levels + 1, (uint64_t)pl->q,
                       (uint64_t)(pl->q >> 64), pl->roots.zeta, (uint64_t)pl->roots.omega,
                       (uint64_t)(pl->roots.omega >> 64), (uint64_t)pl->roots.gamma,
                       (uint64_t)(pl->roots.gamma >> 64), pl->LR, form,
                       (uint64_t)(pl->ntt_ok && pl->ntt_bias.prescale),
                       (uint64_t)(pl->ntt_ok && pl->ntt_bias.eval_ok && pl->m <= 32), pl->ntt_bias.eval_skip,
                       pl->M, pl->m, pl->u, (uint64_t)pl->p, pl->z, (uint64_t)(pl->p >> 64), pl->q_sparse ? 1u : 0u,
-                      pl->dev_bytes};
-    for (size_t i = 0; i < n && i < 24; ++i) consts[i] = v[i];
+                      pl->dev_bytes, pl->padic ? 1u : 0u};
+    for (size_t i = 0; i < n && i < 25; ++i) consts[i] = v[i];
 }
 
 }  // namespace
@@ -727,6 +784,18 @@ dkss_status finish_plan(dkss_plan_s* pl, dkss_status s, dkss_plan_t* plan) {
     if (!pl->ntt_ok && !(flags & (DKSS_RMUL_DIRECT | DKSS_FORM_INT8TC))) pl->flags |= DKSS_RMUL_DIRECT;
     // inner levels in evaluation coordinates: the NTT form, m <= 32, within their limits
     pl->eval_levels = pl->eval_levels && !(pl->flags & DKSS_RMUL_DIRECT);
+    // m = 64 NTT kernels over p^4 with p < 2^30: p-adic digits (padic.cuh) within their limits
+    pl->padic = !(pl->flags & (DKSS_RMUL_DIRECT | DKSS_FORM_INT8TC | DKSS_ARITH_MONT)) && pl->m == 64 &&
+                pl->z == 4 && pl->p < ((u128)1 << 30) && !pl->q_sparse &&
+                pd_lazy_bounds((uint64_t)pl->p, pl->m, pl->L, &pl->pd_bias);
+    if (pl->padic) {
+        const uint64_t p = (uint64_t)pl->p;
+        uint32_t s = 0;
+        while ((p >> (s + 1)) != 0) ++s;
+        pl->pd_s = s;
+        pl->pd_nmu = (uint32_t)(((uint64_t)1 << 32) / p);
+        pl->pd_mu = (uint64_t)((((u128)1) << (64 + s)) / p);
+    }
     if (cudaGetDevice(&pl->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&pl->sm_count, cudaDevAttrMultiProcessorCount, pl->device) != cudaSuccess) {
         delete pl;

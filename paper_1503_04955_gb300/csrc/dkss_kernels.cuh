@@ -22,6 +22,7 @@
 #include "arith.cuh"
 #include "i8_rmul.cuh"
 #include "ntt_rmul.cuh"
+#include "padic.cuh"
 #include "rr_arith.cuh"
 
 namespace dkss {
@@ -577,10 +578,93 @@ __device__ __forceinline__ void twiddle_ntt_group(const LevelParams& prm, const 
     }
 }
 
+// Coefficient t of alpha^r x in p-adic digits (padic.cuh): x's residue
+// converted from its L words (pw: digits of 2^(32j) mod p^z), a negated one
+// as the bias bn - y (bn = (p, p-1, ..., p-1), y canonical).
+template <int m, int L, int Z>
+__device__ __forceinline__ void load_shifted_pd(uint32_t (&out)[Z], const uint32_t* x, int t, int r,
+                                                const uint32_t (&bn)[Z], const uint32_t* pw, const ModPD<Z>& md) {
+    int src = t - r;
+    bool neg = false;
+    if (src < 0) {
+        src += m;
+        neg = true;
+        if (src < 0) {
+            src += m;
+            neg = false;
+        }
+    }
+    uint32_t v[L], y[Z];
+    ld_res<L>(v, x + src * L);
+    pd_from_words<L, Z>(y, v, pw, md);
+#pragma unroll
+    for (int i = 0; i < Z; ++i) out[i] = neg ? bn[i] - y[i] : y[i];
+}
+
+// The bad multiplications of twiddle_ntt_group with the transform in R in
+// p-adic digits: the element's residues are converted on load and back on
+// store, the twiddle table and the transform constants hold digits.
+template <int m, int L, bool INV, int Z>
+__device__ __forceinline__ void twiddle_pd_group(const LevelParams& prm, const ModPD<Z>& md, uint64_t group, int op,
+                                                 uint32_t* xbuf) {
+    using G = Geo<m, L>;
+    using NT = NttTeam<m>;
+    NT tm;
+    uint32_t* poly = prm.data + (op ? prm.poly_words : 0);
+    const int lg_len = __ffsll((long long)prm.len) - 1;
+    const int lg_mu = lg_len - ilog2<G::TWO_M>();
+    const uint64_t idx = group * NT::NTEAMS + tm.id;
+    if (idx >= prm.P2) return;
+    const uint64_t blk = idx >> lg_len, rem = idx & (prm.len - 1);
+    const uint64_t v = rem >> lg_mu, l = rem & ((1ull << lg_mu) - 1);
+    if (v == 0 || l == 0) return;
+    const uint64_t mu_d = 1ull << lg_mu;
+    uint64_t e = v * l * prm.bp;
+    if (INV) e = prm.P2 - e;
+    const int r = (int)(e >> prm.log2_mu_top);
+    const uint64_t sidx = e & (prm.mu_top - 1);
+    uint32_t* x = poly + (blk * prm.len + v * mu_d + l) * G::EW;
+    uint32_t* buf = xbuf + tm.id * m * Z;
+    const int lane = tm.lane;
+    const uint32_t* cst = prm.ntt_cst;
+    uint32_t bn[Z], pw[4 * Z];
+    ldg_rr<Z>(bn, cst + NttLayout<m>::BN * Z);
+#pragma unroll
+    for (int i = 0; i < 4 * Z; ++i) pw[i] = __ldg(cst + PdLayout<m>::POW32 * Z + i);
+    uint32_t vv[4][Z];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) load_shifted_pd<m, L, Z>(vv[j], x, lane + j * NT::TEAM, r, bn, pw, md);
+    ntt_forward_pd<m, Z>(vv, buf, lane, tm.mask, cst, md);
+    const uint32_t* tw = prm.table_eval + (sidx * m + 4 * lane) * Z;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        uint32_t t[Z];
+        ldg_rr<Z>(t, tw + j * Z);
+        mmul<Z>(vv[j], vv[j], t, md);
+    }
+    // the table carries m^-1: the last stage multiplies only by psi^-1
+    ntt_backward_pd<m, Z, true>(vv, buf, lane, tm.mask, cst, 0, NttLayout<m>::ZLAST, md);
+    __syncwarp(tm.mask);   // every lane has read its shifted inputs before any write
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        uint32_t c[Z], o[L];
+        if (j < 2) pd_canon<Z>(c, vv[j], md);
+        else {
+#pragma unroll
+            for (int w = 0; w < Z; ++w) c[w] = vv[j][w];
+        }
+        pd_to_words<L, Z>(o, c, md);
+        st_res<L>(x + (lane + j * NT::TEAM) * L, o);
+    }
+}
+
 template <int m, int L, int LR, bool INV, class MR = ModRR<LR>>
 __global__ void __launch_bounds__(kThreads, (LR >= 5 || m >= 64) ? 3 : 4) k_twiddle_ntt(LevelParams prm, MR mr) {
     extern __shared__ __align__(16) uint32_t smem[];
-    twiddle_ntt_group<m, L, LR, INV, MR>(prm, mr, blockIdx.x, blockIdx.y, smem);
+    if constexpr (IsPD<MR>::value)
+        twiddle_pd_group<m, L, INV, LR>(prm, mr, blockIdx.x, blockIdx.y, smem);
+    else
+        twiddle_ntt_group<m, L, LR, INV, MR>(prm, mr, blockIdx.x, blockIdx.y, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -783,6 +867,54 @@ __device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>
             }
             __syncwarp();
         }
+    } else if constexpr (FORM == kFormNtt && IsPD<MR>::value) {
+        // the transform in R in p-adic digits (padic.cuh): per team an exchange
+        // buffer, then b's canonical evaluations while a is transformed
+        using NT = NttTeam<m>;
+        NT nt;
+        uint32_t* buf = tbuf + nt.id * 2 * m * LR;
+        const int lane = nt.lane;
+        uint32_t* park = buf + m * LR + nt.lane * LR;
+        const uint32_t* cst = prm.ntt_cst;
+        uint32_t pw[4 * LR];
+#pragma unroll
+        for (int i = 0; i < 4 * LR; ++i) pw[i] = __ldg(cst + PdLayout<m>::POW32 * LR + i);
+#pragma unroll 1
+        for (int v = nt.id; v < nn; v += NT::NTEAMS) {
+            uint32_t x[4][LR], w[L];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                ld_res<L>(w, sb + v * G::ES + (lane + j * NT::TEAM) * L);
+                pd_from_words<L, LR>(x[j], w, pw, mr);
+            }
+            ntt_forward_pd<m, LR>(x, buf, lane, nt.mask, cst, mr);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                pd_canon<LR>(x[j], x[j], mr);
+                st_rr<LR>(park + j * NT::TEAM * LR, x[j]);
+            }
+            // a square keeps a = b's evaluations in registers
+            if (!prm.square) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    ld_res<L>(w, sa + v * G::ES + (lane + j * NT::TEAM) * L);
+                    pd_from_words<L, LR>(x[j], w, pw, mr);
+                }
+                ntt_forward_pd<m, LR>(x, buf, lane, nt.mask, cst, mr);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                uint32_t y[LR];
+                ld_rr<LR>(y, park + j * NT::TEAM * LR);
+                mmul<LR>(x[j], x[j], y, mr);
+            }
+            ntt_backward_pd<m, LR>(x, buf, lane, nt.mask, cst, NttLayout<m>::PW_LO, NttLayout<m>::PW_HI, mr);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                pd_to_words<L, LR>(w, x[j], mr);
+                st_res<L>(sa + v * G::ES + (lane + j * NT::TEAM) * L, w);
+            }
+        }
     } else if constexpr (FORM == kFormNtt) {
         // per team: an exchange buffer, then a buffer holding b's evaluations
         // while a is transformed (one element in registers at a time)
@@ -887,7 +1019,8 @@ __device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>
 }
 
 template <int m, int L, int LR, int FORM, class MR = ModRR<LR>>
-__global__ void __launch_bounds__(kThreads, FORM == kFormNtt ? (LR >= 5 ? 2 : 3) : 1) k_final_pointwise(LevelParams prm, Mod<L> md, MR mr) {
+__global__ void __launch_bounds__(kThreads, FORM == kFormNtt ? ((LR >= 5 || IsPD<MR>::value) ? 2 : 3) : 1)
+    k_final_pointwise(LevelParams prm, Mod<L> md, MR mr) {
     extern __shared__ __align__(16) uint32_t smem[];
     final_block<m, L, LR, FORM, MR>(prm, md, mr, smem, blockIdx.x);
 }

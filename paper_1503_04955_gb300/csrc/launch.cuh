@@ -27,6 +27,22 @@ static MR make_modrr(const dkss_plan_s* pl) {
     return md;
 }
 
+// Modulus constants of the NTT-form kernels: 26-bit-limb Montgomery
+// (ModRR, ModRRSparse) or p-adic digits (ModPD, padic.cuh).
+template <int LR, class MR>
+static MR make_mr(const dkss_plan_s* pl) {
+    if constexpr (IsPD<MR>::value) {
+        MR md;
+        md.p = (uint32_t)pl->p;
+        md.nmu = pl->pd_nmu;
+        md.s = pl->pd_s;
+        md.mu = pl->pd_mu;
+        return md;
+    } else {
+        return make_modrr<LR, MR>(pl);
+    }
+}
+
 static LevelParams make_level(const dkss_plan_s* pl) {
     LevelParams lp{};
     lp.data = pl->d_work;
@@ -242,6 +258,23 @@ dkss_status prepare(dkss_plan_s* pl) {
              cudaFuncSetAttribute(k_twiddle_ntt<m, L, LR, true, MS>, cudaFuncAttributeMaxDynamicSharedMemorySize, twn)))
             return DKSS_ECUDA;
     }
+    if constexpr (m == 64) {
+        if (pl->padic) {
+            using PD = ModPD<kPdDigits>;
+            constexpr int Z = kPdDigits;
+            const int twp = (int)twiddle_ntt_smem_bytes<m, L, Z>();
+            const int finp = (int)std::min<size_t>(final_smem_bytes<m, L, Z>(G::TWO_M, kFormNtt), (size_t)optin);
+            if ((int)final_smem_bytes<m, L, Z>((int)pl->r_last, kFormNtt) > optin || twp > optin)
+                return DKSS_EUNSUPPORTED;
+            if (cudaFuncSetAttribute(k_twiddle_ntt<m, L, Z, false, PD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     twp) ||
+                cudaFuncSetAttribute(k_twiddle_ntt<m, L, Z, true, PD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     twp) ||
+                cudaFuncSetAttribute(k_final_pointwise<m, L, Z, kFormNtt, PD>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, finp))
+                return DKSS_ECUDA;
+        }
+    }
     if constexpr (m <= 32) {
         if (pl->eval_levels) {
             const int fe = (int)std::min<size_t>(final_eval_smem_bytes<m, L, LR>(G::TWO_M), (size_t)optin);
@@ -273,12 +306,15 @@ static inline void level_geometry(const dkss_plan_s* pl, uint32_t d, uint64_t* l
 template <int m, int L, int LR, bool INV, class MR = ModRR<LR>>
 static dkss_status launch_twiddle(dkss_plan_s* pl, LevelParams lp, int operands, cudaStream_t st) {
     using G = Geo<m, L>;
-    const MR mr = make_modrr<LR, MR>(pl);
+    const MR mr = make_mr<LR, MR>(pl);
     const uint64_t mu_d = lp.len / G::TWO_M;
     const uint64_t total = (uint64_t)(G::TWO_M - 1) * (mu_d - 1) * (pl->P2 / lp.len);
     if (total == 0) return DKSS_OK;
     dim3 grid((unsigned)((total + G::NTEAMS - 1) / G::NTEAMS), operands);
-    if (pl->flags & DKSS_FORM_INT8TC) {
+    if constexpr (IsPD<MR>::value) {
+        dim3 gn((unsigned)((pl->P2 + NttTeam<m>::NTEAMS - 1) / NttTeam<m>::NTEAMS), operands);
+        k_twiddle_ntt<m, L, LR, INV, MR><<<gn, kThreads, twiddle_ntt_smem_bytes<m, L, LR>(), st>>>(lp, mr);
+    } else if (pl->flags & DKSS_FORM_INT8TC) {
         if constexpr (m >= 32) {
             dim3 g8((unsigned)((total + kWarps - 1) / kWarps), operands);
             k_twiddle_i8<m, L, LR, INV><<<g8, kThreads, twiddle_i8_smem_bytes<m, L, LR>((int)pl->i8_S), st>>>(lp, mr);
@@ -299,18 +335,21 @@ static dkss_status launch_forward_levels(dkss_plan_s* pl, LevelParams lp, int op
     using G = Geo<m, L>;
     const Mod<L> md = make_mod<L>(pl);
     dim3 grid((unsigned)(pl->P2 / G::TWO_M), operands);
-    const bool fused = fused_levels<m, L, LR>(pl);
+    const bool fused = !IsPD<MR>::value && fused_levels<m, L, LR>(pl);
     for (uint32_t d = 0; d < pl->col_levels; ++d) {
         level_geometry(pl, d, &lp.len, &lp.bp);
-        if (fused) {   // inner DFT and R-multiplications of a column in one kernel (NTT form)
-            ProfScope ps(pl, st, kProfFwdTwiddle);
-            const MR mr = make_modrr<LR, MR>(pl);
-            if (d == 0)
-                k_level_fwd_ntt<m, L, LR, true, MR><<<grid, kThreads, level_ntt_smem_bytes<m, L, LR>(), st>>>(lp, md, mr);
-            else
-                k_level_fwd_ntt<m, L, LR, false, MR><<<grid, kThreads, level_ntt_smem_bytes<m, L, LR>(), st>>>(lp, md, mr);
-            DKSS_CHECK_LAUNCH();
-            continue;
+        if constexpr (!IsPD<MR>::value) {
+            if (fused) {   // inner DFT and R-multiplications of a column in one kernel (NTT form)
+                ProfScope ps(pl, st, kProfFwdTwiddle);
+                const MR mr = make_modrr<LR, MR>(pl);
+                if (d == 0)
+                    k_level_fwd_ntt<m, L, LR, true, MR><<<grid, kThreads, level_ntt_smem_bytes<m, L, LR>(), st>>>(lp, md, mr);
+                else
+                    k_level_fwd_ntt<m, L, LR, false, MR><<<grid, kThreads, level_ntt_smem_bytes<m, L, LR>(), st>>>(lp, md,
+                                                                                                                 mr);
+                DKSS_CHECK_LAUNCH();
+                continue;
+            }
         }
         {
             ProfScope ps(pl, st, kProfFwdDft);
@@ -415,8 +454,7 @@ template <int m, int L, int LR, class MR>
 static dkss_status run_mul_coef(dkss_plan_s* pl, const uint64_t* a, const uint64_t* b, uint64_t* out, cudaStream_t st) {
     using G = Geo<m, L>;
     const Mod<L> md = make_mod<L>(pl);
-    const MR mr = make_modrr<LR, MR>(pl);
-    const ModRR<LR> mr0 = make_modrr<LR>(pl);
+    const MR mr = make_mr<LR, MR>(pl);
     LevelParams lp = make_level(pl);
     lp.raw_a = a;
     lp.raw_b = b;
@@ -436,16 +474,21 @@ static dkss_status run_mul_coef(dkss_plan_s* pl, const uint64_t* a, const uint64
     {
         ProfScope ps(pl, st, kProfFinal);
         const unsigned blocks = (unsigned)(pl->P2 / pl->r_last);
-        if (pl->flags & DKSS_FORM_INT8TC) {
+        const unsigned nblocks = blocks / (unsigned)final_blocks_per_cta<m>((int)pl->r_last);
+        if constexpr (IsPD<MR>::value) {
+            k_final_pointwise<m, L, LR, kFormNtt, MR>
+                <<<nblocks, kThreads, final_smem_bytes<m, L, LR>((int)pl->r_last, kFormNtt), st>>>(lp, md, mr);
+        } else if (pl->flags & DKSS_FORM_INT8TC) {
+            const ModRR<LR> mr0 = make_modrr<LR>(pl);
             if constexpr (m >= 32)
                 k_final_pointwise<m, L, LR, kFormI8>
                     <<<blocks, kThreads, final_smem_bytes<m, L, LR>((int)pl->r_last, kFormI8, (int)pl->i8_S), st>>>(
                         lp, md, mr0);
         } else if (pl->flags & DKSS_RMUL_DIRECT) {
+            const ModRR<LR> mr0 = make_modrr<LR>(pl);
             k_final_pointwise<m, L, LR, kFormDirect><<<blocks, kThreads, final_smem_bytes<m, L, LR>((int)pl->r_last), st>>>(
                 lp, md, mr0);
         } else {
-            const unsigned nblocks = blocks / (unsigned)final_blocks_per_cta<m>((int)pl->r_last);
             k_final_pointwise<m, L, LR, kFormNtt, MR>
                 <<<nblocks, kThreads, final_smem_bytes<m, L, LR>((int)pl->r_last, kFormNtt), st>>>(lp, md, mr);
         }
@@ -454,15 +497,17 @@ static dkss_status run_mul_coef(dkss_plan_s* pl, const uint64_t* a, const uint64
     lp.poly_words = pl->poly_words;
     lp.square = 0;
     if ((s = range_check<L>(pl, pl->d_work, pl->P2 * m, st)) != DKSS_OK) return s;
-    const bool fused = fused_levels<m, L, LR>(pl);
+    const bool fused = !IsPD<MR>::value && fused_levels<m, L, LR>(pl);
     for (int d = (int)pl->col_levels - 1; d >= 0; --d) {
         level_geometry(pl, (uint32_t)d, &lp.len, &lp.bp);
-        if (fused) {   // R-multiplications and inner DFT of a column in one kernel (NTT form)
-            ProfScope ps(pl, st, kProfInvTwiddle);
-            k_level_inv_ntt<m, L, LR, MR><<<(unsigned)(pl->P2 / G::TWO_M), kThreads, level_ntt_smem_bytes<m, L, LR>(),
-                                           st>>>(lp, md, mr);
-            DKSS_CHECK_LAUNCH();
-            continue;
+        if constexpr (!IsPD<MR>::value) {
+            if (fused) {   // R-multiplications and inner DFT of a column in one kernel (NTT form)
+                ProfScope ps(pl, st, kProfInvTwiddle);
+                k_level_inv_ntt<m, L, LR, MR><<<(unsigned)(pl->P2 / G::TWO_M), kThreads,
+                                               level_ntt_smem_bytes<m, L, LR>(), st>>>(lp, md, mr);
+                DKSS_CHECK_LAUNCH();
+                continue;
+            }
         }
         {
             ProfScope ps(pl, st, kProfInvTwiddle);
@@ -497,6 +542,9 @@ dkss_status run_mul(dkss_plan_s* pl, const uint64_t* a, const uint64_t* b, uint6
             return launch_decode<m, L, LR>(pl, out, st);
         }
     }
+    if constexpr (m == 64) {
+        if (pl->padic) return run_mul_coef<m, L, kPdDigits, ModPD<kPdDigits>>(pl, a, b, out, st);
+    }
     if constexpr (LR >= 3) {
         if (sparse_ntt<LR>(pl)) return run_mul_coef<m, L, LR, ModRRSparse<LR>>(pl, a, b, out, st);
     }
@@ -511,7 +559,13 @@ dkss_status run_forward(dkss_plan_s* pl, const uint64_t* a, uint64_t* out, cudaS
     lp.raw_a = a;
     lp.raw_b = a;
     if (pl->d_table_minv) lp.table_eval = pl->d_table_minv;   // coefficient levels for a plan in evaluation coordinates
-    dkss_status s = launch_forward_levels<m, L, LR>(pl, lp, 1, st);
+    dkss_status s = DKSS_OK;
+    if constexpr (m == 64) {
+        if (pl->padic) s = launch_forward_levels<m, L, kPdDigits, ModPD<kPdDigits>>(pl, lp, 1, st);
+        else s = launch_forward_levels<m, L, LR>(pl, lp, 1, st);
+    } else {
+        s = launch_forward_levels<m, L, LR>(pl, lp, 1, st);
+    }
     if (s != DKSS_OK) return s;
     lp.len = pl->r_last;
     k_final_dft<m, L><<<(unsigned)(pl->P2 / pl->r_last), kThreads, sizeof(uint32_t) * pl->r_last * G::ES, st>>>(lp, md);

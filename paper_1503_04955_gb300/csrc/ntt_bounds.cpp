@@ -334,4 +334,90 @@ bool ntt_lazy_bounds(uint32_t m, uint32_t LR, u128 q, NttBiases* out) {
     return true;
 }
 
+// Limits of the p-adic digit form (padic.cuh), z = 4 digits: the largest
+// digit of every value and every product column, through ntt_forward_pd,
+// the componentwise product, ntt_backward_pd and the conversions.
+namespace {
+
+struct PdCtx {
+    uint64_t p, nmu, r32;   // floor(2^32 / p), 2^32 mod p
+    static constexpr uint64_t kW = (uint64_t)1 << 32;
+
+    // product of digits <= A and <= B: every column (with its carry) below 2^64
+    bool mmul_ok(uint64_t A, uint64_t B) const {
+        u128 carry = 0;
+        for (int k = 0; k < 4; ++k) {
+            const u128 col = (u128)(k + 1) * A * B + carry;
+            if (col >> 64) return false;
+            carry = col / p + 1;
+        }
+        return true;
+    }
+    // pd_norm / pd_canon of digits <= V: every digit plus its carry below 2^32;
+    // the result's digits (pd_norm) are at most *out
+    bool norm(uint64_t V, uint64_t* out) const {
+        uint64_t C = 0;
+        for (int it = 0; it < 8; ++it) C = ((V + C) * nmu) >> 32;   // carry bound (fixed point)
+        const uint64_t v = V + C;
+        if (v >= kW) return false;
+        *out = ((v * r32) >> 32) + p;
+        return true;
+    }
+};
+
+}  // namespace
+
+bool pd_lazy_bounds(uint64_t p, uint32_t m, uint32_t L, PdBiases* out) {
+    *out = PdBiases{};
+    if (p < 3 || p >= ((uint64_t)1 << 30) || L < 2 || L > 4) return false;
+    PdCtx c;
+    c.p = p;
+    c.nmu = PdCtx::kW / p;
+    c.r32 = PdCtx::kW % p;
+    uint32_t lg = 0;
+    while ((1u << lg) < m) ++lg;
+    const uint64_t C = p - 1;   // a canonical digit
+    // conversion from L words: sum_j w_j P_j with canonical P_j
+    {
+        u128 carry = 0;
+        for (int k = 0; k < 4; ++k) {
+            const u128 col = (k == 0 ? (u128)(PdCtx::kW - 1) : 0) + (u128)(L - 1) * (PdCtx::kW - 1) * C + carry;
+            if (col >> 64) return false;
+            carry = col / p + 1;
+        }
+    }
+    // forward: inputs canonical or negated (digits <= p), bias K = 1
+    out->kf = 1;
+    uint64_t V = p;
+    for (uint32_t st = 0; st < lg; ++st) {
+        if (!c.mmul_ok(V, C)) return false;
+        V += p;   // lo + t, lo + D - t
+        if (V >= PdCtx::kW) return false;
+        if (st % 2 == 1 || st + 1 == lg) {
+            if (!c.norm(V, &V)) return false;
+        }
+    }
+    // componentwise: by a canonical twiddle, or a by b's canonical evaluations
+    if (!c.mmul_ok(V, C)) return false;
+    // backwards: products canonical, sums normalised after every stage but the last
+    uint64_t U = C;
+    for (uint32_t b = 0; b < lg; ++b) {
+        const uint64_t K = (U + C - 1) / C;   // bias digits K (p - 1) >= U
+        if (K > 255) return false;
+        out->kb[b] = (uint32_t)K;
+        const uint64_t d = U + K * p, s = 2 * U;
+        if (d >= PdCtx::kW || s >= PdCtx::kW || !c.mmul_ok(d, C)) return false;
+        if (b + 1 == lg) {
+            uint64_t tmp;
+            if (!c.mmul_ok(s, C) || !c.norm(s, &tmp)) return false;   // scaled, or made canonical
+        } else {
+            uint64_t sn;
+            if (!c.norm(s, &sn)) return false;
+            U = sn > C ? sn : C;
+        }
+    }
+    out->ok = true;
+    return true;
+}
+
 }  // namespace dkss_planning

@@ -37,4 +37,19 @@ struct NttBiases {
 // limbs of 26 bits stays within every limit above; fills *out.
 bool ntt_lazy_bounds(uint32_t m, uint32_t LR, dkss_host::u128 q, NttBiases* out);
 
+// Bias multiples of the p-adic digit form (padic.cuh): a difference x - y
+// adds K (p, p-1, p-1, p-1), K p^4 = 0 mod p^4, with K (p-1) at least y's
+// digits.  kf: forward stages and negated inputs; kb[b]: backwards stage b.
+struct PdBiases {
+    uint32_t kf = 0;
+    uint32_t kb[7] = {0, 0, 0, 0, 0, 0, 0};
+    bool ok = false;
+};
+
+// true when the p-adic digit form with z = 4 digits (p < 2^30, residues
+// stored in L <= 4 words, transforms of length m) keeps every digit below
+// 2^32 and every product column below 2^64 (pd_lazy_bounds in
+// ntt_bounds.cpp); fills *out.
+bool pd_lazy_bounds(uint64_t p, uint32_t m, uint32_t L, PdBiases* out);
+
 }  // namespace dkss_planning

@@ -33,6 +33,12 @@ struct dkss_plan_s {
     dkss_host::Roots roots;
     bool ntt_ok = false;                  // the lazy NTT form's limits hold for this ring
     dkss_planning::NttBiases ntt_bias{};  // its bias constants
+    // p-adic digit form of the m = 64 NTT kernels (padic.cuh): z = 4, p < 2^30, within
+    // the limits pd_lazy_bounds checks; tables and constants then hold 4 digits per residue
+    bool padic = false;
+    dkss_planning::PdBiases pd_bias{};
+    uint32_t pd_nmu = 0, pd_s = 0;
+    uint64_t pd_mu = 0;
     // device memory owned by the plan
     int device = 0;
     int sm_count = 1;

@@ -53,7 +53,10 @@ def check_product(dk, oc, cfg, A, B, with_oracle=True, with_forward=True, flags=
         # the default runs the evaluation-map form of the R-multiplications on every
         # ring tested here; levels in evaluation coordinates apply for m <= 32
         want = 2 if flags & 2 else 1 if flags & 16 else 3 if (flags & 128 and cfg[2] <= 32) else 0
-        assert plan.info()["rmul"] == want
+        info = plan.info()
+        assert info["rmul"] == want
+        # m = 64 over p^4, p < 2^30: the NTT form computes in p-adic digits unless DKSS_ARITH_MONT
+        assert info["padic"] == int(want == 0 and not flags & 512 and cfg[2] == 64 and cfg[5] == 4 and cfg[4] < 1 << 30)
         c = plan.mul(to_dev(A), to_dev(B))
         fwd = plan.forward(to_dev(A)) if with_forward else None
         plan.sync_status()
@@ -68,9 +71,11 @@ def check_product(dk, oc, cfg, A, B, with_oracle=True, with_forward=True, flags=
 
 
 # alpha-shift inner DFTs with R-multiplications through the evaluation map of
-# R (default), inner levels in evaluation coordinates (DKSS_LEVELS_EVAL), and
-# the direct negacyclic convolution (DKSS_RMUL_DIRECT)
-FORMS = [0, 128, 16]
+# R (default: p-adic digits for m = 64 over p^4), the same with 26-bit-limb
+# Montgomery products (DKSS_ARITH_MONT), inner levels in evaluation
+# coordinates (DKSS_LEVELS_EVAL), and the direct negacyclic convolution
+# (DKSS_RMUL_DIRECT)
+FORMS = [0, 512, 128, 16]
 
 
 @pytest.mark.parametrize("flags", FORMS)

@@ -11,8 +11,8 @@ tensor-core form.
 about half an hour and 32 GiB, so tests/golden/make_large_digests.py ran it
 once and stored SHA-256 digests of its product words and of its a_hat (the
 whole array and 16 equal slices); the GPU's full outputs are hashed the same
-way and must match every digest, in the default, the direct and the INT8
-form.
+way and must match every digest, in the default form (p-adic digits), with
+Montgomery products, the direct and the INT8 form.
 """
 import hashlib
 import os
@@ -30,7 +30,7 @@ import make_large_digests as golden  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-FORM_DEFAULT, FORM_DIRECT, FORM_INT8 = 0, 16, 2
+FORM_DEFAULT, FORM_DIRECT, FORM_INT8, FORM_MONT = 0, 16, 2, 512
 
 
 @pytest.fixture(scope="module")
@@ -67,7 +67,7 @@ def first_mismatch(got, want):
     return None if bad.size == 0 else int(bad[0])
 
 
-@pytest.mark.parametrize("flags", [FORM_DEFAULT, FORM_DIRECT, FORM_INT8])
+@pytest.mark.parametrize("flags", [FORM_DEFAULT, FORM_MONT, FORM_DIRECT, FORM_INT8])
 def test_2p28_bits_exact(dk, c4_oracle, flags):
     cfg, A, B, c_want, ahat_want = c4_oracle
     with dk.Plan(*cfg, flags=flags) as plan:
@@ -106,7 +106,7 @@ def check_digests(got, want, what):
     assert got[0] == whole
 
 
-@pytest.mark.parametrize("flags", [FORM_DEFAULT, FORM_DIRECT, FORM_INT8])
+@pytest.mark.parametrize("flags", [FORM_DEFAULT, FORM_MONT, FORM_DIRECT, FORM_INT8])
 def test_2p32_bits_exact(dk, flags):
     name = "dkss_2p32b"
     want = golden.read_golden(name)
