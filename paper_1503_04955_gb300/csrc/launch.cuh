@@ -35,6 +35,7 @@ static MR make_mr(const dkss_plan_s* pl) {
         MR md;
         md.p = (uint32_t)pl->p;
         md.nmu = pl->pd_nmu;
+        md.nsh = pl->pd_s + 1;
         md.s = pl->pd_s;
         md.mu = pl->pd_mu;
         return md;

@@ -340,7 +340,8 @@ bool ntt_lazy_bounds(uint32_t m, uint32_t LR, u128 q, NttBiases* out) {
 namespace {
 
 struct PdCtx {
-    uint64_t p, nmu, r32;   // floor(2^32 / p), 2^32 mod p
+    uint64_t p, nmu;        // floor(2^32 / p)
+    uint32_t nsh;           // ceil(log2 p)
     static constexpr uint64_t kW = (uint64_t)1 << 32;
 
     // product of digits <= A and <= B: every column (with its carry) below 2^64
@@ -353,15 +354,23 @@ struct PdCtx {
         }
         return true;
     }
-    // pd_norm / pd_canon of digits <= V: every digit plus its carry below 2^32;
-    // the result's digits (pd_norm) are at most *out
+    // pd_norm of digits <= V: every digit plus its carry (at most v >> nsh)
+    // below 2^32; the result's digits are at most *out
     bool norm(uint64_t V, uint64_t* out) const {
         uint64_t C = 0;
-        for (int it = 0; it < 8; ++it) C = ((V + C) * nmu) >> 32;   // carry bound (fixed point)
+        for (int it = 0; it < 8; ++it) C = (V + C) >> nsh;   // carry bound (fixed point)
         const uint64_t v = V + C;
         if (v >= kW) return false;
-        *out = ((v * r32) >> 32) + p;
+        // v - floor(v / 2^nsh) p is largest where floor(v / 2^nsh) is smallest:
+        // below v (1 - p / 2^nsh) + p
+        *out = ((v * (((uint64_t)1 << nsh) - p)) >> nsh) + p;
         return true;
+    }
+    // pd_canon of digits <= V: every digit plus its carry (at most v nmu / 2^32) below 2^32
+    bool canon_ok(uint64_t V) const {
+        uint64_t C = 0;
+        for (int it = 0; it < 8; ++it) C = ((V + C) * nmu) >> 32;
+        return V + C < kW;
     }
 };
 
@@ -373,7 +382,8 @@ bool pd_lazy_bounds(uint64_t p, uint32_t m, uint32_t L, PdBiases* out) {
     PdCtx c;
     c.p = p;
     c.nmu = PdCtx::kW / p;
-    c.r32 = PdCtx::kW % p;
+    c.nsh = 0;
+    while (((uint64_t)1 << c.nsh) < p) ++c.nsh;
     uint32_t lg = 0;
     while ((1u << lg) < m) ++lg;
     const uint64_t C = p - 1;   // a canonical digit
@@ -397,8 +407,8 @@ bool pd_lazy_bounds(uint64_t p, uint32_t m, uint32_t L, PdBiases* out) {
             if (!c.norm(V, &V)) return false;
         }
     }
-    // componentwise: by a canonical twiddle, or a by b's canonical evaluations
-    if (!c.mmul_ok(V, C)) return false;
+    // componentwise: by a canonical twiddle, or a by b's evaluations made canonical
+    if (!c.mmul_ok(V, C) || !c.canon_ok(V)) return false;
     // backwards: products canonical, sums normalised after every stage but the last
     uint64_t U = C;
     for (uint32_t b = 0; b < lg; ++b) {
@@ -408,8 +418,7 @@ bool pd_lazy_bounds(uint64_t p, uint32_t m, uint32_t L, PdBiases* out) {
         const uint64_t d = U + K * p, s = 2 * U;
         if (d >= PdCtx::kW || s >= PdCtx::kW || !c.mmul_ok(d, C)) return false;
         if (b + 1 == lg) {
-            uint64_t tmp;
-            if (!c.mmul_ok(s, C) || !c.norm(s, &tmp)) return false;   // scaled, or made canonical
+            if (!c.mmul_ok(s, C) || !c.canon_ok(s)) return false;   // scaled, or made canonical
         } else {
             uint64_t sn;
             if (!c.norm(s, &sn)) return false;

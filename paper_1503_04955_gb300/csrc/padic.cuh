@@ -32,7 +32,8 @@ constexpr int kPdDigits = 4;   // z of the rings that take this form
 template <int Z>
 struct ModPD {
     uint32_t p;
-    uint32_t nmu;   // floor(2^32 / p): quotient estimates of single digits
+    uint32_t nmu;   // floor(2^32 / p): quotient estimates of single digits (pd_canon)
+    uint32_t nsh;   // ceil(log2 p): quotient estimates of lazy digits (pd_norm)
     uint32_t s;     // floor(log2 p)
     uint64_t mu;    // floor(2^(64 + s) / p): quotient estimates of columns
 };
@@ -85,16 +86,16 @@ DKSS_HD void mmul(uint32_t (&r)[Z], const uint32_t (&a)[Z], const uint32_t (&b)[
 }
 
 // Lazy normalisation: digit v = x_k + carry becomes v - k p with
-// k = floor(v floor(2^32/p) / 2^32) <= v / p, so below (2^32 mod p) + p < 2p;
-// k moves to the next digit, the top digit's is dropped (a multiple of p^Z).
-// Every x_k + carry must stay below 2^32.
+// k = floor(v / 2^ceil(log2 p)) <= v / p (a shift), so below
+// v (1 - p / 2^ceil(log2 p)) + p; k moves to the next digit, the top digit's
+// is dropped (a multiple of p^Z).  Every x_k + carry must stay below 2^32.
 template <int Z>
 DKSS_HD void pd_norm(uint32_t (&x)[Z], const ModPD<Z>& md) {
     uint32_t cin = 0;
 #pragma unroll
     for (int k = 0; k < Z; ++k) {
         const uint32_t v = x[k] + cin;
-        const uint32_t kq = mulhi32(v, md.nmu);
+        const uint32_t kq = v >> md.nsh;
         x[k] = v - kq * md.p;
         cin = kq;
     }

@@ -25,6 +25,7 @@ static ModPD<4> make(uint64_t p) {
     uint32_t s = 0;
     while ((p >> (s + 1)) != 0) ++s;
     md.s = s;
+    md.nsh = s + 1;   // p is odd: ceil(log2 p) = floor(log2 p) + 1
     md.mu = (uint64_t)((((unsigned __int128)1) << (64 + s)) / p);
     return md;
 }

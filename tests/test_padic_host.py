@@ -5,9 +5,9 @@ integers.
 
 A residue mod p^4 is four base-p digits x = sum_k x_k p^k; digits may exceed
 p (lazy).  mmul returns the canonical digits of a b mod p^4, pd_canon those of
-x mod p^4, pd_norm digits of a congruent value each below 2p, pd_from_words
-the digits of a value given as 32-bit words, pd_to_words the words of a value
-given as canonical digits.  The primes are those of the 2^28- and 2^32-bit
+x mod p^4, pd_norm digits of a congruent value near p (quotients by a shift),
+pd_from_words the digits of a value given as 32-bit words, pd_to_words the
+words of a value given as canonical digits.  The primes are those of the 2^28- and 2^32-bit
 workloads, one just below 2^30 and a small one.
 """
 import os
@@ -87,7 +87,10 @@ def test_norm_and_canon(driver):
         nrm, can = got[2 * i], got[2 * i + 1]
         q = p ** 4
         assert value(p, nrm) % q == value(p, x) % q
-        assert all(d < 2 * p for d in nrm)
+        # pd_norm's quotient is v >> ceil(log2 p): a digit v becomes below v (1 - p / 2^sh) + p
+        sh = p.bit_length()
+        vmax = max(x) + (max(x) >> sh) + 1
+        assert all(d < vmax * ((1 << sh) - p) // (1 << sh) + p + 1 for d in nrm)
         assert can == digits(p, value(p, x) % q)
 
 
