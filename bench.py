@@ -487,7 +487,7 @@ def run_ours(args):
                              "bits_per_operand_bit": round(8 * info["dev_bytes"] / n_bits, 2)},
             "gpu_launches": launches,
             "e2e": {"value": round(e2e_value, 4), "unit": "Gbit/s", "h2d_bytes_per_step": 2 * A.nbytes,
-                    "d2h_bytes_per_step": 4 * A.nbytes, "steps": e2e_steps},
+                    "d2h_bytes_per_step": 2 * A.nbytes, "steps": e2e_steps},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "forms": forms,

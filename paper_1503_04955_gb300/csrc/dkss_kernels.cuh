@@ -627,10 +627,9 @@ __device__ __forceinline__ void twiddle_pd_group(const LevelParams& prm, const M
     uint32_t* buf = xbuf + tm.id * m * Z;
     const int lane = tm.lane;
     const uint32_t* cst = prm.ntt_cst;
-    uint32_t bn[Z], pw[4 * Z];
+    uint32_t bn[Z];
     ldg_rr<Z>(bn, cst + NttLayout<m>::BN * Z);
-#pragma unroll
-    for (int i = 0; i < 4 * Z; ++i) pw[i] = __ldg(cst + PdLayout<m>::POW32 * Z + i);
+    const uint32_t* pw = cst + PdLayout<m>::POW32 * Z;
     uint32_t vv[4][Z];
 #pragma unroll
     for (int j = 0; j < 4; ++j) load_shifted_pd<m, L, Z>(vv[j], x, lane + j * NT::TEAM, r, bn, pw, md);
@@ -876,9 +875,7 @@ __device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>
         const int lane = nt.lane;
         uint32_t* park = buf + m * LR + nt.lane * LR;
         const uint32_t* cst = prm.ntt_cst;
-        uint32_t pw[4 * LR];
-#pragma unroll
-        for (int i = 0; i < 4 * LR; ++i) pw[i] = __ldg(cst + PdLayout<m>::POW32 * LR + i);
+        const uint32_t* pw = cst + PdLayout<m>::POW32 * LR;
 #pragma unroll 1
         for (int v = nt.id; v < nn; v += NT::NTEAMS) {
             uint32_t x[4][LR], w[L];
@@ -1123,6 +1120,33 @@ __device__ __forceinline__ void copy_words_block(uint32_t* dst, const uint32_t* 
         *reinterpret_cast<uint4*>(dst + i) = *reinterpret_cast<const uint4*>(src + i);
 }
 
+// Asynchronous 16-byte copies global -> shared (cp.async, L2 only): a thread
+// issues all of its copies before it waits, so many loads are in flight
+// without staging registers.
+__device__ __forceinline__ void cp_async16(uint32_t* smem_dst, const uint32_t* gsrc) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// n elements of EW words (a multiple of 4; 16-byte aligned in global and
+// shared memory): element i from src(i) to dst + slot(i) * ES, in 16-byte
+// pieces spread over the CTA; the caller synchronises the CTA afterwards.
+template <int m, int L, class Src, class Slot>
+__device__ __forceinline__ void cp_async_elements(uint32_t* dst, int n, Src src, Slot slot) {
+    using G = Geo<m, L>;
+    static_assert(G::EW % 4 == 0 && G::ES % 4 == 0, "elements move in 16-byte pieces");
+    constexpr int PIECES = G::EW / 4;
+    for (int idx = threadIdx.x; idx < n * PIECES; idx += kThreads) {
+        const int i = idx / PIECES, pc = idx % PIECES;
+        cp_async16(dst + slot(i) * G::ES + 4 * pc, src(i) + 4 * pc);
+    }
+    cp_async_wait_all();
+}
+
 // Elements j = 2i + parity (i < m) of the column into slot bitrev(i) (log2 m bits).
 template <int m, int L, bool FIRST>
 __device__ __forceinline__ void half_load_fwd(const LevelParams& prm, uint32_t* half, uint64_t base, uint64_t l,
@@ -1132,6 +1156,12 @@ __device__ __forceinline__ void half_load_fwd(const LevelParams& prm, uint32_t* 
     const uint32_t* poly = prm.data + (op ? prm.poly_words : 0);
     const uint64_t* raw = op ? prm.raw_b : prm.raw_a;
     const int h = m / 2;
+    if constexpr (!FIRST) {
+        cp_async_elements<m, L>(
+            half, m, [&](int i) { return poly + (base + (2 * (uint64_t)i + parity) * mu_d + l) * G::EW; },
+            [&](int i) { return bitrev(i, LOG2_M); });
+        return;
+    }
     for (int idx = threadIdx.x; idx < m * m; idx += kThreads) {
         const int i = idx / m, t = idx % m;
         const uint64_t j = 2 * (uint64_t)i + parity;
@@ -1251,7 +1281,8 @@ __global__ void __launch_bounds__(kThreads) k_dft_inv_half(LevelParams prm, Mod<
         }
         __syncthreads();
         // odd outputs X_(2v+1)
-        copy_words_block<m, L>(smem, D, m * G::EW);
+        cp_async_elements<m, L>(
+            smem, m, [&](int i) { return D + (uint64_t)i * G::EW; }, [](int i) { return i; });
         __syncthreads();
         dft_dif<m, L>(smem, 1, m, SUB_ROOT, md);
         for (int idx = threadIdx.x; idx < m * m; idx += kThreads) {

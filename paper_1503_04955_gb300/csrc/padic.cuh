@@ -55,6 +55,15 @@ DKSS_HD uint32_t mulhi32(uint32_t a, uint32_t b) {
 #endif
 }
 
+// A constant of the plan's table: read-only cache on the device.
+DKSS_HD uint32_t ld_const(const uint32_t* p) {
+#ifdef __CUDA_ARCH__
+    return __ldg(p);
+#else
+    return *p;
+#endif
+}
+
 // Carry chain of the columns c_0 .. c_{Z-1} (each below 2^64 with the carry
 // it receives): canonical digits of sum_k c_k p^k mod p^Z.
 template <int Z>
@@ -131,7 +140,7 @@ DKSS_HD void pd_from_words(uint32_t (&r)[Z], const uint32_t (&w)[L], const uint3
 #pragma unroll
     for (int j = 1; j < L; ++j)
 #pragma unroll
-        for (int k = 0; k < Z; ++k) c[k] += (uint64_t)w[j] * pw[j * Z + k];
+        for (int k = 0; k < Z; ++k) c[k] += (uint64_t)w[j] * ld_const(pw + j * Z + k);
     pd_carry<Z>(r, c, md);
 }
 
