@@ -795,6 +795,9 @@ dkss_status finish_plan(dkss_plan_s* pl, dkss_status s, dkss_plan_t* plan) {
         pl->pd_s = s;
         pl->pd_nmu = (uint32_t)(((uint64_t)1 << 32) / p);
         pl->pd_mu = (uint64_t)((((u128)1) << (64 + s)) / p);
+        pl->pd_fast = pl->pd_bias.fast;
+        pl->pd_mu_lo = (uint32_t)((((u128)1) << 64) / p);
+        while ((1u << (pl->pd_lg_nmu + 1)) <= pl->pd_nmu) ++pl->pd_lg_nmu;
     }
     if (cudaGetDevice(&pl->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&pl->sm_count, cudaDevAttrMultiProcessorCount, pl->device) != cudaSuccess) {

@@ -581,9 +581,9 @@ __device__ __forceinline__ void twiddle_ntt_group(const LevelParams& prm, const 
 // Coefficient t of alpha^r x in p-adic digits (padic.cuh): x's residue
 // converted from its L words (pw: digits of 2^(32j) mod p^z), a negated one
 // as the bias bn - y (bn = (p, p-1, ..., p-1), y canonical).
-template <int m, int L, int Z>
+template <int m, int L, int Z, bool F>
 __device__ __forceinline__ void load_shifted_pd(uint32_t (&out)[Z], const uint32_t* x, int t, int r,
-                                                const uint32_t (&bn)[Z], const uint32_t* pw, const ModPD<Z>& md) {
+                                                const uint32_t (&bn)[Z], const uint32_t* pw, const ModPD<Z, F>& md) {
     int src = t - r;
     bool neg = false;
     if (src < 0) {
@@ -604,8 +604,8 @@ __device__ __forceinline__ void load_shifted_pd(uint32_t (&out)[Z], const uint32
 // The bad multiplications of twiddle_ntt_group with the transform in R in
 // p-adic digits: the element's residues are converted on load and back on
 // store, the twiddle table and the transform constants hold digits.
-template <int m, int L, bool INV, int Z>
-__device__ __forceinline__ void twiddle_pd_group(const LevelParams& prm, const ModPD<Z>& md, uint64_t group, int op,
+template <int m, int L, bool INV, int Z, bool F>
+__device__ __forceinline__ void twiddle_pd_group(const LevelParams& prm, const ModPD<Z, F>& md, uint64_t group, int op,
                                                  uint32_t* xbuf) {
     using G = Geo<m, L>;
     using NT = NttTeam<m>;

@@ -36,6 +36,8 @@ static MR make_mr(const dkss_plan_s* pl) {
         md.p = (uint32_t)pl->p;
         md.nmu = pl->pd_nmu;
         md.nsh = pl->pd_s + 1;
+        md.mu_lo = pl->pd_mu_lo;
+        md.lg_nmu = pl->pd_lg_nmu;
         md.s = pl->pd_s;
         md.mu = pl->pd_mu;
         return md;
@@ -261,19 +263,21 @@ dkss_status prepare(dkss_plan_s* pl) {
     }
     if constexpr (m == 64) {
         if (pl->padic) {
-            using PD = ModPD<kPdDigits>;
             constexpr int Z = kPdDigits;
             const int twp = (int)twiddle_ntt_smem_bytes<m, L, Z>();
             const int finp = (int)std::min<size_t>(final_smem_bytes<m, L, Z>(G::TWO_M, kFormNtt), (size_t)optin);
             if ((int)final_smem_bytes<m, L, Z>((int)pl->r_last, kFormNtt) > optin || twp > optin)
                 return DKSS_EUNSUPPORTED;
-            if (cudaFuncSetAttribute(k_twiddle_ntt<m, L, Z, false, PD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     twp) ||
-                cudaFuncSetAttribute(k_twiddle_ntt<m, L, Z, true, PD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     twp) ||
-                cudaFuncSetAttribute(k_final_pointwise<m, L, Z, kFormNtt, PD>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, finp))
-                return DKSS_ECUDA;
+            auto set = [&](auto pd) {
+                using PD = decltype(pd);
+                return cudaFuncSetAttribute(k_twiddle_ntt<m, L, Z, false, PD>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, twp) ||
+                       cudaFuncSetAttribute(k_twiddle_ntt<m, L, Z, true, PD>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, twp) ||
+                       cudaFuncSetAttribute(k_final_pointwise<m, L, Z, kFormNtt, PD>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, finp);
+            };
+            if (pl->pd_fast ? set(ModPD<Z, true>{}) : set(ModPD<Z, false>{})) return DKSS_ECUDA;
         }
     }
     if constexpr (m <= 32) {
@@ -544,6 +548,7 @@ dkss_status run_mul(dkss_plan_s* pl, const uint64_t* a, const uint64_t* b, uint6
         }
     }
     if constexpr (m == 64) {
+        if (pl->padic && pl->pd_fast) return run_mul_coef<m, L, kPdDigits, ModPD<kPdDigits, true>>(pl, a, b, out, st);
         if (pl->padic) return run_mul_coef<m, L, kPdDigits, ModPD<kPdDigits>>(pl, a, b, out, st);
     }
     if constexpr (LR >= 3) {
@@ -562,7 +567,8 @@ dkss_status run_forward(dkss_plan_s* pl, const uint64_t* a, uint64_t* out, cudaS
     if (pl->d_table_minv) lp.table_eval = pl->d_table_minv;   // coefficient levels for a plan in evaluation coordinates
     dkss_status s = DKSS_OK;
     if constexpr (m == 64) {
-        if (pl->padic) s = launch_forward_levels<m, L, kPdDigits, ModPD<kPdDigits>>(pl, lp, 1, st);
+        if (pl->padic && pl->pd_fast) s = launch_forward_levels<m, L, kPdDigits, ModPD<kPdDigits, true>>(pl, lp, 1, st);
+        else if (pl->padic) s = launch_forward_levels<m, L, kPdDigits, ModPD<kPdDigits>>(pl, lp, 1, st);
         else s = launch_forward_levels<m, L, LR>(pl, lp, 1, st);
     } else {
         s = launch_forward_levels<m, L, LR>(pl, lp, 1, st);

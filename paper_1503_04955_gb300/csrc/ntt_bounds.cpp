@@ -342,14 +342,22 @@ namespace {
 struct PdCtx {
     uint64_t p, nmu;        // floor(2^32 / p)
     uint32_t nsh;           // ceil(log2 p)
+    bool fast = false;      // fast carries (padic.cuh, ModPD<Z, true>)
+    uint64_t mu_lo = 0;     // floor(2^64 / p) mod 2^32
     static constexpr uint64_t kW = (uint64_t)1 << 32;
 
-    // product of digits <= A and <= B: every column (with its carry) below 2^64
+    // a column below 2^64; with fast carries also c1 mu_lo + c0 nmu + 2^32 < 2^64
+    bool col_ok(u128 col) const {
+        if (col >> 64) return false;
+        if (fast && (u128)(uint64_t)(col >> 32) * mu_lo + (u128)(kW - 1) * nmu + kW >= ((u128)1 << 64)) return false;
+        return true;
+    }
+    // product of digits <= A and <= B: every column (with its carry) within col_ok
     bool mmul_ok(uint64_t A, uint64_t B) const {
         u128 carry = 0;
         for (int k = 0; k < 4; ++k) {
             const u128 col = (u128)(k + 1) * A * B + carry;
-            if (col >> 64) return false;
+            if (!col_ok(col)) return false;
             carry = col / p + 1;
         }
         return true;
@@ -376,6 +384,12 @@ struct PdCtx {
 
 }  // namespace
 
+namespace {
+
+bool pd_schedule(const PdCtx& c, uint32_t m, uint32_t L, PdBiases* out);
+
+}  // namespace
+
 bool pd_lazy_bounds(uint64_t p, uint32_t m, uint32_t L, PdBiases* out) {
     *out = PdBiases{};
     if (p < 3 || p >= ((uint64_t)1 << 30) || L < 2 || L > 4) return false;
@@ -384,6 +398,23 @@ bool pd_lazy_bounds(uint64_t p, uint32_t m, uint32_t L, PdBiases* out) {
     c.nmu = PdCtx::kW / p;
     c.nsh = 0;
     while (((uint64_t)1 << c.nsh) < p) ++c.nsh;
+    if (!pd_schedule(c, m, L, out)) return false;
+    // fast carries when floor(2^32 / p) is a power of two and the columns allow them
+    if ((c.nmu & (c.nmu - 1)) == 0) {
+        PdCtx f = c;
+        f.fast = true;
+        f.mu_lo = (uint64_t)((((u128)1) << 64) / p) & (PdCtx::kW - 1);
+        PdBiases tmp;
+        out->fast = pd_schedule(f, m, L, &tmp);
+    }
+    out->ok = true;
+    return true;
+}
+
+namespace {
+
+bool pd_schedule(const PdCtx& c, uint32_t m, uint32_t L, PdBiases* out) {
+    const uint64_t p = c.p;
     uint32_t lg = 0;
     while ((1u << lg) < m) ++lg;
     const uint64_t C = p - 1;   // a canonical digit
@@ -392,7 +423,7 @@ bool pd_lazy_bounds(uint64_t p, uint32_t m, uint32_t L, PdBiases* out) {
         u128 carry = 0;
         for (int k = 0; k < 4; ++k) {
             const u128 col = (k == 0 ? (u128)(PdCtx::kW - 1) : 0) + (u128)(L - 1) * (PdCtx::kW - 1) * C + carry;
-            if (col >> 64) return false;
+            if (!c.col_ok(col)) return false;
             carry = col / p + 1;
         }
     }
@@ -425,8 +456,9 @@ bool pd_lazy_bounds(uint64_t p, uint32_t m, uint32_t L, PdBiases* out) {
             U = sn > C ? sn : C;
         }
     }
-    out->ok = true;
     return true;
 }
+
+}  // namespace
 
 }  // namespace dkss_planning

@@ -44,6 +44,7 @@ struct PdBiases {
     uint32_t kf = 0;
     uint32_t kb[7] = {0, 0, 0, 0, 0, 0, 0};
     bool ok = false;
+    bool fast = false;   // the fast carries of ModPD<Z, true> stay within their limits too
 };
 
 // true when the p-adic digit form with z = 4 digits (p < 2^30, residues

@@ -29,21 +29,27 @@ namespace dkss {
 
 constexpr int kPdDigits = 4;   // z of the rings that take this form
 
-template <int Z>
+// F (fast carries): floor(2^32 / p) is a power of two, 2^e; then the
+// reciprocal floor(2^64 / p) is 2^e 2^32 + mu_lo and a column's quotient
+// takes one wide product and one multiply-high instead of the high half of
+// a 64 x 64-bit product (pd_carry).
+template <int Z, bool F = false>
 struct ModPD {
     uint32_t p;
-    uint32_t nmu;   // floor(2^32 / p): quotient estimates of single digits (pd_canon)
-    uint32_t nsh;   // ceil(log2 p): quotient estimates of lazy digits (pd_norm)
-    uint32_t s;     // floor(log2 p)
-    uint64_t mu;    // floor(2^(64 + s) / p): quotient estimates of columns
+    uint32_t nmu;     // floor(2^32 / p): quotient estimates of single digits (pd_canon)
+    uint32_t nsh;     // ceil(log2 p): quotient estimates of lazy digits (pd_norm)
+    uint32_t s;       // floor(log2 p)
+    uint64_t mu;      // floor(2^(64 + s) / p): quotient estimates of columns
+    uint32_t mu_lo;   // floor(2^64 / p) mod 2^32 (F)
+    uint32_t lg_nmu;  // log2 floor(2^32 / p) (F)
 };
 
 template <class MR>
 struct IsPD {
     static constexpr bool value = false;
 };
-template <int Z>
-struct IsPD<ModPD<Z>> {
+template <int Z, bool F>
+struct IsPD<ModPD<Z, F>> {
     static constexpr bool value = true;
 };
 
@@ -66,11 +72,21 @@ DKSS_HD uint32_t ld_const(const uint32_t* p) {
 
 // Carry chain of the columns c_0 .. c_{Z-1} (each below 2^64 with the carry
 // it receives): canonical digits of sum_k c_k p^k mod p^Z.
-template <int Z>
-DKSS_HD void pd_carry(uint32_t (&r)[Z], uint64_t (&c)[Z], const ModPD<Z>& md) {
+template <int Z, bool F>
+DKSS_HD void pd_carry(uint32_t (&r)[Z], uint64_t (&c)[Z], const ModPD<Z, F>& md) {
 #pragma unroll
     for (int k = 0; k < Z; ++k) {
-        uint64_t q = mulhi64(c[k], md.mu) >> md.s;   // floor(c / p) or one less
+        uint64_t q;   // floor(c / p) or one less
+        if constexpr (F) {
+            // floor(c (2^e 2^32 + mu_lo) / 2^64) from c = c1 2^32 + c0: the
+            // integer part of (c1 mu_lo + c0 2^e + hi(c0 mu_lo)) / 2^32 plus
+            // c1 2^e (the plan's check keeps the sum below 2^64)
+            const uint32_t c0 = (uint32_t)c[k], c1 = (uint32_t)(c[k] >> 32);
+            const uint64_t t = (uint64_t)c1 * md.mu_lo + ((uint64_t)c0 << md.lg_nmu) + mulhi32(c0, md.mu_lo);
+            q = ((uint64_t)c1 << md.lg_nmu) + (t >> 32);
+        } else {
+            q = mulhi64(c[k], md.mu) >> md.s;
+        }
         uint32_t d = (uint32_t)c[k] - (uint32_t)q * md.p;
         if (d >= md.p) {
             d -= md.p;
@@ -82,8 +98,8 @@ DKSS_HD void pd_carry(uint32_t (&r)[Z], uint64_t (&c)[Z], const ModPD<Z>& md) {
 }
 
 // r = a b mod p^Z, canonical digits
-template <int Z>
-DKSS_HD void mmul(uint32_t (&r)[Z], const uint32_t (&a)[Z], const uint32_t (&b)[Z], const ModPD<Z>& md) {
+template <int Z, bool F>
+DKSS_HD void mmul(uint32_t (&r)[Z], const uint32_t (&a)[Z], const uint32_t (&b)[Z], const ModPD<Z, F>& md) {
     uint64_t c[Z];
 #pragma unroll
     for (int k = 0; k < Z; ++k) c[k] = 0;
@@ -98,8 +114,8 @@ DKSS_HD void mmul(uint32_t (&r)[Z], const uint32_t (&a)[Z], const uint32_t (&b)[
 // k = floor(v / 2^ceil(log2 p)) <= v / p (a shift), so below
 // v (1 - p / 2^ceil(log2 p)) + p; k moves to the next digit, the top digit's
 // is dropped (a multiple of p^Z).  Every x_k + carry must stay below 2^32.
-template <int Z>
-DKSS_HD void pd_norm(uint32_t (&x)[Z], const ModPD<Z>& md) {
+template <int Z, bool F>
+DKSS_HD void pd_norm(uint32_t (&x)[Z], const ModPD<Z, F>& md) {
     uint32_t cin = 0;
 #pragma unroll
     for (int k = 0; k < Z; ++k) {
@@ -111,8 +127,8 @@ DKSS_HD void pd_norm(uint32_t (&x)[Z], const ModPD<Z>& md) {
 }
 
 // Canonical digits (each below p) of a lazy value, same limits as pd_norm.
-template <int Z>
-DKSS_HD void pd_canon(uint32_t (&r)[Z], const uint32_t (&x)[Z], const ModPD<Z>& md) {
+template <int Z, bool F>
+DKSS_HD void pd_canon(uint32_t (&r)[Z], const uint32_t (&x)[Z], const ModPD<Z, F>& md) {
     uint32_t cin = 0;
 #pragma unroll
     for (int k = 0; k < Z; ++k) {
@@ -132,8 +148,8 @@ DKSS_HD void pd_canon(uint32_t (&r)[Z], const uint32_t (&x)[Z], const ModPD<Z>& 
 // w = sum_j w_j 2^(32j) = sum_j w_j P_j (mod p^Z) with P_j the canonical
 // digits of 2^(32j) mod p^Z (pw[j * Z + k], from the plan), then one carry
 // chain.  Columns stay below L 2^32 p + carry < 2^64 for L <= 4, p < 2^30.
-template <int L, int Z>
-DKSS_HD void pd_from_words(uint32_t (&r)[Z], const uint32_t (&w)[L], const uint32_t* pw, const ModPD<Z>& md) {
+template <int L, int Z, bool F>
+DKSS_HD void pd_from_words(uint32_t (&r)[Z], const uint32_t (&w)[L], const uint32_t* pw, const ModPD<Z, F>& md) {
     uint64_t c[Z];
 #pragma unroll
     for (int k = 0; k < Z; ++k) c[k] = k == 0 ? w[0] : 0;
@@ -146,8 +162,8 @@ DKSS_HD void pd_from_words(uint32_t (&r)[Z], const uint32_t (&w)[L], const uint3
 
 // 32-bit words of a residue from its canonical digits (Horner's rule from
 // the top digit): the canonical value below p^Z < 2^(32L).
-template <int L, int Z>
-DKSS_HD void pd_to_words(uint32_t (&w)[L], const uint32_t (&d)[Z], const ModPD<Z>& md) {
+template <int L, int Z, bool F>
+DKSS_HD void pd_to_words(uint32_t (&w)[L], const uint32_t (&d)[Z], const ModPD<Z, F>& md) {
 #pragma unroll
     for (int j = 0; j < L; ++j) w[j] = j == 0 ? d[Z - 1] : 0u;
 #pragma unroll
@@ -179,9 +195,9 @@ struct PdLayout {
 // Forward negacyclic transform (as ntt_forward): digits grow by at most p
 // per stage (t is canonical, the bias digits are at most p), and both
 // outputs are normalised after every second stage and after the last.
-template <int m, int Z>
+template <int m, int Z, bool F>
 __device__ __forceinline__ void ntt_forward_pd(uint32_t (&v)[4][Z], uint32_t* buf, int lane, unsigned mask,
-                                               const uint32_t* cst, const ModPD<Z>& md) {
+                                               const uint32_t* cst, const ModPD<Z, F>& md) {
     using NL = NttLayout<m>;
     constexpr int LG = NL::LG;
     uint32_t bf[Z];
@@ -217,9 +233,9 @@ __device__ __forceinline__ void ntt_forward_pd(uint32_t (&v)[4][Z], uint32_t* bu
 // difference takes the stage's bias.  The last stage multiplies by cst[lo_c]
 // and cst[hi_c] (plain residues), or with RAW_LO leaves slots 0 and 1 as the
 // sums (the caller makes them canonical with pd_canon).
-template <int m, int Z, bool RAW_LO = false>
+template <int m, int Z, bool RAW_LO = false, bool F = false>
 __device__ __forceinline__ void ntt_backward_pd(uint32_t (&v)[4][Z], uint32_t* buf, int lane, unsigned mask,
-                                                const uint32_t* cst, int lo_c, int hi_c, const ModPD<Z>& md) {
+                                                const uint32_t* cst, int lo_c, int hi_c, const ModPD<Z, F>& md) {
     using NL = NttLayout<m>;
     constexpr int LG = NL::LG;
     int h = 1;

@@ -39,6 +39,8 @@ struct dkss_plan_s {
     dkss_planning::PdBiases pd_bias{};
     uint32_t pd_nmu = 0, pd_s = 0;
     uint64_t pd_mu = 0;
+    bool pd_fast = false;         // fast carries (floor(2^32/p) a power of two; padic.cuh)
+    uint32_t pd_mu_lo = 0, pd_lg_nmu = 0;
     // device memory owned by the plan
     int device = 0;
     int sm_count = 1;

@@ -2,11 +2,12 @@
 // check (csrc/ntt_bounds.cpp, pd_lazy_bounds), read by tests/test_padic_host.py.
 // One request per input line, one answer line each:
 //   mul p a0..a3 b0..b3          -> canonical digits of a b mod p^4
+//   mulf p a0..a3 b0..b3         -> the same with fast carries (floor(2^32/p) = 2^e)
 //   norm p x0..x3                -> pd_norm's digits
 //   canon p x0..x3               -> pd_canon's digits
 //   from p L w0..w(L-1) P0..P15  -> pd_from_words (P: digits of 2^(32j) mod p^4)
 //   to p L d0..d3                -> pd_to_words's L words
-//   bounds p m L                 -> ok kf kb0..kb6
+//   bounds p m L                 -> ok kf kb0..kb6 fast
 #include <cstdio>
 #include <cstring>
 #include <iostream>
@@ -18,8 +19,9 @@
 
 using namespace dkss;
 
-static ModPD<4> make(uint64_t p) {
-    ModPD<4> md;
+template <bool F = false>
+static ModPD<4, F> make(uint64_t p) {
+    ModPD<4, F> md;
     md.p = (uint32_t)p;
     md.nmu = (uint32_t)(((uint64_t)1 << 32) / p);
     uint32_t s = 0;
@@ -27,6 +29,9 @@ static ModPD<4> make(uint64_t p) {
     md.s = s;
     md.nsh = s + 1;   // p is odd: ceil(log2 p) = floor(log2 p) + 1
     md.mu = (uint64_t)((((unsigned __int128)1) << (64 + s)) / p);
+    md.mu_lo = (uint32_t)((((unsigned __int128)1) << 64) / p);
+    md.lg_nmu = 0;
+    while ((1u << (md.lg_nmu + 1)) <= md.nmu) ++md.lg_nmu;
     return md;
 }
 
@@ -57,10 +62,11 @@ int main() {
         if (!(in >> op >> p)) continue;
         const ModPD<4> md = make(p);
         uint32_t a[4], b[4], r[4];
-        if (op == "mul") {
+        if (op == "mul" || op == "mulf") {
             for (auto& v : a) in >> v;
             for (auto& v : b) in >> v;
-            mmul<4>(r, a, b, md);
+            if (op == "mul") mmul<4>(r, a, b, md);
+            else mmul<4>(r, a, b, make<true>(p));   // fast carries: floor(2^32/p) a power of two
             printf("%u %u %u %u\n", r[0], r[1], r[2], r[3]);
         } else if (op == "norm" || op == "canon") {
             for (auto& v : a) in >> v;
@@ -90,7 +96,7 @@ int main() {
             const bool ok = dkss_planning::pd_lazy_bounds(p, m, L, &bi);
             printf("%d %u", ok ? 1 : 0, bi.kf);
             for (int i = 0; i < 7; ++i) printf(" %u", bi.kb[i]);
-            printf("\n");
+            printf(" %d\n", bi.fast ? 1 : 0);
         } else {
             printf("?\n");
         }

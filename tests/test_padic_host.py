@@ -71,6 +71,23 @@ def test_product_is_canonical_and_exact(driver):
     assert call(driver, lines) == want
 
 
+def test_fast_carries(driver):
+    """floor(2^32/p) = 4 for the 2^32-bit workload's prime and one just below
+    2^30: the carries take floor(2^64/p) as 4 2^32 + mu_lo; the product must be
+    the same within the limit check's columns (a lazy below 4.3p, b canonical)."""
+    rng = random.Random(10)
+    lines, want = [], []
+    for p in (998244353, 1073479681):
+        assert (1 << 32) // p == 4
+        q = p ** 4
+        cases = [([0] * 4, [0] * 4), ([p - 1] * 4, [p - 1] * 4), ([W - 1] * 4, [p - 1] * 4)]
+        cases += [([rng.randrange(W) for _ in range(4)], digits(p, rng.randrange(q))) for _ in range(200)]
+        for a, b in cases:
+            lines.append("mulf %d %s %s" % (p, " ".join(map(str, a)), " ".join(map(str, b))))
+            want.append(digits(p, value(p, a) * value(p, b) % q))
+    assert call(driver, lines) == want
+
+
 def test_norm_and_canon(driver):
     rng = random.Random(8)
     lines, kinds = [], []
@@ -121,3 +138,5 @@ def test_limits(driver):
     for g in got[:3]:
         kf, kb = g[1], g[2:8]
         assert kf == 1 and all(1 <= k <= 255 for k in kb)
+    # fast carries: floor(2^32/p) = 4 for p = 998244353 and 1073479681, 585 for 7340033
+    assert got[0][9] == 1 and got[2][9] == 1 and got[1][9] == 0
