@@ -60,9 +60,11 @@ enum {
     DKSS_RMUL_DIRECT = 16, /* R-multiplications by the direct negacyclic convolution
                               (Section 2.9.2) instead of through the evaluation map of R */
     DKSS_ARITH_MONT = 512, /* NTT form with m = 64 over p^4, p < 2^30: keep the 26-bit-limb Montgomery
-                              products instead of the default p-adic digits (each residue as
-                              four base-p digits, a product as ten digit products and a carry
-                              chain; Section 3.2.2's ring Z/p^zZ, no change of the transform) */
+                              products instead of p-adic digits (each residue as four base-p
+                              digits, a product as ten digit products and a carry chain;
+                              Section 3.2.2's ring Z/p^zZ, no change of the transform).  Without
+                              the flag the library takes the digits where they need fewer
+                              multiply-adds: floor(2^32/p) a power of two, or five 26-bit limbs */
     DKSS_LEVELS_EVAL = 128 /* every radix-2m level but the first, and the last level, in the
                               evaluation coordinates of R (the CRT map of Section 3.2.3):
                               their inner DFTs become m independent DFTs over Z/p^zZ with

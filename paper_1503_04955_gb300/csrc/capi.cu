@@ -174,7 +174,6 @@ bool proth_ring_lr(uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, uint32_t
 // (Section 3.2.3) and the constants of the lazy arithmetic.
 static dkss_status plan_ring(dkss_plan_s* pl, uint64_t n_bits, uint64_t M, uint32_t m, uint32_t u, u128 p, uint32_t z,
                              u128 q, uint64_t zeta, u128 zeta_z) {
-    const uint64_t h = m / 2;
     const uint64_t P2 = 2 * M;
     if ((u128)m * q >= ((u128)1 << 127)) return DKSS_EUNSUPPORTED;  // host sums of m products; 4 m q < 2^130
     // limbs: one spare bit for sums, and m q^2 + R q < 2^(64L) for the REDC of m-term sums
@@ -784,10 +783,21 @@ dkss_status finish_plan(dkss_plan_s* pl, dkss_status s, dkss_plan_t* plan) {
     if (!pl->ntt_ok && !(flags & (DKSS_RMUL_DIRECT | DKSS_FORM_INT8TC))) pl->flags |= DKSS_RMUL_DIRECT;
     // inner levels in evaluation coordinates: the NTT form, m <= 32, within their limits
     pl->eval_levels = pl->eval_levels && !(pl->flags & DKSS_RMUL_DIRECT);
-    // m = 64 NTT kernels over p^4 with p < 2^30: p-adic digits (padic.cuh) within their limits
+    // m = 64 forward half-column DFTs: unreduced between stages where 2^7 p^z fits L words and the
+    // top word of p^z is at least 2^8 (the final reduction's quotient estimate)
+    {
+        const uint32_t qtop = pl->q_limbs[pl->L - 1];
+        pl->dft_lazy = pl->m == 64 && pl->L >= 3 && bitlen(pl->q) + 7 <= 32 * pl->L && qtop >= 256;
+        pl->red_rcp = pl->dft_lazy ? (uint32_t)(((uint64_t)1 << 40) / ((uint64_t)qtop + 1)) : 0;
+    }
+    // m = 64 NTT kernels over p^4 with p < 2^30: p-adic digits (padic.cuh) within their limits,
+    // where they take fewer multiply-adds than the Montgomery products: with fast carries
+    // (floor(2^32/p) a power of two), or against five 26-bit limbs.  Four limbs with the
+    // generic carries measured slower (p = 7340033: 12.3 against 11.3 ms at 2^28 bits).
     pl->padic = !(pl->flags & (DKSS_RMUL_DIRECT | DKSS_FORM_INT8TC | DKSS_ARITH_MONT)) && pl->m == 64 &&
                 pl->z == 4 && pl->p < ((u128)1 << 30) && !pl->q_sparse &&
-                pd_lazy_bounds((uint64_t)pl->p, pl->m, pl->L, &pl->pd_bias);
+                pd_lazy_bounds((uint64_t)pl->p, pl->m, pl->L, &pl->pd_bias) &&
+                (pl->pd_bias.fast || pl->LR >= 5);
     if (pl->padic) {
         const uint64_t p = (uint64_t)pl->p;
         uint32_t s = 0;

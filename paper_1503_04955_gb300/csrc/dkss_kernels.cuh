@@ -78,6 +78,8 @@ struct LevelParams {
     uint32_t eval_skip;          // their DFTs: bit s = stage s adds t = b unreduced where the twiddle is 1
     uint32_t eval_noscale;       // last level: multiply a b unscaled, scale by (2M)^-1 at the end
     uint32_t square;             // last level of a square (b is a): one forward transform per element
+    uint32_t dft_lazy;           // m = 64 forward half-column DFTs with unreduced sums (2^7 p^z fits the words)
+    uint32_t red_rcp;            // floor(2^40 / (q_top + 1)), q_top the top word of p^z (their final reduction)
 };
 
 // How R-multiplications are computed.
@@ -1147,6 +1149,135 @@ __device__ __forceinline__ void cp_async_elements(uint32_t* dst, int n, Src src,
     cp_async_wait_all();
 }
 
+// ---------------------------------------------------------------------------
+// Lazy DFT arithmetic of the forward half-column kernel: residues stay
+// unreduced L-word integers congruent mod q = p^z.  A sum is a plain carry
+// chain; a difference at a stage whose inputs are below 2^s q is
+// a - b + 2^s q (nonnegative), so both results stay below 2^(s+1) q.  The
+// host enables this only where 2^7 q fits the L words (dft_lazy), and every
+// value is reduced once when it is written back (lz32_reduce).
+// ---------------------------------------------------------------------------
+// The carries run in the condition-code chain (one asm block per chain, so
+// nothing comes between its instructions): one instruction per word.
+template <int L>
+__device__ __forceinline__ void lz32_add(uint32_t (&r)[L], const uint32_t (&a)[L], const uint32_t (&b)[L]) {
+    static_assert(L == 3 || L == 4, "half-column kernels hold 3- or 4-word residues");
+    if constexpr (L == 4) {
+        asm("add.cc.u32 %0, %4, %8;\n\taddc.cc.u32 %1, %5, %9;\n\taddc.cc.u32 %2, %6, %10;\n\taddc.u32 %3, %7, %11;"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]));
+    } else {
+        asm("add.cc.u32 %0, %3, %6;\n\taddc.cc.u32 %1, %4, %7;\n\taddc.u32 %2, %5, %8;"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2])
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(b[0]), "r"(b[1]), "r"(b[2]));
+    }
+}
+
+// r = a - b (no borrow out: a >= b as integers)
+template <int L>
+__device__ __forceinline__ void lz32_sub_n(uint32_t (&r)[L], const uint32_t (&a)[L], const uint32_t (&b)[L]) {
+    static_assert(L == 3 || L == 4, "half-column kernels hold 3- or 4-word residues");
+    if constexpr (L == 4) {
+        asm("sub.cc.u32 %0, %4, %8;\n\tsubc.cc.u32 %1, %5, %9;\n\tsubc.cc.u32 %2, %6, %10;\n\tsubc.u32 %3, %7, %11;"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]));
+    } else {
+        asm("sub.cc.u32 %0, %3, %6;\n\tsubc.cc.u32 %1, %4, %7;\n\tsubc.u32 %2, %5, %8;"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2])
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(b[0]), "r"(b[1]), "r"(b[2]));
+    }
+}
+
+// r = a - b + B (B >= b as integers, the result below 2^(32L))
+template <int L>
+__device__ __forceinline__ void lz32_sub(uint32_t (&r)[L], const uint32_t (&a)[L], const uint32_t (&b)[L],
+                                         const uint32_t (&B)[L]) {
+    uint32_t t[L];
+    lz32_sub_n<L>(t, B, b);
+    lz32_add<L>(r, a, t);
+}
+
+// B = q 2^s (s <= 7, no overflow: checked on the host)
+template <int L>
+__device__ __forceinline__ void lz32_bias(uint32_t (&B)[L], const Mod<L>& md, int s) {
+#pragma unroll
+    for (int i = L - 1; i >= 0; --i)
+        B[i] = s == 0 ? md.q[i] : (md.q[i] << s) | (i > 0 ? md.q[i - 1] >> (32 - s) : 0u);
+}
+
+// Canonical residue of x < 2^7 q: k = floor(x_top rcp / 2^40), rcp =
+// floor(2^40 / (q_top + 1)), is floor(x / q) or up to two less (x_top and
+// q_top the top words; q_top >= 2^8 on the host), so x - k q is below 3q and
+// two conditional subtractions finish.
+template <int L>
+__device__ __forceinline__ void lz32_reduce(uint32_t (&r)[L], const uint32_t (&x)[L], const Mod<L>& md,
+                                            uint32_t rcp) {
+    const uint32_t k = (uint32_t)(((uint64_t)x[L - 1] * rcp) >> 40);
+    uint32_t kq[L];
+    uint64_t carry = 0;
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+        const uint64_t t = (uint64_t)k * md.q[i] + carry;
+        kq[i] = (uint32_t)t;
+        carry = t >> 32;
+    }
+    lz32_sub_n<L>(r, x, kq);
+    // r below 3q: two conditional subtractions of q.  sub_mod(r, q) computes
+    // r - q and adds q back where that borrows, i.e. r - q if r >= q, else r.
+#pragma unroll
+    for (int pass = 0; pass < 2; ++pass) {
+        uint32_t d[L];
+        sub_mod<L>(d, r, md.q, md);
+#pragma unroll
+        for (int i = 0; i < L; ++i) r[i] = d[i];
+    }
+}
+
+// dft_dit with lazy arithmetic: the inputs below 2^s0 q, stage lh's below
+// 2^(s0+lh) q; the outputs below 2^(s0+log2 n) q, unreduced.
+template <int m, int L>
+__device__ void dft_dit_lazy(uint32_t* base, int n, int root, int s0, const Mod<L>& md) {
+    using G = Geo<m, L>;
+    Team<m, L> tm;
+    const int log2n = 31 - __clz(n);
+    for (int lh = 0; lh < log2n; ++lh) {
+        const int half = 1 << lh;
+        const int scale = n >> (lh + 1);
+        uint32_t B[L];
+        lz32_bias<L>(B, md, s0 + lh);
+        for (int bf = tm.id; bf < n / 2; bf += G::NTEAMS) {
+            int k_in = bf & (half - 1);
+            int ia = ((bf >> lh) << (lh + 1)) + k_in;
+            int ib = ia + half;
+            int sh = (root * scale * k_in) & (G::TWO_M - 1);
+            uint32_t* pa = base + ia * G::ES;
+            uint32_t* pb = base + ib * G::ES;
+            uint32_t a[G::CPL][L], y[G::CPL][L];
+            bool ng[G::CPL];
+#pragma unroll
+            for (int c = 0; c < G::CPL; ++c) {
+                int t = tm.lane + c * G::TEAM;
+                ld_res<L>(a[c], pa + t * L);
+                shifted<m, L>(y[c], ng[c], pb, t, sh);
+            }
+            __syncwarp(tm.mask);
+#pragma unroll
+            for (int c = 0; c < G::CPL; ++c) {
+                int t = tm.lane + c * G::TEAM;
+                uint32_t pl[L], mi[L];
+                lz32_add<L>(pl, a[c], y[c]);
+                lz32_sub<L>(mi, a[c], y[c], B);
+                uint32_t* d0 = (ng[c] ? pb : pa) + t * L;
+                uint32_t* d1 = (ng[c] ? pa : pb) + t * L;
+                st_res<L>(d0, pl);
+                st_res<L>(d1, mi);
+            }
+            __syncwarp(tm.mask);
+        }
+        __syncthreads();
+    }
+}
+
 // Elements j = 2i + parity (i < m) of the column into slot bitrev(i) (log2 m bits).
 template <int m, int L, bool FIRST>
 __device__ __forceinline__ void half_load_fwd(const LevelParams& prm, uint32_t* half, uint64_t base, uint64_t l,
@@ -1197,16 +1328,21 @@ __global__ void __launch_bounds__(kThreads) k_dft_fwd_half(LevelParams prm, Mod<
         const uint64_t blk = column >> lg_mu, l = column & (mu_d - 1);
         const uint64_t base = blk * prm.len;
         uint32_t* poly = prm.data + (op ? prm.poly_words : 0);
+        const bool lazy = prm.dft_lazy != 0;   // unreduced sums, one reduction per output
         // even elements: E_v, v < m, to the scratch slice
         half_load_fwd<m, L, FIRST>(prm, smem, base, l, mu_d, op, 0);
         __syncthreads();
-        dft_dit<m, L>(smem, 1, m, 2, md);
+        if (lazy) dft_dit_lazy<m, L>(smem, m, 2, 0, md);
+        else dft_dit<m, L>(smem, 1, m, 2, md);
         copy_words_block<m, L>(E, smem, m * G::EW);
         __syncthreads();
         // odd elements: O_v in shared memory
         half_load_fwd<m, L, FIRST>(prm, smem, base, l, mu_d, op, 1);
         __syncthreads();
-        dft_dit<m, L>(smem, 1, m, 2, md);
+        if (lazy) dft_dit_lazy<m, L>(smem, m, 2, 0, md);
+        else dft_dit<m, L>(smem, 1, m, 2, md);
+        uint32_t B6[L];   // the lazy halves are below 2^6 q
+        lz32_bias<L>(B6, md, ilog2<m>());
         // X_v = E_v + alpha^v O_v, X_(v+m) = E_v - alpha^v O_v
         for (int v = tm.id; v < m; v += G::NTEAMS) {
 #pragma unroll
@@ -1216,8 +1352,16 @@ __global__ void __launch_bounds__(kThreads) k_dft_fwd_half(LevelParams prm, Mod<
                 bool ng;
                 ld_res<L>(a, E + v * G::EW + t * L);
                 shifted<m, L>(y, ng, smem + v * G::ES, t, v);
-                add_mod<L>(pl, a, y, md);
-                sub_mod<L>(mi, a, y, md);
+                if (lazy) {
+                    uint32_t x[L];
+                    lz32_add<L>(x, a, y);
+                    lz32_reduce<L>(pl, x, md, prm.red_rcp);
+                    lz32_sub<L>(x, a, y, B6);
+                    lz32_reduce<L>(mi, x, md, prm.red_rcp);
+                } else {
+                    add_mod<L>(pl, a, y, md);
+                    sub_mod<L>(mi, a, y, md);
+                }
                 // where the shifted coefficient carries a minus sign the two results trade places
                 uint32_t* d0 = poly + ((base + (uint64_t)v * mu_d + l) * m + t) * L;
                 uint32_t* d1 = poly + ((base + (uint64_t)(v + m) * mu_d + l) * m + t) * L;

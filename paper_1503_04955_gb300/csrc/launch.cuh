@@ -64,6 +64,8 @@ static LevelParams make_level(const dkss_plan_s* pl) {
     lp.i8_S = pl->i8_S;
     lp.ntt_prescale = pl->ntt_bias.prescale ? 1u : 0u;
     lp.eval_skip = pl->ntt_bias.eval_skip;
+    lp.dft_lazy = pl->dft_lazy ? 1u : 0u;
+    lp.red_rcp = pl->red_rcp;
     {
         uint32_t k = 0;
         while ((1ull << k) < pl->r_last) ++k;

@@ -24,7 +24,9 @@ SMALL = [
     (262144, 2048, 16, 16, 12289, 4),       # m=16, two radix-2m levels, last level 4
     (786432, 2048, 32, 24, 65537, 5),       # m=32, L=3, last level 2m
     (1 << 22, 1 << 12, 64, 32, 7340033, 4),  # m=64, L=3 (three REDC subtractions), last level 2m
-    (1 << 21, 1 << 14, 64, 16, 998244353, 4),  # m=64, L=4, two radix-2m levels, last level 2
+    (1 << 21, 1 << 14, 64, 16, 998244353, 4),  # m=64, L=4, two radix-2m levels, last level 2; p-adic, fast carries
+    (1 << 21, 1 << 14, 64, 16, 754974721, 4),  # m=64, L=4, LR=5: p-adic with the generic carries
+    (1 << 21, 1 << 14, 64, 16, 1073479681, 4),  # m=64, p just below 2^30: p-adic, fast carries at their limits
     (4096, 32, 16, 16, 40961, 3),           # m=16, L=2, LR=2: NTT form prescales the componentwise products
     (65536, 256, 16, 32, 12289, 6),         # m=16, L=3: padded shared-memory element stride
 ]
@@ -55,8 +57,12 @@ def check_product(dk, oc, cfg, A, B, with_oracle=True, with_forward=True, flags=
         want = 2 if flags & 2 else 1 if flags & 16 else 3 if (flags & 128 and cfg[2] <= 32) else 0
         info = plan.info()
         assert info["rmul"] == want
-        # m = 64 over p^4, p < 2^30: the NTT form computes in p-adic digits unless DKSS_ARITH_MONT
-        assert info["padic"] == int(want == 0 and not flags & 512 and cfg[2] == 64 and cfg[5] == 4 and cfg[4] < 1 << 30)
+        # m = 64 over p^4, p < 2^30: the NTT form computes in p-adic digits unless DKSS_ARITH_MONT,
+        # where floor(2^32/p) is a power of two or the Montgomery products need five limbs
+        nmu = (1 << 32) // cfg[4]
+        fewer = (nmu & (nmu - 1)) == 0 or info["LR"] >= 5
+        assert info["padic"] == int(want == 0 and not flags & 512 and cfg[2] == 64 and cfg[5] == 4
+                                    and cfg[4] < 1 << 30 and fewer)
         c = plan.mul(to_dev(A), to_dev(B))
         fwd = plan.forward(to_dev(A)) if with_forward else None
         plan.sync_status()
