@@ -327,12 +327,20 @@ uint32_t brv(uint32_t x, uint32_t bits) {
 // Constants of the transform in p-adic digits (padic.cuh, PdLayout): the
 // entries of NttLayout as plain residues, biases K (p, p-1, p-1, p-1), then the
 // digits of 2^(32j) mod p^4, j < 4.
+// Residue index of the digits of 2^(32j) mod p^4 in that table (PdLayout<m>::POW32).
+uint32_t pd_pow32_index(uint32_t m) {
+    uint32_t lg = 0;
+    while ((1u << lg) < m) ++lg;
+    const uint32_t Q = 2 * m + lg + 2, PSI = Q + 7 + lg + 1;
+    return PSI + 2 * m;
+}
+
 void build_ntt_consts_pd(const dkss_plan_s* pl, std::vector<uint32_t>& out) {
     constexpr uint32_t Z = 4;
     const uint32_t m = pl->m;
     uint32_t lg = 0;
     while ((1u << lg) < m) ++lg;
-    const uint32_t Q = 2 * m + lg + 2, PSI = Q + 7 + lg + 1, COUNT = PSI + 2 * m;
+    const uint32_t Q = 2 * m + lg + 2, COUNT = pd_pow32_index(m);
     out.assign((size_t)(COUNT + 4) * Z, 0);
     MontCtx c(pl->q);
     const u128 phi = pl->q / pl->p * (pl->p - 1);
@@ -806,6 +814,9 @@ dkss_status finish_plan(dkss_plan_s* pl, dkss_status s, dkss_plan_t* plan) {
         pl->pd_nmu = (uint32_t)(((uint64_t)1 << 32) / p);
         pl->pd_mu = (uint64_t)((((u128)1) << (64 + s)) / p);
         pl->pd_fast = pl->pd_bias.fast;
+        // residues of 4 words hold 4 digits as well: the forward levels keep them in HBM
+        pl->pd_io = pl->L == 4 && pl->pd_bias.dft_ok;
+        pl->pd_pw_off = (uint64_t)pd_pow32_index(pl->m) * 4;
         pl->pd_mu_lo = (uint32_t)((((u128)1) << 64) / p);
         while ((1u << (pl->pd_lg_nmu + 1)) <= pl->pd_nmu) ++pl->pd_lg_nmu;
     }

@@ -20,6 +20,7 @@ struct RangeParams {
     uint64_t n_res;         // residues to check
     uint32_t q[4];          // p^z, L limbs (limbs >= L zero)
     uint32_t* status;
+    uint32_t digit_p;       // nonzero: the residues are p-adic digits, each must be below p
 };
 
 // x >= q for L-limb little-endian values
@@ -52,7 +53,12 @@ __global__ void __launch_bounds__(256) k_check_range(RangeParams prm) {
 #pragma unroll
             for (int i = 0; i < L; ++i) x[i] = __ldg(p + i);
         }
-        bad |= ge_q<L>(x, q);
+        if (prm.digit_p) {
+#pragma unroll
+            for (int i = 0; i < L; ++i) bad |= x[i] >= prm.digit_p;
+        } else {
+            bad |= ge_q<L>(x, q);
+        }
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(prm.status, kStatusRange);
 }

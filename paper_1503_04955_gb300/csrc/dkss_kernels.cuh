@@ -80,6 +80,10 @@ struct LevelParams {
     uint32_t square;             // last level of a square (b is a): one forward transform per element
     uint32_t dft_lazy;           // m = 64 forward half-column DFTs with unreduced sums (2^7 p^z fits the words)
     uint32_t red_rcp;            // floor(2^40 / (q_top + 1)), q_top the top word of p^z (their final reduction)
+    uint32_t pd_io;              // the forward levels keep p-adic digits in HBM (4 words, padic.cuh)
+    uint32_t pd_fast;            // their conversions may take the fast carries (ModPD<4, true>)
+    ModPD<kPdDigits> pd;         // the conversions' constants (generic carries; same fields for fast ones)
+    const uint32_t* pd_pw;       // digits of 2^(32j) mod p^4, j < 4 (the plan's constant table)
 };
 
 // How R-multiplications are computed.
@@ -603,6 +607,26 @@ __device__ __forceinline__ void load_shifted_pd(uint32_t (&out)[Z], const uint32
     for (int i = 0; i < Z; ++i) out[i] = neg ? bn[i] - y[i] : y[i];
 }
 
+// The same coefficient where the residues in HBM already are canonical digits.
+template <int m, int Z>
+__device__ __forceinline__ void load_shifted_digits(uint32_t (&out)[Z], const uint32_t* x, int t, int r,
+                                                    const uint32_t (&bn)[Z]) {
+    int src = t - r;
+    bool neg = false;
+    if (src < 0) {
+        src += m;
+        neg = true;
+        if (src < 0) {
+            src += m;
+            neg = false;
+        }
+    }
+    uint32_t y[Z];
+    ld_res<Z>(y, x + src * Z);
+#pragma unroll
+    for (int i = 0; i < Z; ++i) out[i] = neg ? bn[i] - y[i] : y[i];
+}
+
 // The bad multiplications of twiddle_ntt_group with the transform in R in
 // p-adic digits: the element's residues are converted on load and back on
 // store, the twiddle table and the transform constants hold digits.
@@ -632,9 +656,15 @@ __device__ __forceinline__ void twiddle_pd_group(const LevelParams& prm, const M
     uint32_t bn[Z];
     ldg_rr<Z>(bn, cst + NttLayout<m>::BN * Z);
     const uint32_t* pw = cst + PdLayout<m>::POW32 * Z;
+    // forward levels with digits in HBM (L = Z words): no conversions at either edge
+    bool dio = false;
+    if constexpr (!INV && L == Z) dio = prm.pd_io != 0;
     uint32_t vv[4][Z];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) load_shifted_pd<m, L, Z>(vv[j], x, lane + j * NT::TEAM, r, bn, pw, md);
+    for (int j = 0; j < 4; ++j) {
+        if (dio) load_shifted_digits<m, Z>(vv[j], x, lane + j * NT::TEAM, r, bn);
+        else load_shifted_pd<m, L, Z>(vv[j], x, lane + j * NT::TEAM, r, bn, pw, md);
+    }
     ntt_forward_pd<m, Z>(vv, buf, lane, tm.mask, cst, md);
     const uint32_t* tw = prm.table_eval + (sidx * m + 4 * lane) * Z;
 #pragma unroll
@@ -653,6 +683,12 @@ __device__ __forceinline__ void twiddle_pd_group(const LevelParams& prm, const M
         else {
 #pragma unroll
             for (int w = 0; w < Z; ++w) c[w] = vv[j][w];
+        }
+        if constexpr (L == Z) {
+            if (dio) {
+                st_res<L>(x + (lane + j * NT::TEAM) * L, c);
+                continue;
+            }
         }
         pd_to_words<L, Z>(o, c, md);
         st_res<L>(x + (lane + j * NT::TEAM) * L, o);
@@ -805,6 +841,65 @@ constexpr size_t level_ntt_smem_bytes() {
     return sizeof(uint32_t) * ((size_t)Geo<m, L>::TWO_M * Geo<m, L>::ES + (size_t)NttTeam<m>::NTEAMS * m * LR);
 }
 
+// dft_dit over residues held as p-adic digits (padic.cuh): sums digitwise,
+// a difference adds 2 (p, p-1, ..., p-1) (zero mod p^z, digits at least those
+// of a normalised residue), every stage normalises its outputs and the last
+// makes them canonical; the plan's check (pd_lazy_bounds) keeps every digit
+// below 2^32.  Inputs canonical digits.
+template <int m, int Z, bool F>
+__device__ void dft_dit_pd(uint32_t* base, int arrays, int n, int root, const ModPD<Z, F>& md) {
+    using G = Geo<m, Z>;
+    Team<m, Z> tm;
+    const int log2n = 31 - __clz(n);
+    uint32_t D2[Z];
+#pragma unroll
+    for (int k = 0; k < Z; ++k) D2[k] = 2 * (k == 0 ? md.p : md.p - 1);
+    for (int lh = 0; lh < log2n; ++lh) {
+        const int half = 1 << lh;
+        const int scale = n >> (lh + 1);
+        const bool last = lh + 1 == log2n;
+        for (int bfa = tm.id; bfa < arrays * (n / 2); bfa += G::NTEAMS) {
+            uint32_t* s = base + (bfa >> (log2n - 1)) * n * G::ES;
+            int bf = bfa & (n / 2 - 1);
+            int k_in = bf & (half - 1);
+            int ia = ((bf >> lh) << (lh + 1)) + k_in;
+            int ib = ia + half;
+            int sh = (root * scale * k_in) & (G::TWO_M - 1);
+            uint32_t* pa = s + ia * G::ES;
+            uint32_t* pb = s + ib * G::ES;
+            uint32_t a[G::CPL][Z], y[G::CPL][Z];
+            bool ng[G::CPL];
+#pragma unroll
+            for (int c = 0; c < G::CPL; ++c) {
+                int t = tm.lane + c * G::TEAM;
+                ld_res<Z>(a[c], pa + t * Z);
+                shifted<m, Z>(y[c], ng[c], pb, t, sh);
+            }
+            __syncwarp(tm.mask);
+#pragma unroll
+            for (int c = 0; c < G::CPL; ++c) {
+                int t = tm.lane + c * G::TEAM;
+                uint32_t pl[Z], mi[Z];
+                lz_add<Z>(pl, a[c], y[c]);
+                lz_sub<Z>(mi, a[c], D2, y[c]);
+                if (last) {
+                    pd_canon<Z>(pl, pl, md);
+                    pd_canon<Z>(mi, mi, md);
+                } else {
+                    pd_norm<Z>(pl, md);
+                    pd_norm<Z>(mi, md);
+                }
+                uint32_t* d0 = (ng[c] ? pb : pa) + t * Z;
+                uint32_t* d1 = (ng[c] ? pa : pb) + t * Z;
+                st_res<Z>(d0, pl);
+                st_res<Z>(d1, mi);
+            }
+            __syncwarp(tm.mask);
+        }
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Last level of both forward transforms, componentwise products scaled by
 // (2M)^-1 (Section 3.2.6), and the first level of the backwards transform,
@@ -838,7 +933,14 @@ __device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>
     }
     __syncthreads();
     const int root = G::TWO_M / n;
-    dft_dit<m, L>(sa, 2 * nb, n, root, md);
+    // forward levels with digits in HBM: the last level's DFT on digits too
+    bool pdio = false;
+    if constexpr (FORM == kFormNtt && IsPD<MR>::value && L == LR) pdio = prm.pd_io != 0;
+    if (pdio) {
+        if constexpr (FORM == kFormNtt && IsPD<MR>::value && L == LR) dft_dit_pd<m, LR>(sa, 2 * nb, n, root, mr);
+    } else {
+        dft_dit<m, L>(sa, 2 * nb, n, root, md);
+    }
     // componentwise products c_v = a_v * b_v * (2M)^-1
     Team<m, L> tm;
     if constexpr (FORM == kFormI8) {
@@ -884,7 +986,12 @@ __device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 ld_res<L>(w, sb + v * G::ES + (lane + j * NT::TEAM) * L);
-                pd_from_words<L, LR>(x[j], w, pw, mr);
+                if (pdio) {
+#pragma unroll
+                    for (int k = 0; k < LR; ++k) x[j][k] = w[k < L ? k : 0];
+                } else {
+                    pd_from_words<L, LR>(x[j], w, pw, mr);
+                }
             }
             ntt_forward_pd<m, LR>(x, buf, lane, nt.mask, cst, mr);
 #pragma unroll
@@ -897,7 +1004,12 @@ __device__ __forceinline__ void final_block(const LevelParams& prm, const Mod<L>
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     ld_res<L>(w, sa + v * G::ES + (lane + j * NT::TEAM) * L);
-                    pd_from_words<L, LR>(x[j], w, pw, mr);
+                    if (pdio) {
+#pragma unroll
+                        for (int k = 0; k < LR; ++k) x[j][k] = w[k < L ? k : 0];
+                    } else {
+                        pd_from_words<L, LR>(x[j], w, pw, mr);
+                    }
                 }
                 ntt_forward_pd<m, LR>(x, buf, lane, nt.mask, cst, mr);
             }
@@ -1234,9 +1346,12 @@ __device__ __forceinline__ void lz32_reduce(uint32_t (&r)[L], const uint32_t (&x
 }
 
 // dft_dit with lazy arithmetic: the inputs below 2^s0 q, stage lh's below
-// 2^(s0+lh) q; the outputs below 2^(s0+log2 n) q, unreduced.
+// 2^(s0+lh) q; the outputs below 2^(s0+log2 n) q, unreduced.  With pd_in
+// (L = 4) the inputs are canonical p-adic digits, converted to words as the
+// first stage loads them (each residue once).
 template <int m, int L>
-__device__ void dft_dit_lazy(uint32_t* base, int n, int root, int s0, const Mod<L>& md) {
+__device__ void dft_dit_lazy(uint32_t* base, int n, int root, int s0, const Mod<L>& md, bool pd_in,
+                             const ModPD<kPdDigits>& pd) {
     using G = Geo<m, L>;
     Team<m, L> tm;
     const int log2n = 31 - __clz(n);
@@ -1259,6 +1374,17 @@ __device__ void dft_dit_lazy(uint32_t* base, int n, int root, int s0, const Mod<
                 int t = tm.lane + c * G::TEAM;
                 ld_res<L>(a[c], pa + t * L);
                 shifted<m, L>(y[c], ng[c], pb, t, sh);
+                if constexpr (L == kPdDigits) {
+                    if (pd_in && lh == 0) {
+                        uint32_t w[L];
+                        pd_to_words<L, L>(w, a[c], pd);
+#pragma unroll
+                        for (int k = 0; k < L; ++k) a[c][k] = w[k];
+                        pd_to_words<L, L>(w, y[c], pd);
+#pragma unroll
+                        for (int k = 0; k < L; ++k) y[c][k] = w[k];
+                    }
+                }
             }
             __syncwarp(tm.mask);
 #pragma unroll
@@ -1291,6 +1417,20 @@ __device__ __forceinline__ void half_load_fwd(const LevelParams& prm, uint32_t* 
         cp_async_elements<m, L>(
             half, m, [&](int i) { return poly + (base + (2 * (uint64_t)i + parity) * mu_d + l) * G::EW; },
             [&](int i) { return bitrev(i, LOG2_M); });
+        if constexpr (L == kPdDigits) {
+            // canonical digits in HBM: words for the DFT's arithmetic (the lazy DFT
+            // converts in its first stage, where it loads every residue once)
+            if (prm.pd_io && !prm.dft_lazy) {
+                __syncthreads();
+                for (int idx = threadIdx.x; idx < m * m; idx += kThreads) {
+                    uint32_t* r = half + (idx / m) * G::ES + (idx % m) * L;
+                    uint32_t d[L], w[L];
+                    ld_res<L>(d, r);
+                    pd_to_words<L, L>(w, d, prm.pd);
+                    st_res<L>(r, w);
+                }
+            }
+        }
         return;
     }
     for (int idx = threadIdx.x; idx < m * m; idx += kThreads) {
@@ -1332,14 +1472,15 @@ __global__ void __launch_bounds__(kThreads) k_dft_fwd_half(LevelParams prm, Mod<
         // even elements: E_v, v < m, to the scratch slice
         half_load_fwd<m, L, FIRST>(prm, smem, base, l, mu_d, op, 0);
         __syncthreads();
-        if (lazy) dft_dit_lazy<m, L>(smem, m, 2, 0, md);
+        const bool pd_in = !FIRST && prm.pd_io;
+        if (lazy) dft_dit_lazy<m, L>(smem, m, 2, 0, md, pd_in, prm.pd);
         else dft_dit<m, L>(smem, 1, m, 2, md);
         copy_words_block<m, L>(E, smem, m * G::EW);
         __syncthreads();
         // odd elements: O_v in shared memory
         half_load_fwd<m, L, FIRST>(prm, smem, base, l, mu_d, op, 1);
         __syncthreads();
-        if (lazy) dft_dit_lazy<m, L>(smem, m, 2, 0, md);
+        if (lazy) dft_dit_lazy<m, L>(smem, m, 2, 0, md, pd_in, prm.pd);
         else dft_dit<m, L>(smem, 1, m, 2, md);
         uint32_t B6[L];   // the lazy halves are below 2^6 q
         lz32_bias<L>(B6, md, ilog2<m>());
@@ -1365,6 +1506,25 @@ __global__ void __launch_bounds__(kThreads) k_dft_fwd_half(LevelParams prm, Mod<
                 // where the shifted coefficient carries a minus sign the two results trade places
                 uint32_t* d0 = poly + ((base + (uint64_t)v * mu_d + l) * m + t) * L;
                 uint32_t* d1 = poly + ((base + (uint64_t)(v + m) * mu_d + l) * m + t) * L;
+                if constexpr (L == kPdDigits) {
+                    if (prm.pd_io) {   // canonical digits for the bad multiplications
+                        uint32_t dg[L];
+                        if (prm.pd_fast) {
+                            const ModPD<L, true> f = pd_fast_view(prm.pd);
+                            pd_from_words<L, L>(dg, pl, prm.pd_pw, f);
+#pragma unroll
+                            for (int w = 0; w < L; ++w) pl[w] = dg[w];
+                            pd_from_words<L, L>(dg, mi, prm.pd_pw, f);
+                        } else {
+                            pd_from_words<L, L>(dg, pl, prm.pd_pw, prm.pd);
+#pragma unroll
+                            for (int w = 0; w < L; ++w) pl[w] = dg[w];
+                            pd_from_words<L, L>(dg, mi, prm.pd_pw, prm.pd);
+                        }
+#pragma unroll
+                        for (int w = 0; w < L; ++w) mi[w] = dg[w];
+                    }
+                }
                 st_res<L>(ng ? d1 : d0, pl);
                 st_res<L>(ng ? d0 : d1, mi);
             }

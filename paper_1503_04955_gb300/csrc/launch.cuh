@@ -66,6 +66,12 @@ static LevelParams make_level(const dkss_plan_s* pl) {
     lp.eval_skip = pl->ntt_bias.eval_skip;
     lp.dft_lazy = pl->dft_lazy ? 1u : 0u;
     lp.red_rcp = pl->red_rcp;
+    lp.pd_io = pl->pd_io ? 1u : 0u;
+    lp.pd_fast = pl->pd_fast ? 1u : 0u;
+    if (pl->pd_io) {
+        lp.pd = make_mr<kPdDigits, ModPD<kPdDigits>>(pl);
+        lp.pd_pw = pl->d_ntt + pl->pd_pw_off;
+    }
     {
         uint32_t k = 0;
         while ((1ull << k) < pl->r_last) ++k;
@@ -86,6 +92,14 @@ __global__ void __launch_bounds__(kThreads) k_final_dft(LevelParams prm, Mod<L> 
         int j = idx / m, t = idx % m;
         uint32_t x[L];
         ld_res<L>(x, prm.data + ((base + j) * m + t) * L);
+        if constexpr (L == kPdDigits) {
+            if (prm.pd_io) {   // the forward levels left canonical p-adic digits
+                uint32_t w[L];
+                pd_to_words<L, L>(w, x, prm.pd);
+#pragma unroll
+                for (int k = 0; k < L; ++k) x[k] = w[k];
+            }
+        }
         st_res<L>(smem + bitrev(j, log2n) * G::ES + t * L, x);
     }
     __syncthreads();
@@ -129,12 +143,14 @@ __global__ void k_unpermute(const uint32_t* src, uint64_t* dst, uint64_t P2, uin
 // DKSS_DEBUG_CHECKS: every residue of n_res residues at poly is below p^z
 // (debug_checks.cuh); a failure sets kStatusRange in the plan's status word.
 template <int L>
-static dkss_status range_check(dkss_plan_s* pl, const uint32_t* poly, uint64_t n_res, cudaStream_t st) {
+static dkss_status range_check(dkss_plan_s* pl, const uint32_t* poly, uint64_t n_res, cudaStream_t st,
+                               bool digits = false) {
     if (!(pl->flags & DKSS_DEBUG_CHECKS)) return DKSS_OK;
     RangeParams rp{};
     rp.poly = poly;
     rp.n_res = n_res;
     for (int i = 0; i < 4; ++i) rp.q[i] = pl->q_limbs[i];
+    rp.digit_p = digits ? (uint32_t)pl->p : 0u;
     rp.status = pl->d_status;
     const uint64_t blocks = std::min<uint64_t>((n_res + 255) / 256, (uint64_t)pl->sm_count * 8);
     k_check_range<L><<<(unsigned)std::max<uint64_t>(1, blocks), 256, 0, st>>>(rp);
@@ -471,8 +487,8 @@ static dkss_status run_mul_coef(dkss_plan_s* pl, const uint64_t* a, const uint64
     s = launch_forward_levels<m, L, LR, MR>(pl, lp, square ? 1 : 2, st);
     if (s != DKSS_OK) return s;
     if ((s = inject_range_fault<L>(pl, st)) != DKSS_OK) return s;
-    // both transformed operands (b directly follows a)
-    if ((s = range_check<L>(pl, pl->d_work, (square ? 1 : 2) * pl->P2 * m, st)) != DKSS_OK) return s;
+    // both transformed operands (b directly follows a); p-adic digits where the forward levels keep them
+    if ((s = range_check<L>(pl, pl->d_work, (square ? 1 : 2) * pl->P2 * m, st, pl->pd_io)) != DKSS_OK) return s;
     lp.len = pl->r_last;
     if (square) {
         lp.poly_words = 0;

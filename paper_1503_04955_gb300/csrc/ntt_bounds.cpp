@@ -399,6 +399,18 @@ bool pd_lazy_bounds(uint64_t p, uint32_t m, uint32_t L, PdBiases* out) {
     c.nsh = 0;
     while (((uint64_t)1 << c.nsh) < p) ++c.nsh;
     if (!pd_schedule(c, m, L, out)) return false;
+    // DFTs on digits (dft_dit_pd): canonical inputs; per stage a + y and a - y + 2 (p, p-1, ...),
+    // both normalised; the bias covers a normalised digit; up to 7 stages, the last made canonical
+    {
+        uint64_t N = p - 1;
+        out->dft_ok = true;
+        for (int st = 0; st < 7 && out->dft_ok; ++st) {
+            const uint64_t S = std::max(2 * N, N + 2 * p);
+            uint64_t Nn;
+            if (N > 2 * (p - 1) || !c.norm(S, &Nn) || !c.canon_ok(S)) out->dft_ok = false;
+            else N = Nn;
+        }
+    }
     // fast carries when floor(2^32 / p) is a power of two and the columns allow them
     if ((c.nmu & (c.nmu - 1)) == 0) {
         PdCtx f = c;

@@ -45,6 +45,7 @@ struct PdBiases {
     uint32_t kb[7] = {0, 0, 0, 0, 0, 0, 0};
     bool ok = false;
     bool fast = false;   // the fast carries of ModPD<Z, true> stay within their limits too
+    bool dft_ok = false; // DFTs of up to 2^7 points on digits (dft_dit_pd) stay within their limits
 };
 
 // true when the p-adic digit form with z = 4 digits (p < 2^30, residues

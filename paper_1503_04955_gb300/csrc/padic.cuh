@@ -44,6 +44,20 @@ struct ModPD {
     uint32_t lg_nmu;  // log2 floor(2^32 / p) (F)
 };
 
+// The same constants for the fast carries (the fields are those of ModPD<Z, false>).
+template <int Z>
+DKSS_HD ModPD<Z, true> pd_fast_view(const ModPD<Z, false>& md) {
+    ModPD<Z, true> f;
+    f.p = md.p;
+    f.nmu = md.nmu;
+    f.nsh = md.nsh;
+    f.s = md.s;
+    f.mu = md.mu;
+    f.mu_lo = md.mu_lo;
+    f.lg_nmu = md.lg_nmu;
+    return f;
+}
+
 template <class MR>
 struct IsPD {
     static constexpr bool value = false;

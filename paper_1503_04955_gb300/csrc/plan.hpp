@@ -41,6 +41,8 @@ struct dkss_plan_s {
     uint64_t pd_mu = 0;
     bool dft_lazy = false;        // m = 64 forward half-column DFTs unreduced between stages: 2^7 p^z < 2^(32L)
     uint32_t red_rcp = 0;         // their reduction: floor(2^40 / (top word of p^z + 1))
+    bool pd_io = false;           // the forward levels keep p-adic digits in HBM (padic: 4 words per residue)
+    uint64_t pd_pw_off = 0;       // word offset of the digits of 2^(32j) mod p^4 in d_ntt
     bool pd_fast = false;         // fast carries (floor(2^32/p) a power of two; padic.cuh)
     uint32_t pd_mu_lo = 0, pd_lg_nmu = 0;
     // device memory owned by the plan

@@ -7,7 +7,7 @@
 //   canon p x0..x3               -> pd_canon's digits
 //   from p L w0..w(L-1) P0..P15  -> pd_from_words (P: digits of 2^(32j) mod p^4)
 //   to p L d0..d3                -> pd_to_words's L words
-//   bounds p m L                 -> ok kf kb0..kb6 fast
+//   bounds p m L                 -> ok kf kb0..kb6 fast dft_ok
 #include <cstdio>
 #include <cstring>
 #include <iostream>
@@ -96,7 +96,7 @@ int main() {
             const bool ok = dkss_planning::pd_lazy_bounds(p, m, L, &bi);
             printf("%d %u", ok ? 1 : 0, bi.kf);
             for (int i = 0; i < 7; ++i) printf(" %u", bi.kb[i]);
-            printf(" %d\n", bi.fast ? 1 : 0);
+            printf(" %d %d\n", bi.fast ? 1 : 0, bi.dft_ok ? 1 : 0);
         } else {
             printf("?\n");
         }

@@ -140,3 +140,5 @@ def test_limits(driver):
         assert kf == 1 and all(1 <= k <= 255 for k in kb)
     # fast carries: floor(2^32/p) = 4 for p = 998244353 and 1073479681, 585 for 7340033
     assert got[0][9] == 1 and got[2][9] == 1 and got[1][9] == 0
+    # DFTs on digits (the forward levels keeping digits in HBM) within their limits
+    assert got[0][10] == 1 and got[1][10] == 1 and got[2][10] == 1
