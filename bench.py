@@ -67,11 +67,12 @@ NCU_TRAFFIC_BYTES = {("dkss_2p24b", "ntt", "fwd_twiddle"): 46.6e6,
 # ring (profiles/stage_kernels_dkss_2p32b.md: 478 MB for 259,842 elements and
 # 408 MB for 227,584); a full launch's traffic is this times its elements.
 # The "mont" figures come from the 26-bit-limb Montgomery kernels, the "ntt"
-# ones from the p-adic digit kernels with fast carries (884.7 MB for 487,426 elements).
+# ones from the p-adic digit kernels with fast carries and digits in HBM
+# (879.6 MB for 487,426 elements).
 NCU_BYTES_PER_ELEMENT = {("dkss_2p32b", "mont", "config", "fwd_twiddle"): 1817.0,
                          ("dkss_2p26b_ring2p32", "mont", "config", "fwd_twiddle"): 1817.0,
-                         ("dkss_2p32b", "ntt", "config", "fwd_twiddle"): 1815.0,
-                         ("dkss_2p26b_ring2p32", "ntt", "config", "fwd_twiddle"): 1815.0}
+                         ("dkss_2p32b", "ntt", "config", "fwd_twiddle"): 1805.0,
+                         ("dkss_2p26b_ring2p32", "ntt", "config", "fwd_twiddle"): 1805.0}
 
 
 def parse_args():

@@ -1484,15 +1484,32 @@ __global__ void __launch_bounds__(kThreads) k_dft_fwd_half(LevelParams prm, Mod<
         else dft_dit<m, L>(smem, 1, m, 2, md);
         uint32_t B6[L];   // the lazy halves are below 2^6 q
         lz32_bias<L>(B6, md, ilog2<m>());
-        // X_v = E_v + alpha^v O_v, X_(v+m) = E_v - alpha^v O_v
-        for (int v = tm.id; v < m; v += G::NTEAMS) {
+        // X_v = E_v + alpha^v O_v, X_(v+m) = E_v - alpha^v O_v.  A thread loads the inputs
+        // of VB elements (CPL coefficients each) before it stores any output: the stores to
+        // the polynomial may alias the scratch slice for the compiler, which would
+        // otherwise keep every scratch load behind the previous output's stores.
+        constexpr int VB = 2;
+        static_assert(m % (VB * G::NTEAMS) == 0, "whole batches of elements");
+        for (int v0 = tm.id; v0 < m; v0 += VB * G::NTEAMS) {
+            uint32_t ea[VB][G::CPL][L], oy[VB][G::CPL][L];
+            bool ngs[VB][G::CPL];
+#pragma unroll
+            for (int b = 0; b < VB; ++b)
+#pragma unroll
+                for (int c = 0; c < G::CPL; ++c) {
+                    const int v = v0 + b * G::NTEAMS, t = tm.lane + c * G::TEAM;
+                    ld_res<L>(ea[b][c], E + v * G::EW + t * L);
+                    shifted<m, L>(oy[b][c], ngs[b][c], smem + v * G::ES, t, v);
+                }
+#pragma unroll
+            for (int b = 0; b < VB; ++b)
 #pragma unroll
             for (int c = 0; c < G::CPL; ++c) {
-                const int t = tm.lane + c * G::TEAM;
-                uint32_t a[L], y[L], pl[L], mi[L];
-                bool ng;
-                ld_res<L>(a, E + v * G::EW + t * L);
-                shifted<m, L>(y, ng, smem + v * G::ES, t, v);
+                const int v = v0 + b * G::NTEAMS, t = tm.lane + c * G::TEAM;
+                uint32_t pl[L], mi[L];
+                const uint32_t(&a)[L] = ea[b][c];
+                const uint32_t(&y)[L] = oy[b][c];
+                const bool ng = ngs[b][c];
                 if (lazy) {
                     uint32_t x[L];
                     lz32_add<L>(x, a, y);
@@ -1547,32 +1564,47 @@ __global__ void __launch_bounds__(kThreads) k_dft_inv_half(LevelParams prm, Mod<
     for (uint64_t column = blockIdx.x; column < cols; column += gridDim.x) {
         const uint64_t blk = column / mu_d, l = column % mu_d;
         const uint64_t base = blk * prm.len;
-        // s_k = x_k + x_(k+m) to shared memory, d_k = alpha^(ROOT k) (x_k - x_(k+m)) to the scratch slice
-        for (int idx = threadIdx.x; idx < m * m; idx += kThreads) {
-            const int k = idx / m, t = idx % m;
-            const uint32_t* pa = poly + (base + (uint64_t)k * mu_d + l) * G::EW;
-            const uint32_t* pb = poly + (base + (uint64_t)(k + m) * mu_d + l) * G::EW;
-            uint32_t a[L], b[L], r[L];
-            ld_res<L>(a, pa + t * L);
-            ld_res<L>(b, pb + t * L);
-            add_mod<L>(r, a, b, md);
-            st_res<L>(smem + k * G::ES + t * L, r);
-            // coefficient t of alpha^sh (a - b): +-(a - b)[t - sh]; b - a where the sign is negative
-            const int sh = (ROOT * k) & (G::TWO_M - 1);
-            int src = t - sh;
-            bool neg = false;
-            if (src < 0) {
-                src += m;
-                neg = true;
+        // s_k = x_k + x_(k+m) to shared memory, d_k = alpha^(ROOT k) (x_k - x_(k+m)) to the scratch slice.
+        // A thread loads the residues of IB items before it stores any result: the stores
+        // to the scratch slice may alias the polynomial for the compiler, which would
+        // otherwise keep every load behind the previous item's store.
+        constexpr int IB = 4;
+        static_assert((m * m) % (IB * kThreads) == 0, "whole batches of items");
+        for (int idx0 = threadIdx.x; idx0 < m * m; idx0 += IB * kThreads) {
+            uint32_t a[IB][L], b[IB][L], a2[IB][L], b2[IB][L];
+#pragma unroll
+            for (int i = 0; i < IB; ++i) {
+                const int idx = idx0 + i * kThreads;
+                const int k = idx / m, t = idx % m;
+                const uint32_t* pa = poly + (base + (uint64_t)k * mu_d + l) * G::EW;
+                const uint32_t* pb = poly + (base + (uint64_t)(k + m) * mu_d + l) * G::EW;
+                ld_res<L>(a[i], pa + t * L);
+                ld_res<L>(b[i], pb + t * L);
+                // coefficient t of alpha^sh (a - b): +-(a - b)[t - sh]; b - a where the sign is negative
+                const int sh = (ROOT * k) & (G::TWO_M - 1);
+                int src = t - sh;
+                bool neg = false;
                 if (src < 0) {
                     src += m;
-                    neg = false;
+                    neg = true;
+                    if (src < 0) {
+                        src += m;
+                        neg = false;
+                    }
                 }
+                ld_res<L>(a2[i], (neg ? pb : pa) + src * L);
+                ld_res<L>(b2[i], (neg ? pa : pb) + src * L);
             }
-            ld_res<L>(a, (neg ? pb : pa) + src * L);
-            ld_res<L>(b, (neg ? pa : pb) + src * L);
-            sub_mod<L>(r, a, b, md);
-            st_res<L>(D + k * G::EW + t * L, r);
+#pragma unroll
+            for (int i = 0; i < IB; ++i) {
+                const int idx = idx0 + i * kThreads;
+                const int k = idx / m, t = idx % m;
+                uint32_t r[L];
+                add_mod<L>(r, a[i], b[i], md);
+                st_res<L>(smem + k * G::ES + t * L, r);
+                sub_mod<L>(r, a2[i], b2[i], md);
+                st_res<L>(D + k * G::EW + t * L, r);
+            }
         }
         __syncthreads();
         // even outputs X_(2v), from slot bitrev(v)
