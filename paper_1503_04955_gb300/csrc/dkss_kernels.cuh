@@ -1453,7 +1453,7 @@ __device__ __forceinline__ void half_load_fwd(const LevelParams& prm, uint32_t* 
 }
 
 template <int m, int L, bool FIRST>
-__global__ void __launch_bounds__(kThreads) k_dft_fwd_half(LevelParams prm, Mod<L> md, uint32_t* scratch,
+__global__ void __launch_bounds__(kThreads, 3) k_dft_fwd_half(LevelParams prm, Mod<L> md, uint32_t* scratch,
                                                            uint32_t operands) {
     using G = Geo<m, L>;
     extern __shared__ __align__(16) uint32_t smem[];
@@ -1526,17 +1526,18 @@ __global__ void __launch_bounds__(kThreads) k_dft_fwd_half(LevelParams prm, Mod<
                 if constexpr (L == kPdDigits) {
                     if (prm.pd_io) {   // canonical digits for the bad multiplications
                         uint32_t dg[L];
+                        // 4-word residues: p^4 >= 2^96, so p > 2^24 and the short conversion applies
                         if (prm.pd_fast) {
                             const ModPD<L, true> f = pd_fast_view(prm.pd);
-                            pd_from_words<L, L>(dg, pl, prm.pd_pw, f);
+                            pd_from_words4_large_p(dg, pl, prm.pd_pw, f);
 #pragma unroll
                             for (int w = 0; w < L; ++w) pl[w] = dg[w];
-                            pd_from_words<L, L>(dg, mi, prm.pd_pw, f);
+                            pd_from_words4_large_p(dg, mi, prm.pd_pw, f);
                         } else {
-                            pd_from_words<L, L>(dg, pl, prm.pd_pw, prm.pd);
+                            pd_from_words4_large_p(dg, pl, prm.pd_pw, prm.pd);
 #pragma unroll
                             for (int w = 0; w < L; ++w) pl[w] = dg[w];
-                            pd_from_words<L, L>(dg, mi, prm.pd_pw, prm.pd);
+                            pd_from_words4_large_p(dg, mi, prm.pd_pw, prm.pd);
                         }
 #pragma unroll
                         for (int w = 0; w < L; ++w) mi[w] = dg[w];

@@ -174,6 +174,22 @@ DKSS_HD void pd_from_words(uint32_t (&r)[Z], const uint32_t (&w)[L], const uint3
     pd_carry<Z>(r, c, md);
 }
 
+// pd_from_words for 4 words and 4 digits where p > 2^22: 2^32 < p^2 and
+// 2^64 < p^3, so the digits of 2^32 are zero from the third on and those of
+// 2^64 from the fourth on; their products are left out (9 instead of 12).
+template <bool F>
+DKSS_HD void pd_from_words4_large_p(uint32_t (&r)[4], const uint32_t (&w)[4], const uint32_t* pw,
+                                    const ModPD<4, F>& md) {
+    uint64_t c[4] = {w[0], 0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) c[k] += (uint64_t)w[1] * ld_const(pw + 4 + k);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) c[k] += (uint64_t)w[2] * ld_const(pw + 8 + k);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) c[k] += (uint64_t)w[3] * ld_const(pw + 12 + k);
+    pd_carry<4>(r, c, md);
+}
+
 // 32-bit words of a residue from its canonical digits (Horner's rule from
 // the top digit): the canonical value below p^Z < 2^(32L).
 template <int L, int Z, bool F>

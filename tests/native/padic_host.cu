@@ -7,6 +7,7 @@
 //   canon p x0..x3               -> pd_canon's digits
 //   from p L w0..w(L-1) P0..P15  -> pd_from_words (P: digits of 2^(32j) mod p^4)
 //   to p L d0..d3                -> pd_to_words's L words
+//   from4 p w0..w3 P0..P15       -> pd_from_words4_large_p (p > 2^22)
 //   bounds p m L                 -> ok kf kb0..kb6 fast dft_ok
 #include <cstdio>
 #include <cstring>
@@ -77,6 +78,12 @@ int main() {
                 pd_canon<4>(r, a, md);
                 printf("%u %u %u %u\n", r[0], r[1], r[2], r[3]);
             }
+        } else if (op == "from4") {   // the short conversion for p > 2^22
+            uint32_t w[4], pw[16];
+            for (auto& v : w) in >> v;
+            for (auto& v : pw) in >> v;
+            pd_from_words4_large_p(r, w, pw, md);
+            printf("%u %u %u %u\n", r[0], r[1], r[2], r[3]);
         } else if (op == "from" || op == "to") {
             int L;
             in >> L;

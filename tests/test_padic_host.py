@@ -128,6 +128,23 @@ def test_words_round_trip(driver):
     assert call(driver, lines) == want
 
 
+def test_short_conversion_for_large_p(driver):
+    """For p > 2^22 the digits of 2^32 mod p^4 end after the second and those
+    of 2^64 after the third: the short conversion leaves those products out
+    and must give the same digits for every 4-word value."""
+    rng = random.Random(11)
+    lines, want = [], []
+    for p in (998244353, 1073479681, 754974721, 7340033):
+        q = p ** 4
+        pw = sum((digits(p, pow(2, 32 * j, q)) for j in range(4)), [])
+        assert pw[4 + 2] == pw[4 + 3] == pw[8 + 3] == 0
+        for v in [0, 1, q - 1, W ** 4 - 1] + [rng.randrange(W ** 4) for _ in range(50)]:
+            words = [(v >> (32 * j)) & (W - 1) for j in range(4)]
+            lines.append("from4 %d %s %s" % (p, " ".join(map(str, words)), " ".join(map(str, pw))))
+            want.append(digits(p, v % q))
+    assert call(driver, lines) == want
+
+
 def test_limits(driver):
     """The rings of the 2^28- and 2^32-bit workloads pass the limit check;
     primes at or above 2^30, more than four words and tiny primes do not."""
