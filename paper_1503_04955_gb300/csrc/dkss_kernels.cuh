@@ -602,7 +602,9 @@ __device__ __forceinline__ void load_shifted_pd(uint32_t (&out)[Z], const uint32
     }
     uint32_t v[L], y[Z];
     ld_res<L>(v, x + src * L);
-    pd_from_words<L, Z>(y, v, pw, md);
+    // 4-word residues: p^4 >= 2^95, so p > 2^23 and the short conversion applies
+    if constexpr (L == 4 && Z == 4) pd_from_words4_large_p(y, v, pw, md);
+    else pd_from_words<L, Z>(y, v, pw, md);
 #pragma unroll
     for (int i = 0; i < Z; ++i) out[i] = neg ? bn[i] - y[i] : y[i];
 }
